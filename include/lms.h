@@ -1,0 +1,136 @@
+/*
+ * lms.h -- C ABI of the GB300 exact 2D Least Median of Squares line estimator.
+ *
+ * Problem (Shapira & Hassner, Sec. 1 Eq. 1 and Sec. 3.1): for points
+ * (x_k, y_k), k = 0..n-1, and an order statistic h (default floor(n/2)+1),
+ * find the line y = theta1 x + theta2 minimising the h-th smallest squared
+ * residual.  Equivalently (Sec. 3.1) find the narrowest vertical slab holding
+ * h points; the line bisects it and med_sq = (slab height / 2)^2.  By the
+ * equioscillation property (Sec. 3.3) the optimal slope is one of the
+ * pairwise slopes (y_j - y_i)/(x_j - x_i); the library examines every one of
+ * them exactly (Algorithm 1, Sec. 3.4).
+ *
+ * Ties are broken by the lexicographic order of (slab height, theta1,
+ * theta2) as exact rationals; (i, j) is then the smallest index pair whose
+ * slope is theta1.  For int16 inputs every field of lms_result is exact and
+ * reproducible bit for bit: theta1, theta2 and med_sq are each one IEEE
+ * double operation on the exact integers.
+ *
+ * Conventions for every call:
+ *   - Pointers documented as "device" must be CUDA device (or managed)
+ *     memory of the current device; "host" pointers are ordinary host memory.
+ *   - The caller owns all input and output buffers.  The library owns an
+ *     internal per-device workspace (grown with cudaMalloc on demand) unless
+ *     the caller installs one with lms_set_workspace.
+ *   - Device-pointer calls are asynchronous on `stream` (NULL = the legacy
+ *     default stream); host-pointer calls synchronise before returning.
+ *   - The return value reports argument and launch errors detected on the
+ *     host.  The per-fit outcome is lms_result.status, written on the device.
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef LMS_H
+#define LMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LMS_API __attribute__((visibility("default")))
+#else
+#define LMS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared without the CUDA headers. */
+typedef struct CUstream_st *lms_stream_t;
+
+enum lms_status {
+    LMS_OK = 0,
+    LMS_ERR_ARG = 1,          /* n < 2, n > 65536, h outside [1, n], null pointer, bad enum */
+    LMS_ERR_RANGE = 2,        /* float input that is not finite */
+    LMS_ERR_VERTICAL = 3,     /* all x equal: no pairwise slope; result is the window at slope 0 */
+    LMS_ERR_TIMEOUT = 4,      /* a bounded device wait expired */
+    LMS_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+    LMS_ERR_WORKSPACE = 6,    /* installed workspace too small (or growth needed during capture) */
+    LMS_ERR_UNSUPPORTED = 7,  /* combination not implemented (e.g. plain algorithm with n > 1024) */
+    LMS_ERR_INTERNAL = 8      /* a device-side consistency check failed (reported, never silent) */
+};
+
+enum lms_dtype {
+    LMS_I16 = 0,              /* int16 coordinates, exact integer arithmetic */
+    LMS_F32 = 1               /* float32 coordinates */
+};
+
+enum lms_algo {
+    LMS_ALGO_AUTO = 0,        /* library choice */
+    LMS_ALGO_PLAIN = 1,       /* sort the projections at every pairwise slope (n <= 1024) */
+    LMS_ALGO_SWEEP = 2,       /* exact kinetic sweep over slope-sorted events */
+    LMS_ALGO_BNB = 3          /* seeded branch-and-bound over slope intervals + sweep of survivors */
+};
+
+typedef struct {
+    int32_t algorithm;        /* enum lms_algo */
+    int32_t sweepers;         /* kinetic-sweep workers per launch, 0 = auto */
+    int32_t buckets;          /* slope buckets for event generation, 0 = auto */
+    int32_t reserved[5];      /* must be zero */
+} lms_options;
+
+/* Result of one fit: 88 bytes, same layout on host and device. */
+typedef struct {
+    int64_t w_num, w_den;     /* slab height w = w_num / w_den, w_den = s_den */
+    int64_t s_num, s_den;     /* theta1 = s_num / s_den, reduced, s_den > 0 */
+    int64_t t_num, t_den;     /* theta2 = t_num / t_den, t_den = 2 s_den */
+    double theta1, theta2;    /* the line y = theta1 x + theta2 */
+    double med_sq;            /* (w/2)^2: the h-th smallest squared residual */
+    int32_t i, j;             /* smallest pair (i < j) with slope theta1; -1 if none */
+    int32_t status;           /* enum lms_status for this fit */
+    int32_t algorithm;        /* enum lms_algo that produced it */
+} lms_result;
+
+/*
+ * lms_fit -- exact LMS of one point set (Algorithm 1, Sec. 3.4).
+ *   x, y    device arrays of n coordinates (int16_t or float, per dtype), SoA.
+ *   n       2 <= n <= 65536.
+ *   h       order statistic in [1, n]; 0 selects floor(n/2) + 1.
+ *   dtype   enum lms_dtype.
+ *   opt     NULL for defaults.
+ *   out     device pointer to one lms_result.
+ * Asynchronous on `stream`.  Returns LMS_OK or a host-detected error.
+ */
+LMS_API int lms_fit(const void *x, const void *y, int64_t n, int64_t h, int32_t dtype,
+            const lms_options *opt, lms_result *out, lms_stream_t stream);
+
+/*
+ * lms_fit_host -- same as lms_fit with host arrays and a host result: copies
+ * the coordinates to the device, fits, copies the result back and waits.
+ * Returns LMS_OK or the error; out->status holds the fit's status.
+ */
+LMS_API int lms_fit_host(const void *x, const void *y, int64_t n, int64_t h, int32_t dtype,
+                 const lms_options *opt, lms_result *out, lms_stream_t stream);
+
+/*
+ * lms_workspace_size -- device bytes one lms_fit of this size needs.
+ * lms_set_workspace  -- install a caller-owned device buffer (NULL restores
+ *                       the internal one).  The buffer must stay valid and
+ *                       unused by others while fits run on it.
+ * lms_reserve        -- grow the internal workspace up front (e.g. before
+ *                       capturing fits into a CUDA graph).
+ */
+LMS_API size_t lms_workspace_size(int64_t n, int32_t dtype, const lms_options *opt);
+LMS_API int lms_set_workspace(void *device_buffer, size_t bytes);
+LMS_API int lms_reserve(int64_t n, int32_t dtype, const lms_options *opt);
+
+/* Human-readable name of a status code (static string). */
+LMS_API const char *lms_status_str(int status);
+
+/* Library version string. */
+LMS_API const char *lms_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LMS_H */

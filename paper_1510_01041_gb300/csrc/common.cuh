@@ -1,0 +1,149 @@
+// common.cuh -- device helpers shared by the LMS kernels (sm_103a).
+//
+// Exact integer formulation (Sec. 1 Eq. 1, Sec. 3.1): at a candidate slope
+// s = dy/dx (dx > 0) the projection of point k scaled by dx is the exact
+// integer key_k = y_k * dx - x_k * dy = dx * (y_k - s x_k).  For int16
+// coordinates |key| <= 2^32, window widths w = key_top - key_bottom < 2^34,
+// and every cross-multiplied comparison below stays under 2^51: int64 is
+// exact throughout.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lms.h"
+
+namespace lms {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// One scored window at one slope.  dx == 0 marks "no candidate".
+struct Cand {
+    long long w;    // window width times dx
+    long long t;    // key_bottom + key_top (window centre times 2 dx)
+    int dy, dx;     // slope dy/dx, dx > 0 (not necessarily reduced)
+    int i, j;       // index pair with that slope (i < j)
+};
+static_assert(sizeof(Cand) == 32, "Cand layout");
+
+__host__ __device__ __forceinline__ Cand cand_empty()
+{
+    Cand c;
+    c.w = 0; c.t = 0; c.dy = 0; c.dx = 0; c.i = -1; c.j = -1;
+    return c;
+}
+
+// Lexicographic order on (w, theta1, theta2, i, j) as exact rationals.
+__host__ __device__ __forceinline__ bool cand_better(const Cand &a, const Cand &b)
+{
+    if (a.dx == 0) return false;
+    if (b.dx == 0) return true;
+    long long l = a.w * (long long)b.dx, r = b.w * (long long)a.dx;
+    if (l != r) return l < r;
+    l = (long long)a.dy * b.dx;
+    r = (long long)b.dy * a.dx;
+    if (l != r) return l < r;
+    l = a.t * (long long)b.dx;
+    r = b.t * (long long)a.dx;
+    if (l != r) return l < r;
+    if (a.i != b.i) return a.i < b.i;
+    return a.j < b.j;
+}
+
+__device__ __forceinline__ Cand cand_shfl_xor(const Cand &c, int m)
+{
+    Cand o;
+    o.w = __shfl_xor_sync(FULL, c.w, m);
+    o.t = __shfl_xor_sync(FULL, c.t, m);
+    o.dy = __shfl_xor_sync(FULL, c.dy, m);
+    o.dx = __shfl_xor_sync(FULL, c.dx, m);
+    o.i = __shfl_xor_sync(FULL, c.i, m);
+    o.j = __shfl_xor_sync(FULL, c.j, m);
+    return o;
+}
+
+// Warp-wide best; every lane returns the same record.
+__device__ __forceinline__ Cand warp_best(Cand c)
+{
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        Cand o = cand_shfl_xor(c, m);
+        if (cand_better(o, c)) c = o;
+    }
+    return c;
+}
+
+// Points are staged as one 32-bit word: x in the low half, y in the high half.
+__host__ __device__ __forceinline__ int pack_xy(int x, int y)
+{
+    return (int)(((unsigned)y << 16) | ((unsigned)x & 0xffffu));
+}
+__device__ __forceinline__ int px(int p) { return (int)(short)(p & 0xffff); }
+__device__ __forceinline__ int py(int p) { return p >> 16; }
+
+// Scaled projection key_k at slope dy/dx.
+__device__ __forceinline__ long long proj(int p, int dy, int dx)
+{
+    return (long long)py(p) * dx - (long long)px(p) * dy;
+}
+
+// Slope of the pair (p, q) with dx > 0; returns false when x_p == x_q.
+__device__ __forceinline__ bool pair_slope(int p, int q, int &dy, int &dx)
+{
+    dx = px(q) - px(p);
+    dy = py(q) - py(p);
+    if (dx == 0) return false;
+    if (dx < 0) { dx = -dx; dy = -dy; }
+    return true;
+}
+
+// Exact, strictly order-preserving integer key of a slope dy/dx
+// (|dy| < 2^16, 0 < dx < 2^16): floor(dy * 2^32 / dx).  Two different
+// slopes differ by at least 1/(dx1 dx2) > 2^-32, so their keys differ;
+// equal slopes give equal keys.  The quotient is assembled from three
+// 16-bit digits, each estimated with a float reciprocal and corrected once
+// with an exact integer remainder.
+__device__ __forceinline__ long long slope_key(int dy, int dx)
+{
+    const unsigned a = (unsigned)(dy < 0 ? -dy : dy);
+    const unsigned d = (unsigned)dx;
+    const float rd = __frcp_rn((float)d);
+    unsigned q0 = __float2uint_rz((float)a * rd);
+    long long r = (long long)a - (long long)q0 * d;
+    if (r < 0) { --q0; r += d; } else if (r >= (long long)d) { ++q0; r -= d; }
+    unsigned t = (unsigned)r << 16;
+    unsigned q1 = __float2uint_rz((float)t * rd);
+    r = (long long)t - (long long)q1 * d;
+    if (r < 0) { --q1; r += d; } else if (r >= (long long)d) { ++q1; r -= d; }
+    t = (unsigned)r << 16;
+    unsigned q2 = __float2uint_rz((float)t * rd);
+    r = (long long)t - (long long)q2 * d;
+    if (r < 0) { --q2; r += d; } else if (r >= (long long)d) { ++q2; r -= d; }
+    long long Q = ((long long)q0 << 32) | ((long long)q1 << 16) | (long long)q2;
+    if (dy < 0) return -(Q + (r != 0));
+    return Q;
+}
+
+// Events are stored as two 16-bit point indices.  The first event of a
+// group of equal slopes stores (i, j) with i < j in (low, high); every
+// further event of the same group stores them swapped, so the order of the
+// two halves carries the "continues the previous group" bit.
+__device__ __forceinline__ unsigned ev_pack(int i, int j, bool cont)
+{
+    return cont ? ((unsigned)i << 16) | (unsigned)j : ((unsigned)j << 16) | (unsigned)i;
+}
+__device__ __forceinline__ bool ev_cont(unsigned e) { return (e & 0xffffu) > (e >> 16); }
+__device__ __forceinline__ int ev_i(unsigned e) { return (int)min(e & 0xffffu, e >> 16); }
+__device__ __forceinline__ int ev_j(unsigned e) { return (int)max(e & 0xffffu, e >> 16); }
+
+// Triangular decode of a pair index p in [0, n(n-1)/2) into i < j.
+__device__ __forceinline__ void pair_decode(long long p, int &i, int &j)
+{
+    int jj = (int)((1.0f + sqrtf(8.0f * (float)p + 1.0f)) * 0.5f);
+    while ((long long)jj * (jj - 1) / 2 > p) --jj;
+    while ((long long)(jj + 1) * jj / 2 <= p) ++jj;
+    j = jj;
+    i = (int)(p - (long long)jj * (jj - 1) / 2);
+}
+
+}  // namespace lms

@@ -1,0 +1,55 @@
+// kernels.cuh -- host-side launch declarations for the LMS kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace lms {
+
+// ---------------------------------------------------------------- plain path
+int plain_elems(int n);
+cudaError_t launch_plain(const short *x, const short *y, int n, int h, Cand *cands, int nwarps_total,
+                         cudaStream_t st);
+
+// ---------------------------------------------------------------- sweep path
+constexpr int SEG_CAP = 16384;   // events a bucket may hold to be sorted in shared memory
+constexpr int BND_MAX = 16384;   // slope-bucket boundaries (power of two, shared memory)
+constexpr int SORT_SMEM_N = 8192;  // sweep start orders sorted in shared memory up to this n
+
+// Device scratch of one sweep-path fit; carved out of the workspace by the host.
+struct SweepPlan {
+    int n, h;
+    int S;             // sampled pairs (power of two, >= 1024)
+    int B;             // target number of quantile buckets
+    int C;             // CTAs of the count / scatter passes
+    int W;             // sweepers
+    int spb;           // sweepers (warps) per sweep CTA
+    bool xy_smem;      // sweep CTAs keep all points in shared memory
+    long long emax;    // n (n - 1) / 2
+    // device buffers
+    int *xy;                   // [n] packed points
+    long long *skeys;          // [S] sampled slope keys
+    long long *skeys2;         // [S] merge ping-pong
+    long long *bnd;            // [BND_MAX] bucket boundaries, padded with INT64_MAX
+    int *meta;                 // [8] 0 nbnd, 1 P2, 2 oversize count, 3 error flags
+    unsigned *hist;            // [C][BND_MAX] per-CTA bucket counts, then offsets
+    unsigned *base;            // [BND_MAX + 1] bucket starts; base[NB] = E
+    int *oversize;             // [BND_MAX] buckets too large for the shared-memory sort
+    unsigned *ev;              // [emax] events
+    unsigned *range;           // [2W] sweeper event ranges
+    unsigned short *orders;    // [W][n] start orders
+    unsigned long long *gsort; // [W][P] global sort scratch when n > SORT_SMEM_N
+    Cand *cands;               // [2W] init + sweep candidates
+};
+
+size_t sweep_plan_bytes(int n, int W, int C, int S);
+void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int want_b);
+void sweep_plan_carve(SweepPlan &p, void *ws);
+cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cudaStream_t st);
+
+// ---------------------------------------------------------------- argmin
+cudaError_t launch_argmin(const Cand *cands, int count, lms_result *out, int algorithm, const int *err,
+                          cudaStream_t st);
+
+}  // namespace lms
