@@ -1,0 +1,294 @@
+#!/usr/bin/env python3
+"""Benchmark of the exact 2D LMS line estimator on the GB300.
+
+Workload (one "step"): one exact LMS fit of n = 8192 int16 points, 40%
+outliers (y = round(0.7 x + 100) + U{-3..3} inliers, uniform outliers), all
+n(n-1)/2 = 33,550,336 candidate slopes, through the C ABI.  Every step uses a
+fresh seeded instance already resident in HBM; L2 is flushed (256 MB write)
+before each step, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank fits its own
+instances (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_POINTS = 8192
+OUTLIER_FRAC = 0.4
+METRIC = "exact LMS solves/sec at n=8192 (candidate slopes/sec alongside)"
+UNIT = "solves/s"
+# Algorithmic work of the sweep kernel per event (one pair of points meeting):
+# 2 position reads, 4 order/position writes, 3 projections (2 IMAD each),
+# 2 window widths and centres, 2 exact candidate comparisons, decode.
+SWEEP_INT_OPS_PER_EVENT = 50
+INT_LANES_PER_SM = 128
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _reference_arm(args):
+    """The CPU oracle (O2 exact sweep) timed on the host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1510_01041_gb300 import datagen
+    oracle.build()
+    cores = oracle.max_threads()
+    inst = [datagen.line_with_outliers(N_POINTS, 1000 + s) for s in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        oracle.lms_i16(*inst[s], 0, "sweep")
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.lms_i16(*inst[args.warmup + s], 0, "sweep")
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    slopes = N_POINTS * (N_POINTS - 1) // 2
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128",
+        "data": "synthetic", "candidate_slopes_per_sec": v * slopes,
+        "config": {"workload": "single exact LMS fit, n=8192 int16, 40% outliers", "n": N_POINTS,
+                   "algorithm": "CPU oracle O2 (exact rational sweep)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full solves at n={N_POINTS}"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _cpu_baseline(x, y):
+    """Bounded oracle sample: one O2 solve of a step's instance (~10 s of CPU work)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.lms_i16(x, y, 0, "sweep")
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"1 full O2 solve at n={N_POINTS} ({dt:.1f} s)"}, r
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--algorithm", default="sweep")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--breakdown", action="store_true", help="per-stage times to stderr")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        _reference_arm(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1510_01041_gb300 import build, datagen, lms
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    total = args.warmup + args.steps
+    seeds = [rank * 100003 + 1 + s for s in range(total)]
+    host = [datagen.line_with_outliers(N_POINTS, s) for s in seeds]
+    xs = [torch.from_numpy(h[0]).to(dev) for h in host]
+    ys = [torch.from_numpy(h[1]).to(dev) for h in host]
+    out = torch.empty((total, lms.RESULT_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lms.reserve(N_POINTS, algorithm=args.algorithm)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for s in range(args.warmup):
+        flush.fill_(s & 0xff)
+        lms.fit(xs[s], ys[s], 0, args.algorithm, out=out[s])
+    barrier()
+    launches0 = lms.launch_count()
+    lms.profile_read()
+    lms.profile_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            s = args.warmup + k
+            flush.fill_(s & 0xff)
+            ev[k][0].record(stream)
+            lms.fit(xs[s], ys[s], 0, args.algorithm, out=out[s])
+            ev[k][1].record(stream)
+        barrier()
+        wall = time.perf_counter() - wall0
+    lms.profile_enable(False)
+    stages = lms.profile_read()
+    launches = lms.launch_count() - launches0
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    res = lms.decode(out)
+    bad = [r for r in res[args.warmup:] if r["status"] != lms.LMS_OK]
+    if bad:
+        raise SystemExit(f"fit failed: {bad[0]}")
+
+    # end to end: host buffers (pinned), copies inside the timed region
+    pin_x = [torch.from_numpy(h[0]).pin_memory() for h in host]
+    pin_y = [torch.from_numpy(h[1]).pin_memory() for h in host]
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        s = args.warmup + k
+        r = lms.fit_host(pin_x[s].numpy(), pin_y[s].numpy(), 0, args.algorithm)
+        assert r["status"] == lms.LMS_OK
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    slopes = N_POINTS * (N_POINTS - 1) // 2
+    solves = ws * args.steps
+    value = solves / (dev_ms / 1000.0)
+    csum = clk.summary()
+    # roofline of the dominant kernel (the sweep): exact events per launch
+    # = candidate pairs with distinct x, measured per instance on the host
+    events = [int(np.sum(np.triu(np.not_equal.outer(h[0], h[0]), 1))) for h in host[args.warmup:]]
+    sweep_ms, sweep_launches = stages.get("sweep", (0.0, 0))
+    roof = None
+    if sweep_launches:
+        per_launch_s = sweep_ms / sweep_launches / 1000.0
+        ev_per_launch = sum(events) / len(events)
+        achieved = SWEEP_INT_OPS_PER_EVENT * ev_per_launch / per_launch_s / 1e12
+        mhz = csum.get("sm_mhz") or 1462.0
+        peak = props.multi_processor_count * INT_LANES_PER_SM * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_sweep",
+                "kernel_ms": per_launch_s * 1e3, "events_per_launch": ev_per_launch,
+                "peak_basis": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int32 lanes x "
+                              f"median SM clock {mhz:.0f} MHz under load"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "candidate_slopes_per_sec": value * slopes,
+        "config": {"workload": "single exact LMS fit, n=8192 int16, 40% outliers (line_with_outliers)",
+                   "n": N_POINTS, "h": N_POINTS // 2 + 1, "algorithm": args.algorithm,
+                   "l2": "flushed before every step (256 MB write, outside the timed events)",
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": solves / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 2 * N_POINTS,
+                "d2h_bytes_per_step": lms.RESULT_DTYPE.itemsize},
+        "gpu_launches": launches,
+        "clocks": {k: csum.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "roofline": roof,
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in sorted(stages.items(), key=lambda kv: -kv[1][0])},
+        "wall_s": wall,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb, o = _cpu_baseline(*host[args.warmup])
+        r = res[args.warmup]
+        cb["agrees_with_gpu"] = (r["w_num"], r["w_den"], r["s_num"], r["s_den"], r["t_num"], r["i"], r["j"]) == (
+            o.w_num, o.w_den, o.s_num, o.s_den, o.t_num, o.i, o.j)
+        line["cpu_baseline"] = cb
+    if args.breakdown and rank == 0:
+        for k, v in sorted(stages.items(), key=lambda kv: -kv[1][0]):
+            print(f"  {k:14s} {v[0] / args.steps:9.3f} ms/step  launches {v[1]}", file=sys.stderr)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

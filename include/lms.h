@@ -123,6 +123,20 @@ LMS_API size_t lms_workspace_size(int64_t n, int32_t dtype, const lms_options *o
 LMS_API int lms_set_workspace(void *device_buffer, size_t bytes);
 LMS_API int lms_reserve(int64_t n, int32_t dtype, const lms_options *opt);
 
+/*
+ * Profiling (off by default).  lms_profile_enable(1) brackets every kernel
+ * launch of the library with CUDA events on the launch's stream.
+ * lms_profile_read waits for the recorded events, writes the accumulated
+ * milliseconds and launch counts per stage (up to max_stages entries, either
+ * pointer may be NULL), clears the record and returns the number of stages.
+ * lms_stage_name names a stage; lms_launch_count counts every kernel this
+ * library has launched since it was loaded.
+ */
+LMS_API void lms_profile_enable(int on);
+LMS_API int lms_profile_read(double *ms, int64_t *launches, int max_stages);
+LMS_API const char *lms_stage_name(int stage);
+LMS_API int64_t lms_launch_count(void);
+
 /* Human-readable name of a status code (static string). */
 LMS_API const char *lms_status_str(int status);
 

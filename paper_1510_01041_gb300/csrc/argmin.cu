@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(1024) k_argmin(const Cand *__restrict__ cands,
 cudaError_t launch_argmin(const Cand *cands, int count, lms_result *out, int algorithm, const int *err,
                           cudaStream_t st)
 {
+    StageTimer _t(STAGE_ARGMIN, st);
     k_argmin<<<1, 1024, 0, st>>>(cands, count, out, algorithm, err);
     return cudaGetLastError();
 }

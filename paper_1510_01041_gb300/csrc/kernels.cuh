@@ -7,6 +7,28 @@
 
 namespace lms {
 
+// Stages of a fit, for per-launch timing (prof.cu).
+enum Stage {
+    STAGE_PACK, STAGE_SAMPLE, STAGE_SAMPLE_SORT, STAGE_SPLITTERS, STAGE_COUNT_PAIRS, STAGE_PREFIX,
+    STAGE_SCAN, STAGE_SCATTER, STAGE_SEGSORT, STAGE_SEGSORT_BIG, STAGE_PLAN, STAGE_INIT, STAGE_SWEEP,
+    STAGE_ARGMIN, STAGE_PLAIN, STAGE_OTHER, STAGE_COUNT
+};
+
+// Counts one kernel launch and, when profiling is on, brackets it with CUDA
+// events on its stream.  Construct it right before the launch.
+class StageTimer {
+  public:
+    StageTimer(int stage, cudaStream_t st);
+    ~StageTimer();
+    StageTimer(const StageTimer &) = delete;
+    StageTimer &operator=(const StageTimer &) = delete;
+
+  private:
+    int stage_;
+    cudaStream_t st_;
+    cudaEvent_t a_;
+};
+
 // ---------------------------------------------------------------- plain path
 int plain_elems(int n);
 cudaError_t launch_plain(const short *x, const short *y, int n, int h, Cand *cands, int nwarps_total,

@@ -198,7 +198,8 @@ cudaError_t launch_plain(const short *x, const short *y, int n, int h, Cand *can
 #define LMS_PLAIN_CASE(EE)                                                                     \
     case EE:                                                                                   \
         cudaFuncSetAttribute(k_plain<EE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        k_plain<EE><<<blocks, threads, smem, st>>>(x, y, n, h, npairs, cands);                  \
+        { StageTimer _t(STAGE_PLAIN, st);                                                      \
+        k_plain<EE><<<blocks, threads, smem, st>>>(x, y, n, h, npairs, cands); }                \
         break;
     switch (E) {
         LMS_PLAIN_CASE(1)

@@ -284,8 +284,18 @@ __device__ __forceinline__ long long event_key(const int *__restrict__ xy, unsig
     return slope_key(dy, dx);
 }
 
-// Sort each bucket by exact slope key; buckets with more than SEG_CAP
-// events are listed for k_segsort_big.
+__device__ __forceinline__ unsigned pair_of(unsigned e) { return ((unsigned)ev_i(e) << 16) | (unsigned)ev_j(e); }
+
+// (slope key, index pair) order: inside a group of equal slopes the event
+// with the smallest pair comes first.
+__device__ __forceinline__ bool ev_less(long long ka, unsigned ea, long long kb, unsigned eb)
+{
+    return ka < kb || (ka == kb && pair_of(ea) < pair_of(eb));
+}
+
+// Sort each bucket by (exact slope key, pair); buckets with more than
+// SEG_CAP events are listed for k_segsort_big.  A bucket holding a single
+// slope only needs its smallest pair moved to the front.
 __global__ void __launch_bounds__(1024) k_segsort(const int *__restrict__ xy, unsigned *__restrict__ ev,
                                                   const unsigned *__restrict__ base,
                                                   const long long *__restrict__ bnd, int *__restrict__ meta,
@@ -294,14 +304,41 @@ __global__ void __launch_bounds__(1024) k_segsort(const int *__restrict__ xy, un
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_key = reinterpret_cast<long long *>(smem);
     unsigned *s_ev = reinterpret_cast<unsigned *>(smem + SEG_CAP * sizeof(long long));
+    __shared__ unsigned s_min[32];
     const int NB = meta[0] + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int b = blockIdx.x; b < NB; b += gridDim.x) {
         const unsigned off = base[b], m = base[b + 1] - off;
         if (m == 0) continue;
         const bool singleton = (b > 0 && b < NB - 1 && bnd[b] == bnd[b - 1] + 1);
         if (m == 1 || singleton) {
+            // position of the smallest pair (pairs are distinct)
+            unsigned best = 0xffffffffu, bpos = 0;
             for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-                const unsigned e = ev[off + k];
+                const unsigned pv = pair_of(ev[off + k]);
+                if (pv < best) { best = pv; bpos = k; }
+            }
+            for (int s = 16; s >= 1; s >>= 1) {
+                const unsigned ob = __shfl_xor_sync(FULL, best, s), op = __shfl_xor_sync(FULL, bpos, s);
+                if (ob < best) { best = ob; bpos = op; }
+            }
+            __syncthreads();
+            if (lane == 0) { s_min[warp] = best; s_key[warp] = bpos; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned bb = 0xffffffffu, bp = 0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+                    if (s_min[q] < bb) { bb = s_min[q]; bp = (unsigned)s_key[q]; }
+                s_min[0] = bp;
+            }
+            __syncthreads();
+            const unsigned mpos = s_min[0];
+            const unsigned e0 = ev[off], em = ev[off + mpos];
+            __syncthreads();
+            for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+                unsigned e = ev[off + k];
+                if (k == 0) e = em;
+                else if (k == mpos) e = e0;
                 ev[off + k] = ev_pack(ev_i(e), ev_j(e), k > 0);
             }
             continue;
@@ -323,7 +360,7 @@ __global__ void __launch_bounds__(1024) k_segsort(const int *__restrict__ xy, un
                 s_ev[k] = e;
             } else {
                 s_key[k] = KEY_INF;
-                s_ev[k] = 0;
+                s_ev[k] = 0xffffffffu;
             }
         }
         __syncthreads();
@@ -334,9 +371,10 @@ __global__ void __launch_bounds__(1024) k_segsort(const int *__restrict__ xy, un
                     const int l = i + j;
                     const bool up = (i & k) == 0;
                     const long long a = s_key[i], c = s_key[l];
-                    if ((a > c) == up && a != c) {
+                    const unsigned ea = s_ev[i], ec = s_ev[l];
+                    if (up ? ev_less(c, ec, a, ea) : ev_less(a, ea, c, ec)) {
                         s_key[i] = c; s_key[l] = a;
-                        const unsigned te = s_ev[i]; s_ev[i] = s_ev[l]; s_ev[l] = te;
+                        s_ev[i] = ec; s_ev[l] = ea;
                     }
                 }
                 __syncthreads();
@@ -371,7 +409,7 @@ __global__ void __launch_bounds__(1024) k_segsort_big(const int *__restrict__ xy
                 const unsigned i = blk * k + r, l = blk * k + k - 1 - r;
                 if (l >= m) continue;
                 const unsigned ea = a[i], eb = a[l];
-                if (event_key(xy, ea) > event_key(xy, eb)) { a[i] = eb; a[l] = ea; }
+                if (ev_less(event_key(xy, eb), eb, event_key(xy, ea), ea)) { a[i] = eb; a[l] = ea; }
             }
             __syncthreads();
             for (unsigned j = k >> 2; j >= 1; j >>= 1) {
@@ -380,7 +418,7 @@ __global__ void __launch_bounds__(1024) k_segsort_big(const int *__restrict__ xy
                     const unsigned l = i + j;
                     if (l >= m) continue;
                     const unsigned ea = a[i], eb = a[l];
-                    if (event_key(xy, ea) > event_key(xy, eb)) { a[i] = eb; a[l] = ea; }
+                    if (ev_less(event_key(xy, eb), eb, event_key(xy, ea), ea)) { a[i] = eb; a[l] = ea; }
                 }
                 __syncthreads();
             }
@@ -480,6 +518,27 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
         a[k] = k < n ? order_word(proj(xy[k], dy, dx), k) : ~0ull;
     __syncthreads();
     cta_bitonic_u64(a, P);
+    // runs of equal projections at the first slope: x ascending, then index
+    // (the order just before that slope)
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const long long kq = word_key(a[q]);
+        if ((q > 0 && word_key(a[q - 1]) == kq) || q + 1 >= n || word_key(a[q + 1]) != kq) continue;
+        int r = q + 1;
+        while (r + 1 < n && word_key(a[r + 1]) == kq) ++r;
+        for (int u = q + 1; u <= r; ++u) {
+            const unsigned long long v = a[u];
+            const int xv = px(xy[v & 0xffffu]);
+            int t = u - 1;
+            while (t >= q) {
+                const int xt = px(xy[a[t] & 0xffffu]);
+                if (xt < xv || (xt == xv && (a[t] & 0xffffu) < (v & 0xffffu))) break;
+                a[t + 1] = a[t];
+                --t;
+            }
+            a[t + 1] = v;
+        }
+    }
+    __syncthreads();
     for (int k = threadIdx.x; k < n; k += blockDim.x)
         orders[(size_t)w * n + k] = (unsigned short)(a[k] & 0xffffu);
     // every window at the first slope
@@ -489,22 +548,11 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
         const long long wd = word_key(a[q + h - 1]) - word_key(a[q]);
         if (wd < bw) { bw = wd; ba = q; }
     }
-    // smallest index pair of the first group of equal slopes
+    // the first event of a group carries its smallest index pair
     unsigned mp = 0xffffffffu;
-    if (!vertical && warp == 0) {
-        for (unsigned base_k = start;; base_k += 32) {
-            const unsigned k = base_k + lane;
-            unsigned e = 0;
-            bool member = false;
-            if (k < end) {
-                e = ev[k];
-                member = (k == start) || ev_cont(e);
-            }
-            const unsigned bal = __ballot_sync(FULL, member);
-            const int valid = (bal == FULL) ? 32 : __ffs(~bal) - 1;
-            if (lane < valid) mp = min(mp, ((unsigned)ev_i(e) << 16) | (unsigned)ev_j(e));
-            if (bal != FULL) break;
-        }
+    if (!vertical) {
+        const unsigned e = ev[start];
+        mp = ((unsigned)ev_i(e) << 16) | (unsigned)ev_j(e);
     }
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
@@ -540,11 +588,6 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
 }
 
 // ---------------------------------------------------------------- sweep
-struct SweepSmem {
-    unsigned short *order, *pos;
-    unsigned *bm;
-};
-
 template <bool XY_SMEM>
 __device__ __forceinline__ int load_xy(const int *s_xy, const int *__restrict__ g_xy, int k)
 {
@@ -553,8 +596,30 @@ __device__ __forceinline__ int load_xy(const int *s_xy, const int *__restrict__ 
 
 __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// One warp per sweeper.  Lane 0 applies simple events (two points meet);
-// the whole warp handles groups of equal slopes (collinear points).
+constexpr int RUN_LANE_MAX = 24;   // runs up to this length are handled by one lane
+
+// One warp per sweeper; each lane takes one of up to 32 consecutive events.
+//
+// Invariant: between two event slopes the order is sorted by projection, and
+// inside every run of equal projections at an event slope the order is x
+// ascending (the order just before the slope).  The just-after order of a
+// run is x descending, i.e. the run reversed.
+//
+// Per event (a, b) with x_a < x_b at slope s:
+//   done    b already sits below a: its run was reversed by an earlier event
+//           of the same group; nothing to do.
+//   simple  a, b adjacent and both outer neighbours project elsewhere: the
+//           run is the pair; swap it.
+//   run     three or more collinear points: the lane finds the run by
+//           comparing projections; the lowest lane of each run (same group,
+//           same first position) reverses it.  Runs longer than
+//           RUN_LANE_MAX are reversed by the whole warp.
+// Every active lane owns the positions [lo, hi] it rewrites and re-scores
+// the window starting at lo and the window ending at hi.  Lanes of different
+// slopes run in parallel unless an earlier lane's [lo, hi] meets a later
+// lane's [lo - 1, hi + 1] or one of its window ends lo + h - 1, hi - h + 1;
+// the batch is cut before the first such lane.  All reads of a batch happen
+// before its writes.
 template <bool XY_SMEM>
 __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int n, int h,
                                                const unsigned *__restrict__ ev,
@@ -564,13 +629,11 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int nwords = (n + 31) >> 5;
     int *s_xy = reinterpret_cast<int *>(smem);
     const size_t off0 = XY_SMEM ? align16((size_t)n * 4) : 0;
-    const size_t per = 2 * align16((size_t)n * 2) + align16((size_t)nwords * 4);
-    unsigned short *order = reinterpret_cast<unsigned short *>(smem + off0 + warp * per);
-    unsigned short *pos = order + align16((size_t)n * 2) / 2;
-    unsigned *bm = reinterpret_cast<unsigned *>(reinterpret_cast<unsigned char *>(pos) + align16((size_t)n * 2));
+    const size_t half = align16((size_t)n * 2);
+    unsigned short *order = reinterpret_cast<unsigned short *>(smem + off0 + warp * 2 * half);
+    unsigned short *pos = reinterpret_cast<unsigned short *>(smem + off0 + warp * 2 * half + half);
     if (XY_SMEM) {
         for (int k = threadIdx.x; k < n; k += blockDim.x) s_xy[k] = g_xy[k];
         __syncthreads();
@@ -578,158 +641,189 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
     const int w = blockIdx.x * nwarp + warp;
     if (w >= W) return;
     const unsigned start = range[2 * w], end = range[2 * w + 1];
+    auto XY = [&](int k) { return load_xy<XY_SMEM>(s_xy, g_xy, k); };
     Cand best = cand_empty();
+    auto offer = [&](long long wd, long long t, int dy, int dx, unsigned pr) {
+        // cheap reject on the width alone before the full lexicographic test
+        if (best.dx != 0 && wd * (long long)best.dx > best.w * (long long)dx) return;
+        Cand c;
+        c.w = wd; c.t = t; c.dy = dy; c.dx = dx;
+        c.i = (int)(pr >> 16); c.j = (int)(pr & 0xffffu);
+        if (cand_better(c, best)) best = c;
+    };
     if (start < end) {
         for (int a = lane; a < n; a += 32) {
             const unsigned short p = orders[(size_t)w * n + a];
             order[a] = p;
             pos[p] = (unsigned short)a;
         }
-        for (int k = lane; k < nwords; k += 32) bm[k] = 0u;
         __syncwarp();
-        auto XY = [&](int k) { return load_xy<XY_SMEM>(s_xy, g_xy, k); };
-        auto offer = [&](long long wd, long long t, int dy, int dx, int i, int j) {
-            Cand c;
-            c.w = wd; c.t = t; c.dy = dy; c.dx = dx; c.i = i; c.j = j;
-            if (cand_better(c, best)) best = c;
-        };
-        // a group of equal slopes: events [g0, g1)
-        auto group = [&](unsigned g0, unsigned g1) {
-            const unsigned e0 = ev[g0];
-            int dy, dx;
-            pair_slope(XY(ev_i(e0)), XY(ev_j(e0)), dy, dx);
-            unsigned mp = 0xffffffffu;
-            for (unsigned k = g0 + lane; k < g1; k += 32) {
-                const unsigned e = ev[k];
-                const int i = ev_i(e), j = ev_j(e);
-                mp = min(mp, ((unsigned)i << 16) | (unsigned)j);
-                const int p = pos[i], q = pos[j];
-                atomicOr(&bm[p >> 5], 1u << (p & 31));
-                atomicOr(&bm[q >> 5], 1u << (q & 31));
+        const unsigned lanemask_le = 0xffffffffu >> (31 - lane);
+        unsigned carried = 0xffffffffu;   // smallest pair of the group open at k
+        unsigned k = start;
+        unsigned e_cur = (k + lane < end) ? ev[k + lane] : 0u;
+        unsigned e_nxt = (k + 32 + lane < end) ? ev[k + 32 + lane] : 0u;
+        while (k < end) {
+            const unsigned navail = min(32u, end - k);
+            const bool valid = (unsigned)lane < navail;
+            const unsigned e = e_cur;
+            const bool is_start = valid && !ev_cont(e);
+            const unsigned smask = __ballot_sync(FULL, is_start);
+            const unsigned le = smask & lanemask_le;
+            const int gfirst = le ? 31 - __clz(le) : -1;
+            const unsigned pairv = ((unsigned)ev_i(e) << 16) | (unsigned)ev_j(e);
+            unsigned gmin = __shfl_sync(FULL, pairv, gfirst < 0 ? 0 : gfirst);
+            if (gfirst < 0) gmin = carried;
+            // ---- analysis (reads only)
+            int a = ev_i(e), b = ev_j(e);
+            int Pa = XY(a), Pb = XY(b);
+            if (px(Pa) > px(Pb)) {
+                const int t = a; a = b; b = t;
+                const int tp = Pa; Pa = Pb; Pb = tp;
             }
-#pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) mp = min(mp, __shfl_xor_sync(FULL, mp, m));
-            __syncwarp();
-            const int gi = (int)(mp >> 16), gj = (int)(mp & 0xffffu);
-            int covered = -1;
-            for (int wb = 0; wb < nwords; wb += 32) {
-                const unsigned word = (wb + lane < nwords) ? bm[wb + lane] : 0u;
-                unsigned nz = __ballot_sync(FULL, word != 0u);
-                while (nz) {
-                    const int l = __ffs(nz) - 1;
-                    nz &= nz - 1;
-                    const unsigned wd = __shfl_sync(FULL, word, l);
-                    if (lane == 0) {
-                        unsigned bits = wd;
-                        while (bits) {
-                            const int b = __ffs(bits) - 1;
-                            bits &= bits - 1;
-                            const int p = (wb + l) * 32 + b;
-                            if (p <= covered) continue;
-                            const long long K = proj(XY(order[p]), dy, dx);
-                            int lo = p, hi = p;
-                            while (lo > 0 && proj(XY(order[lo - 1]), dy, dx) == K) --lo;
-                            while (hi + 1 < n && proj(XY(order[hi + 1]), dy, dx) == K) ++hi;
-                            covered = hi;
-                            // just-after order inside the run: x descending, then index
-                            for (int u = lo + 1; u <= hi; ++u) {
-                                const unsigned short v = order[u];
-                                const int xv = px(XY(v));
-                                int t = u - 1;
-                                while (t >= lo) {
-                                    const unsigned short o = order[t];
-                                    const int xo = px(XY(o));
-                                    if (xo > xv || (xo == xv && o < v)) break;
-                                    order[t + 1] = o;
-                                    --t;
-                                }
-                                order[t + 1] = v;
-                            }
-                            for (int u = lo; u <= hi; ++u) pos[order[u]] = (unsigned short)u;
-                            if (lo + h - 1 < n) {
-                                const long long kb = proj(XY(order[lo]), dy, dx);
-                                const long long kt = proj(XY(order[lo + h - 1]), dy, dx);
-                                offer(kt - kb, kb + kt, dy, dx, gi, gj);
-                            }
-                            if (hi - h + 1 >= 0) {
-                                const long long kb = proj(XY(order[hi - h + 1]), dy, dx);
-                                const long long kt = proj(XY(order[hi]), dy, dx);
-                                offer(kt - kb, kb + kt, dy, dx, gi, gj);
-                            }
-                        }
-                        bm[wb + l] = 0u;
+            const int dx = px(Pb) - px(Pa), dy = py(Pb) - py(Pa);
+            const int pa = valid ? pos[a] : 0, pb = valid ? pos[b] : 0;
+            const bool done = valid && pb < pa;
+            const long long K = proj(Pa, dy, dx);
+            int lo = pa, hi = pb;
+            bool simple = false, run = false, longrun = false, interior_bad = false;
+            if (valid && !done) {
+                const bool lo_eq = pa > 0 && proj(XY(order[pa - 1]), dy, dx) == K;
+                const bool hi_eq = pb < n - 1 && proj(XY(order[pb + 1]), dy, dx) == K;
+                if (pb == pa + 1 && !lo_eq && !hi_eq) {
+                    simple = true;
+                } else {
+                    run = true;
+                    if (lo_eq) {
+                        --lo;
+                        while (lo > 0 && hi - lo < RUN_LANE_MAX && proj(XY(order[lo - 1]), dy, dx) == K) --lo;
                     }
-                    __syncwarp();
+                    if (hi_eq) {
+                        ++hi;
+                        while (hi < n - 1 && hi - lo < RUN_LANE_MAX && proj(XY(order[hi + 1]), dy, dx) == K) ++hi;
+                    }
+                    longrun = hi - lo >= RUN_LANE_MAX;
+                    // the two points must sit inside one run; if an earlier lane of
+                    // this batch is still to move a point in between, the lane waits
+                    for (int q = pa + 1; q < pb && !longrun; ++q)
+                        if (proj(XY(order[q]), dy, dx) != K) { interior_bad = true; break; }
                 }
             }
-        };
-        unsigned k = start;
-        while (k < end) {
-            const unsigned idx = k + lane;
-            const unsigned e = idx < end ? ev[idx] : 0u;
-            const unsigned cmask = __ballot_sync(FULL, idx < end && ev_cont(e));
-            const unsigned cnt = min(32u, end - k);
-            const bool tail_cont = (k + 32 < end) ? ev_cont(ev[k + 32]) : false;
-            unsigned t = 0;
-            bool jumped = false;
-            while (t < cnt) {
-                const bool next_cont = (t + 1 < 32) ? ((cmask >> (t + 1)) & 1u) : tail_cont;
-                if (!next_cont) {
-                    const unsigned et = __shfl_sync(FULL, e, t);
-                    int ok = 1;
-                    if (lane == 0) {
-                        const int u = ev_i(et), v = ev_j(et);
-                        const int pu = pos[u], pv = pos[v];
-                        if (pu - pv == 1 || pv - pu == 1) {
-                            const int Pu = XY(u), Pv = XY(v);
-                            int dy, dx;
-                            pair_slope(Pu, Pv, dy, dx);
-                            const int lo = min(pu, pv);
-                            if (px(Pu) > px(Pv)) {
-                                order[lo] = (unsigned short)u; order[lo + 1] = (unsigned short)v;
-                                pos[u] = (unsigned short)lo; pos[v] = (unsigned short)(lo + 1);
-                            } else {
-                                order[lo] = (unsigned short)v; order[lo + 1] = (unsigned short)u;
-                                pos[v] = (unsigned short)lo; pos[u] = (unsigned short)(lo + 1);
-                            }
-                            const long long K = proj(Pu, dy, dx);
-                            if (lo + h - 1 < n) {
-                                const long long kt = proj(XY(order[lo + h - 1]), dy, dx);
-                                offer(kt - K, K + kt, dy, dx, u, v);
-                            }
-                            if (lo - h + 2 >= 0 && lo + 1 < n) {
-                                const long long kb = proj(XY(order[lo - h + 2]), dy, dx);
-                                offer(K - kb, kb + K, dy, dx, u, v);
-                            }
-                        } else {
-                            ok = 0;   // two points that meet must be neighbours
-                            atomicOr(err, 1);
+            // one leader per run: the lowest lane with the same group and run start
+            const unsigned runkey = run ? (((unsigned)lo << 12) | ((unsigned)min(hi - lo, 63) << 6) |
+                                           (unsigned)(gfirst + 1))
+                                        : (0x80000000u | (unsigned)lane);
+            const unsigned peers = __match_any_sync(FULL, runkey);
+            const bool leader = run && !longrun && lane == __ffs(peers) - 1;
+            const bool act = simple || leader;
+            // ---- conflicts with earlier active lanes of other groups
+            const unsigned me = act ? (((unsigned)lo << 16) | ((unsigned)(hi - lo) << 6) | (unsigned)(gfirst + 1)) : 0xffffffffu;
+            bool conflict = false;
+            {
+                const int top = lo + h - 1, bot = hi - h + 1;
+                for (int t = 0; t < 31; ++t) {
+                    const unsigned o = __shfl_sync(FULL, me, t);
+                    if (!act || t >= lane || o == 0xffffffffu || (o & 0x3fu) == (unsigned)(gfirst + 1)) continue;
+                    const int olo = (int)(o >> 16), ohi = olo + (int)((o >> 6) & 0x3ffu);
+                    if ((olo <= hi + 1 && ohi >= lo - 1) || (top >= olo && top <= ohi) || (bot >= olo && bot <= ohi))
+                        conflict = true;
+                }
+            }
+            const unsigned bad = __ballot_sync(FULL, longrun || interior_bad || conflict);
+            const int cut = bad ? __ffs(bad) - 1 : (int)navail;
+            int advance;
+            if (cut > 0) {
+                // ---- parallel events: window reads, then the rewrites
+                const bool go = act && lane < cut;
+                long long kt = K, kb = K;
+                const int top = lo + h - 1, bot = hi - h + 1;
+                if (go) {
+                    if (top < n && top > hi) kt = proj(XY(order[top]), dy, dx);
+                    if (bot >= 0 && bot < lo) kb = proj(XY(order[bot]), dy, dx);
+                }
+                __syncwarp();
+                if (go) {
+                    if (simple) {
+                        order[pa] = (unsigned short)b;
+                        order[pa + 1] = (unsigned short)a;
+                        pos[b] = (unsigned short)pa;
+                        pos[a] = (unsigned short)(pa + 1);
+                    } else {
+                        for (int u = lo, v = hi; u < v; ++u, --v) {
+                            const unsigned short ou = order[u], ov = order[v];
+                            order[u] = ov;
+                            order[v] = ou;
+                            pos[ov] = (unsigned short)u;
+                            pos[ou] = (unsigned short)v;
                         }
                     }
-                    ok = __shfl_sync(FULL, ok, 0);
-                    if (!ok) group(k + t, k + t + 1);
-                    __syncwarp();
-                    ++t;
-                } else {
-                    // group [k + t, g1): find its end
-                    unsigned g1 = k + t + 1;
-                    for (;;) {
-                        const unsigned q = g1 + lane;
-                        const bool c = q < end && ev_cont(ev[q]);
-                        const unsigned bal = __ballot_sync(FULL, c);
-                        if (bal == FULL) { g1 += 32; continue; }
-                        g1 += __ffs(~bal) - 1;
-                        break;
-                    }
-                    group(k + t, g1);
-                    k = g1;
-                    jumped = true;
+                    if (top < n) offer(kt - K, K + kt, dy, dx, gmin);
+                    if (bot >= 0) offer(K - kb, kb + K, dy, dx, gmin);
+                }
+                __syncwarp();
+                advance = cut;
+            } else {
+                // ---- lane 0 holds a long run (or one to verify): the warp reverses it
+                const int ra = __shfl_sync(FULL, pa, 0), rb = __shfl_sync(FULL, pb, 0);
+                const int rdy = __shfl_sync(FULL, dy, 0), rdx = __shfl_sync(FULL, dx, 0);
+                const long long RK = __shfl_sync(FULL, K, 0);
+                const unsigned rmin = __shfl_sync(FULL, gmin, 0);
+                int rlo = min(ra, rb), rhi = max(ra, rb);
+                for (;;) {
+                    const int q = rlo - 1 - lane;
+                    const bool eq = q >= 0 && proj(XY(order[q]), rdy, rdx) == RK;
+                    const unsigned bal = __ballot_sync(FULL, eq);
+                    if (bal == FULL) { rlo -= 32; continue; }
+                    rlo -= __ffs(~bal) - 1;
                     break;
                 }
+                for (;;) {
+                    const int q = rhi + 1 + lane;
+                    const bool eq = q < n && proj(XY(order[q]), rdy, rdx) == RK;
+                    const unsigned bal = __ballot_sync(FULL, eq);
+                    if (bal == FULL) { rhi += 32; continue; }
+                    rhi += __ffs(~bal) - 1;
+                    break;
+                }
+                bool broken = false;
+                for (int q = rlo + lane; q <= rhi; q += 32)
+                    if (proj(XY(order[q]), rdy, rdx) != RK) broken = true;
+                if (__any_sync(FULL, broken) && lane == 0) atomicOr(err, 2);
+                const int len = rhi - rlo + 1;
+                for (int t = lane; t < len / 2; t += 32) {
+                    const unsigned short u = order[rlo + t], v = order[rhi - t];
+                    order[rlo + t] = v;
+                    order[rhi - t] = u;
+                }
+                __syncwarp();
+                for (int t = lane; t < len; t += 32) pos[order[rlo + t]] = (unsigned short)(rlo + t);
+                __syncwarp();
+                if (lane == 0) {
+                    if (rlo + h - 1 < n) {
+                        const long long t2 = proj(XY(order[rlo + h - 1]), rdy, rdx);
+                        offer(t2 - RK, RK + t2, rdy, rdx, rmin);
+                    }
+                    if (rhi - h + 1 >= 0) {
+                        const long long b2 = proj(XY(order[rhi - h + 1]), rdy, rdx);
+                        offer(RK - b2, b2 + RK, rdy, rdx, rmin);
+                    }
+                }
+                __syncwarp();
+                advance = 1;
             }
-            if (!jumped) k += cnt;
+            carried = __shfl_sync(FULL, gmin, advance - 1);
+            // slide the 64-event window by `advance`
+            const int src = (lane + advance) & 31;
+            const unsigned c1 = __shfl_sync(FULL, e_cur, src);
+            const unsigned c2 = __shfl_sync(FULL, e_nxt, src);
+            const bool from_cur = lane + advance < 32;
+            k += advance;
+            e_cur = from_cur ? c1 : c2;
+            const unsigned q = k + 32 + lane;
+            e_nxt = from_cur ? c2 : ((q < end) ? ev[q] : 0u);
         }
     }
+    best = warp_best(best);
     if (lane == 0) cands[W + w] = best;
 }
 
@@ -745,7 +839,7 @@ void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int w
     p.emax = (long long)n * (n - 1) / 2;
     p.xy_smem = n <= 16384;
     // sweepers per CTA limited by shared memory (order + pos + bitmap each)
-    const size_t per = 2 * ((size_t)n * 2 + 15) / 16 * 16 + ((size_t)(n + 31) / 32 * 4 + 15) / 16 * 16;
+    const size_t per = 2 * (((size_t)n * 2 + 15) / 16 * 16);
     const size_t xyb = p.xy_smem ? ((size_t)n * 4 + 15) / 16 * 16 : 0;
     const size_t cap = 227 * 1024;
     int spb = (int)((cap - xyb) / per);
@@ -814,43 +908,47 @@ void sweep_plan_carve(SweepPlan &p, void *ws)
 cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cudaStream_t st)
 {
     const int n = p.n;
-    k_pack<<<(n + 255) / 256, 256, 0, st>>>(x, y, n, p.xy);
-    k_sample<<<(p.S + 255) / 256, 256, 0, st>>>(p.xy, n, p.emax, p.S, p.skeys);
-    k_sort_chunks<<<p.S / SORT_CHUNK, SORT_CHUNK / 2, 0, st>>>(p.skeys);
+    { StageTimer _t(STAGE_PACK, st); k_pack<<<(n + 255) / 256, 256, 0, st>>>(x, y, n, p.xy); }
+    { StageTimer _t(STAGE_SAMPLE, st); k_sample<<<(p.S + 255) / 256, 256, 0, st>>>(p.xy, n, p.emax, p.S, p.skeys); }
+    { StageTimer _t(STAGE_SAMPLE_SORT, st); k_sort_chunks<<<p.S / SORT_CHUNK, SORT_CHUNK / 2, 0, st>>>(p.skeys); }
     long long *src = p.skeys, *dst = p.skeys2;
     for (int width = SORT_CHUNK; width < p.S; width <<= 1) {
-        k_merge_runs<<<(p.S + 255) / 256, 256, 0, st>>>(src, dst, p.S, width);
+        { StageTimer _t(STAGE_SAMPLE_SORT, st); k_merge_runs<<<(p.S + 255) / 256, 256, 0, st>>>(src, dst, p.S, width); }
         long long *t = src; src = dst; dst = t;
     }
-    k_splitters<<<1, 1024, 0, st>>>(src, p.S, p.B, p.bnd, p.meta);
+    { StageTimer _t(STAGE_SPLITTERS, st); k_splitters<<<1, 1024, 0, st>>>(src, p.S, p.B, p.bnd, p.meta); }
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
     cudaFuncSetAttribute(k_bucket_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
     cudaFuncSetAttribute(k_bucket_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    k_bucket_pairs<false><<<p.C, CNT_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.meta, p.hist, nullptr, nullptr);
-    k_bucket_prefix<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.hist, p.C, p.meta, p.base);
-    k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta);
-    k_bucket_pairs<true><<<p.C, CNT_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.meta, p.hist, p.base, p.ev);
+    { StageTimer _t(STAGE_COUNT_PAIRS, st); k_bucket_pairs<false><<<p.C, CNT_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.meta, p.hist, nullptr, nullptr); }
+    { StageTimer _t(STAGE_PREFIX, st); k_bucket_prefix<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.hist, p.C, p.meta, p.base); }
+    { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta); }
+    { StageTimer _t(STAGE_SCATTER, st); k_bucket_pairs<true><<<p.C, CNT_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.meta, p.hist, p.base, p.ev); }
     const size_t seg_smem = (size_t)SEG_CAP * 12;
     cudaFuncSetAttribute(k_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
-    k_segsort<<<p.C, 1024, seg_smem, st>>>(p.xy, p.ev, p.base, p.bnd, p.meta, p.oversize);
-    k_segsort_big<<<p.C, 1024, 0, st>>>(p.xy, p.ev, p.base, p.meta, p.oversize);
-    k_plan<<<(p.W + 255) / 256, 256, 0, st>>>(p.base, p.meta, p.W, p.range);
+    { StageTimer _t(STAGE_SEGSORT, st); k_segsort<<<p.C, 1024, seg_smem, st>>>(p.xy, p.ev, p.base, p.bnd, p.meta, p.oversize); }
+    { StageTimer _t(STAGE_SEGSORT_BIG, st); k_segsort_big<<<p.C, 1024, 0, st>>>(p.xy, p.ev, p.base, p.meta, p.oversize); }
+    { StageTimer _t(STAGE_PLAN, st); k_plan<<<(p.W + 255) / 256, 256, 0, st>>>(p.base, p.meta, p.W, p.range); }
     int P = 1;
     while (P < n) P <<= 1;
     const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)P * 8 : 0;
     cudaFuncSetAttribute(k_sweep_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)init_smem);
-    k_sweep_init<<<p.W, 1024, init_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.meta, p.base, p.orders,
-                                              p.gsort, p.cands);
-    const int nwords = (n + 31) / 32;
-    const size_t per = 2 * (((size_t)n * 2 + 15) / 16 * 16) + ((size_t)nwords * 4 + 15) / 16 * 16;
+    {
+        StageTimer _t(STAGE_INIT, st);
+        k_sweep_init<<<p.W, 1024, init_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.meta, p.base, p.orders,
+                                                  p.gsort, p.cands);
+    }
+    const size_t per = 2 * (((size_t)n * 2 + 15) / 16 * 16);
     const size_t xyb = p.xy_smem ? ((size_t)n * 4 + 15) / 16 * 16 : 0;
     const size_t sw_smem = xyb + per * p.spb;
     const int blocks = (p.W + p.spb - 1) / p.spb;
     if (p.xy_smem) {
         cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
+        StageTimer _t(STAGE_SWEEP, st);
         k_sweep<true><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta + 3);
     } else {
         cudaFuncSetAttribute(k_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
+        StageTimer _t(STAGE_SWEEP, st);
         k_sweep<false><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta + 3);
     }
     return cudaGetLastError();

@@ -183,3 +183,35 @@ def exact_fields(r: dict):
     """The fields compared bit for bit against the oracle."""
     return (r["status"], r["w_num"], r["w_den"], r["s_num"], r["s_den"], r["t_num"], r["t_den"],
             r["i"], r["j"])
+
+
+# ------------------------------------------------------------------ profiling
+def _prof_sigs():
+    L = lib()
+    if not getattr(L, "_prof_ready", False):
+        L.lms_profile_enable.argtypes = [ctypes.c_int]
+        L.lms_profile_enable.restype = None
+        L.lms_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.lms_profile_read.restype = ctypes.c_int
+        L.lms_stage_name.argtypes = [ctypes.c_int]
+        L.lms_stage_name.restype = ctypes.c_char_p
+        L.lms_launch_count.restype = ctypes.c_int64
+        L._prof_ready = True
+    return L
+
+
+def profile_enable(on: bool = True) -> None:
+    _prof_sigs().lms_profile_enable(1 if on else 0)
+
+
+def profile_read() -> dict:
+    """{stage name: (milliseconds, launches)} accumulated since the last read."""
+    L = _prof_sigs()
+    ms = np.zeros(64, dtype=np.float64)
+    cnt = np.zeros(64, dtype=np.int64)
+    ns = L.lms_profile_read(ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(cnt.ctypes.data), 64)
+    return {L.lms_stage_name(s).decode(): (float(ms[s]), int(cnt[s])) for s in range(ns) if cnt[s]}
+
+
+def launch_count() -> int:
+    return int(_prof_sigs().lms_launch_count())

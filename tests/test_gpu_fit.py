@@ -30,11 +30,25 @@ def gpu_fit(L, x, y, h=0, algorithm="auto", **kw):
     return L.decode(out)[0]
 
 
+FIELDS = ("status", "w_num", "w_den", "s_num", "s_den", "t_num", "t_den", "i", "j",
+          "theta1", "theta2", "med_sq")
+
+
+class Diff:
+    """Truthy when the GPU record equals the oracle's; repr lists the differences."""
+
+    def __init__(self, r, o):
+        self.d = {k: (r[k], getattr(o, k)) for k in FIELDS if r[k] != getattr(o, k)}
+
+    def __bool__(self):
+        return not self.d
+
+    def __repr__(self):
+        return "differs (gpu, oracle): " + repr(self.d)
+
+
 def same(r, o):
-    return (r["status"], r["w_num"], r["w_den"], r["s_num"], r["s_den"], r["t_num"], r["t_den"],
-            r["i"], r["j"], r["theta1"], r["theta2"], r["med_sq"]) == (
-        o.status, o.w_num, o.w_den, o.s_num, o.s_den, o.t_num, o.t_den, o.i, o.j,
-        o.theta1, o.theta2, o.med_sq)
+    return Diff(r, o)
 
 
 def _degenerate(rng, n):
