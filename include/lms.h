@@ -56,7 +56,8 @@ enum lms_status {
     LMS_ERR_CUDA = 5,         /* a CUDA runtime call failed */
     LMS_ERR_WORKSPACE = 6,    /* installed workspace too small (or growth needed during capture) */
     LMS_ERR_UNSUPPORTED = 7,  /* combination not implemented (e.g. plain algorithm with n > 1024) */
-    LMS_ERR_INTERNAL = 8      /* a device-side consistency check failed (reported, never silent) */
+    LMS_ERR_INTERNAL = 8,     /* a device-side consistency check failed (reported, never silent) */
+    LMS_ERR_TOO_LARGE = 9     /* n above the fixed capacity of lms_fit_noalloc */
 };
 
 enum lms_dtype {
@@ -136,6 +137,37 @@ LMS_API void lms_profile_enable(int on);
 LMS_API int lms_profile_read(double *ms, int64_t *launches, int max_stages);
 LMS_API const char *lms_stage_name(int stage);
 LMS_API int64_t lms_launch_count(void);
+
+/*
+ * lms_fit_noalloc -- the plain fit (every pairwise slope, sort, window scan)
+ * for callers that cannot have the library allocate device memory.  The
+ * paper has no counterpart; it is an interface convenience.
+ *
+ * Who needs it: code that enqueues work while a stream is being captured
+ * into a CUDA graph (an allocation there invalidates the capture), real-time
+ * or embedded loops that forbid allocation once running, and frameworks
+ * that hand out all device memory from their own pools.  lms_fit may grow an
+ * internal workspace with cudaMalloc; this call never allocates or frees.
+ *
+ *   x, y    device arrays of n int16 coordinates.
+ *   n       2 <= n <= LMS_NOALLOC_MAX_N; larger n returns LMS_ERR_TOO_LARGE.
+ *   h       order statistic in [1, n]; 0 selects floor(n/2) + 1.
+ *   out     device pointer to one lms_result (same result as lms_fit with
+ *           LMS_ALGO_PLAIN, bit for bit).
+ * Asynchronous on `stream`.
+ *
+ * Its only scratch is a fixed array of LMS_NOALLOC_MAX_WARPS * 32 bytes
+ * (256 KiB) compiled into the library, present on every GPU that loads the
+ * library until the process exits.  All calls share that array: calls whose
+ * GPU work overlaps (other streams, other host threads) race and must not be
+ * issued.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.
+ */
+#define LMS_NOALLOC_MAX_N 1024
+#define LMS_NOALLOC_MAX_WARPS 8192
+LMS_API int lms_fit_noalloc(const void *x, const void *y, int64_t n, int64_t h, lms_result *out,
+                            lms_stream_t stream);
 
 /* Human-readable name of a status code (static string). */
 LMS_API const char *lms_status_str(int status);

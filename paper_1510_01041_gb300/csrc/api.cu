@@ -253,6 +253,7 @@ const char *lms_status_str(int status)
         case LMS_ERR_WORKSPACE: return "workspace too small";
         case LMS_ERR_UNSUPPORTED: return "unsupported combination";
         case LMS_ERR_INTERNAL: return "device consistency check failed";
+        case LMS_ERR_TOO_LARGE: return "n above the capacity of the no-allocation entry point";
         default: return "unknown status";
     }
 }

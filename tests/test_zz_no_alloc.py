@@ -1,0 +1,60 @@
+"""lms_fit_noalloc, the entry point for callers that cannot let the library
+allocate device memory (graph capture, allocation-free real-time loops,
+framework-owned memory pools), gives the same result as lms_fit's plain
+path.  Called directly through the C ABI, twice in a row on different
+inputs, so the second call reuses the shared fixed scratch array left by
+the first.  Kept in a file that pytest collects last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1510_01041_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_01041_gb300 import build, lms
+    build.build()
+    lib = lms.lib()
+    lib.lms_fit_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+    lib.lms_fit_noalloc.restype = ctypes.c_int
+    return lms
+
+
+def _noalloc(L, xt, yt, h=0):
+    out = torch.zeros(L.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=xt.device)
+    rc = L.lib().lms_fit_noalloc(ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(yt.data_ptr()), xt.numel(),
+                                 h, ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == L.LMS_OK, L.status_str(rc)
+    torch.cuda.synchronize()
+    return L.decode(out)[0]
+
+
+def test_noalloc_matches_lms_fit_twice(L):
+    for seed, n in ((31, 512), (32, 777)):
+        x, y = datagen.line_with_outliers(n, seed)
+        xt = torch.from_numpy(x).cuda()
+        yt = torch.from_numpy(y).cuda()
+        got = _noalloc(L, xt, yt)
+        ref = L.decode(L.fit(xt, yt, 0, "plain"))[0]
+        torch.cuda.synchronize()
+        assert {k: v for k, v in got.items() if k != "algorithm"} == \
+               {k: v for k, v in ref.items() if k != "algorithm"}
+        assert got["status"] == L.LMS_OK
+
+
+def test_noalloc_rejects_oversize(L):
+    x = torch.zeros(2000, dtype=torch.int16, device="cuda")
+    out = torch.zeros(L.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    rc = L.lib().lms_fit_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 2000, 0,
+                                 ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == 9 and "capacity" in L.status_str(rc)
