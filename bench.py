@@ -2,8 +2,12 @@
 """Benchmark of the exact 2D LMS line estimator on the GB300.
 
 Workload (one "step"): one exact LMS fit of n = 8192 int16 points, 40%
-outliers (y = round(0.7 x + 100) + U{-3..3} inliers, uniform outliers), all
-n(n-1)/2 = 33,550,336 candidate slopes, through the C ABI.  Every step uses a
+outliers (y = round(0.7 x + 100) + U{-3..3} inliers, uniform outliers), over
+all n(n-1)/2 = 33,550,336 candidate slopes, through the C ABI.  The headline
+path is the learned-seeded exact branch-and-bound (lms_fit_learned: the set
+network predicts the slope, bounds drop slope intervals, the rest is swept);
+the plain kinetic sweep over every candidate slope (lms_fit) is timed the
+same way beside it.  Both are bit-identical to the oracle.  Every step uses a
 fresh seeded instance already resident in HBM; L2 is flushed (256 MB write)
 before each step, outside the timed events.
 
@@ -28,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 N_POINTS = 8192
 OUTLIER_FRAC = 0.4
-METRIC = "exact LMS solves/sec at n=8192 (candidate slopes/sec alongside)"
+METRIC = "exact LMS solves/sec at n=8192, learned-seeded branch-and-bound (plain sweep alongside)"
 UNIT = "solves/s"
 # Algorithmic work of the sweep kernel per event (one pair of points meeting):
 # 2 position reads, 4 order/position writes, 3 projections (2 IMAD each),
@@ -143,13 +147,27 @@ def _cpu_baseline(x, y):
             "sample": f"1 full O2 solve at n={N_POINTS} ({dt:.1f} s)"}, r
 
 
+def _timed(fit, steps, warmup, flush, stream, barrier):
+    """Per-step CUDA-event device time of `fit(k)` for steps warmup..warmup+steps-1."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    for k in range(steps):
+        s = warmup + k
+        flush.fill_(s & 0xff)
+        ev[k][0].record(stream)
+        fit(s)
+        ev[k][1].record(stream)
+    barrier()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--algorithm", default="sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="per-stage times to stderr")
     args = ap.parse_args()
@@ -175,10 +193,12 @@ def main():
     host = [datagen.line_with_outliers(N_POINTS, s) for s in seeds]
     xs = [torch.from_numpy(h[0]).to(dev) for h in host]
     ys = [torch.from_numpy(h[1]).to(dev) for h in host]
-    out = torch.empty((total, lms.RESULT_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    out_l = torch.empty((total, lms.RESULT_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    out_p = torch.empty((total, lms.RESULT_DTYPE.itemsize), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    lms.reserve(N_POINTS, algorithm=args.algorithm)
+    lms.reserve(N_POINTS, algorithm="bnb")
+    net = lms.pretrained()
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -187,83 +207,103 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    def max_over_ranks(v):
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([v], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return v
+
+    learned_stats = []
+
+    def fit_learned(s):
+        learned_stats.append(net.fit(xs[s], ys[s], 0, out=out_l[s])[1])
+
+    def fit_plain(s):
+        lms.fit(xs[s], ys[s], 0, "sweep", out=out_p[s])
+
     for s in range(args.warmup):
         flush.fill_(s & 0xff)
-        lms.fit(xs[s], ys[s], 0, args.algorithm, out=out[s])
+        fit_learned(s)
+        fit_plain(s)
     barrier()
+    learned_stats.clear()
     launches0 = lms.launch_count()
     lms.profile_read()
     lms.profile_enable(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
-        barrier()
         wall0 = time.perf_counter()
-        for k in range(args.steps):
-            s = args.warmup + k
-            flush.fill_(s & 0xff)
-            ev[k][0].record(stream)
-            lms.fit(xs[s], ys[s], 0, args.algorithm, out=out[s])
-            ev[k][1].record(stream)
-        barrier()
+        learned_ms = _timed(fit_learned, args.steps, args.warmup, flush, stream, barrier)
         wall = time.perf_counter() - wall0
+        launches = lms.launch_count() - launches0
+        stages_l = lms.profile_read()
+        plain_ms = _timed(fit_plain, args.steps, args.warmup, flush, stream, barrier)
+        stages_p = lms.profile_read()
     lms.profile_enable(False)
-    stages = lms.profile_read()
-    launches = lms.launch_count() - launches0
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
-    res = lms.decode(out)
-    bad = [r for r in res[args.warmup:] if r["status"] != lms.LMS_OK]
-    if bad:
-        raise SystemExit(f"fit failed: {bad[0]}")
+    learned_ms = max_over_ranks(learned_ms)
+    plain_ms = max_over_ranks(plain_ms)
+    res_l = lms.decode(out_l)[args.warmup:]
+    res_p = lms.decode(out_p)[args.warmup:]
+    keys = ("status", "w_num", "w_den", "s_num", "s_den", "t_num", "t_den", "i", "j", "theta1", "theta2", "med_sq")
+    for a, b in zip(res_l, res_p):
+        if a["status"] != lms.LMS_OK or tuple(a[k] for k in keys) != tuple(b[k] for k in keys):
+            raise SystemExit(f"learned and plain fits disagree: {a} {b}")
 
-    # end to end: host buffers (pinned), copies inside the timed region
+    # end to end through the public API with host buffers (pinned), copies inside
     pin_x = [torch.from_numpy(h[0]).pin_memory() for h in host]
     pin_y = [torch.from_numpy(h[1]).pin_memory() for h in host]
+    dres = torch.empty(lms.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    hres = torch.empty(lms.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    dx = torch.empty(N_POINTS, dtype=torch.int16, device=dev)
+    dy = torch.empty(N_POINTS, dtype=torch.int16, device=dev)
     barrier()
     t0 = time.perf_counter()
     for k in range(args.steps):
         s = args.warmup + k
-        r = lms.fit_host(pin_x[s].numpy(), pin_y[s].numpy(), 0, args.algorithm)
-        assert r["status"] == lms.LMS_OK
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        dx.copy_(pin_x[s], non_blocking=True)
+        dy.copy_(pin_y[s], non_blocking=True)
+        net.fit(dx, dy, 0, out=dres)
+        hres.copy_(dres, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        assert lms.decode(hres)[0]["status"] == lms.LMS_OK
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
 
     slopes = N_POINTS * (N_POINTS - 1) // 2
     solves = ws * args.steps
-    value = solves / (dev_ms / 1000.0)
+    value = solves / (learned_ms / 1000.0)
+    plain_value = solves / (plain_ms / 1000.0)
     csum = clk.summary()
-    # roofline of the dominant kernel (the sweep): exact events per launch
-    # = candidate pairs with distinct x, measured per instance on the host
+    mhz = csum.get("sm_mhz") or 1462.0
+    int_peak = props.multi_processor_count * INT_LANES_PER_SM * mhz * 1e6 / 1e12
+    # roofline of the plain path's dominant kernel, the sweep: exact events per
+    # launch = pairs with distinct x, counted per instance on the host
     events = [int(np.sum(np.triu(np.not_equal.outer(h[0], h[0]), 1))) for h in host[args.warmup:]]
-    sweep_ms, sweep_launches = stages.get("sweep", (0.0, 0))
+    sweep_ms, sweep_launches = stages_p.get("sweep", (0.0, 0))
     roof = None
     if sweep_launches:
         per_launch_s = sweep_ms / sweep_launches / 1000.0
         ev_per_launch = sum(events) / len(events)
         achieved = SWEEP_INT_OPS_PER_EVENT * ev_per_launch / per_launch_s / 1e12
-        mhz = csum.get("sm_mhz") or 1462.0
-        peak = props.multi_processor_count * INT_LANES_PER_SM * mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_sweep",
+        roof = {"bound": "alu", "achieved": achieved, "peak": int_peak, "unit": "Tops/s (int32)",
+                "frac": achieved / int_peak, "traffic": None, "kernel": "k_sweep (plain path)",
                 "kernel_ms": per_launch_s * 1e3, "events_per_launch": ev_per_launch,
+                "ops_per_event": SWEEP_INT_OPS_PER_EVENT,
                 "peak_basis": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int32 lanes x "
-                              f"median SM clock {mhz:.0f} MHz under load"}
+                              f"median SM clock {mhz:.0f} MHz under load (derived, not measured)"}
+    mean = lambda k: float(np.mean([st[k] for st in learned_stats])) if learned_stats else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": learned_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "candidate_slopes_per_sec": value * slopes,
+        "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms / args.steps,
+                  "candidate_slopes_per_sec": plain_value * slopes, "algorithm": "kinetic sweep, every slope"},
+        "learned": {"events_swept_mean": mean("events_swept"), "events_total_mean": mean("events_total"),
+                    "nodes_evaluated_mean": mean("nodes_evaluated"), "upper_bound_mean": mean("upper_bound")},
         "config": {"workload": "single exact LMS fit, n=8192 int16, 40% outliers (line_with_outliers)",
-                   "n": N_POINTS, "h": N_POINTS // 2 + 1, "algorithm": args.algorithm,
+                   "n": N_POINTS, "h": N_POINTS // 2 + 1,
+                   "algorithm": "learned-seeded branch-and-bound + sweep of surviving slopes",
                    "l2": "flushed before every step (256 MB write, outside the timed events)",
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": solves / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 2 * N_POINTS,
@@ -271,18 +311,20 @@ def main():
         "gpu_launches": launches,
         "clocks": {k: csum.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "roofline": roof,
-        "stage_ms_per_step": {k: v[0] / args.steps for k, v in sorted(stages.items(), key=lambda kv: -kv[1][0])},
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in sorted(stages_l.items(), key=lambda kv: -kv[1][0])},
+        "plain_stage_ms_per_step": {k: v[0] / args.steps for k, v in sorted(stages_p.items(), key=lambda kv: -kv[1][0])},
         "wall_s": wall,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, o = _cpu_baseline(*host[args.warmup])
-        r = res[args.warmup]
+        r = res_l[0]
         cb["agrees_with_gpu"] = (r["w_num"], r["w_den"], r["s_num"], r["s_den"], r["t_num"], r["i"], r["j"]) == (
             o.w_num, o.w_den, o.s_num, o.s_den, o.t_num, o.i, o.j)
         line["cpu_baseline"] = cb
     if args.breakdown and rank == 0:
-        for k, v in sorted(stages.items(), key=lambda kv: -kv[1][0]):
-            print(f"  {k:14s} {v[0] / args.steps:9.3f} ms/step  launches {v[1]}", file=sys.stderr)
+        for name, st in (("learned", stages_l), ("plain", stages_p)):
+            for k, v in sorted(st.items(), key=lambda kv: -kv[1][0]):
+                print(f"  {name:8s} {k:14s} {v[0] / args.steps:9.3f} ms/step  launches {v[1]}", file=sys.stderr)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -76,7 +76,10 @@ typedef struct {
     int32_t algorithm;        /* enum lms_algo */
     int32_t sweepers;         /* kinetic-sweep workers per launch, 0 = auto */
     int32_t buckets;          /* slope buckets for event generation, 0 = auto */
-    int32_t reserved[5];      /* must be zero */
+    int32_t seed_mode;        /* branch-and-bound without a predicted slope: 0 = upper bound at
+                                 quantiles of sampled pairwise slopes, 1 = at evenly spaced
+                                 slope angles (no look at the data) */
+    int32_t reserved[4];      /* must be zero */
 } lms_options;
 
 /* Result of one fit: 88 bytes, same layout on host and device. */
@@ -111,6 +114,74 @@ LMS_API int lms_fit(const void *x, const void *y, int64_t n, int64_t h, int32_t 
  */
 LMS_API int lms_fit_host(const void *x, const void *y, int64_t n, int64_t h, int32_t dtype,
                  const lms_options *opt, lms_result *out, lms_stream_t stream);
+
+/* Branch-and-bound statistics (lms_fit_bnb). */
+typedef struct {
+    int64_t events_total;     /* pairs with distinct x: the candidate slopes */
+    int64_t events_swept;     /* pairs in slope buckets that survived the bounds */
+    int64_t nodes_evaluated;  /* slope intervals whose lower bound was computed */
+    int64_t nodes_pruned;     /* intervals dropped (lower bound > upper bound) */
+    int32_t buckets_total, buckets_swept;
+    int32_t levels;           /* bisection levels */
+    int32_t seeded;           /* 1 if a predicted slope chose the upper-bound slopes */
+    double upper_bound;       /* slab height bound used for pruning, -1 if none */
+} lms_bnb_stats;
+
+/*
+ * lms_fit_bnb -- exact LMS by branch-and-bound over slope intervals: an
+ * upper bound from the exact window width at a few slopes, a lower bound
+ * for every slope interval from the hulls of the projections over the
+ * interval, intervals with lower bound > upper bound dropped, and the
+ * surviving intervals swept exactly.  The result equals lms_fit's bit for
+ * bit (ties are never pruned).
+ *   seed_slope  device pointer to one float: a predicted slope; the upper
+ *               bound is taken at the sampled slopes nearest it.  NULL: at
+ *               evenly spaced sampled slopes instead.
+ *   stats       host pointer (may be NULL).
+ * Other arguments as lms_fit (int16 points, n <= 32768).  The call waits for
+ * the stream between bisection levels and returns after the fit is done.
+ */
+LMS_API int lms_fit_bnb(const void *x, const void *y, int64_t n, int64_t h, const float *seed_slope,
+                        const lms_options *opt, lms_result *out, lms_bnb_stats *stats, lms_stream_t stream);
+
+/*
+ * Learned slope proposal: a set network (per point 2 -> 64 -> 64 ReLU, max
+ * over the points, 64 -> 32 ReLU -> 2) that predicts the LMS line's slope
+ * angle and intercept in a normalised frame; BF16 weights, FP32
+ * accumulation, trained by its own forward/backward/Adam kernels.  Its
+ * prediction only chooses where branch-and-bound takes its upper bound; the
+ * answer stays exact.  Not in the paper (an extension of its method).
+ *
+ * Sets are given in CSR form: device int16 x[], y[] and device int64
+ * offsets[B + 1].  pred (device, B x 4 floats): angle, normalised intercept,
+ * slope, intercept.  targets (device, B x 2): angle and normalised intercept;
+ * the frame of a set is its bounding box: centre (cx, cy), scale = half the
+ * larger side, normalised intercept b = (theta2 - cy + theta1 * cx) / scale.
+ * Loss = mean over sets of (angle error)^2 + intercept_weight (b error)^2.
+ */
+typedef struct lms_setnet lms_setnet;
+LMS_API int lms_setnet_create(uint64_t seed, lms_setnet **net);   /* on the current device */
+LMS_API void lms_setnet_destroy(lms_setnet *net);
+LMS_API int64_t lms_setnet_param_count(void);
+/* copy the FP32 master weights to (set = 0) or from (set = 1) a host array */
+LMS_API int lms_setnet_params(lms_setnet *net, float *host, int64_t count, int32_t set);
+LMS_API int lms_setnet_forward(lms_setnet *net, const int16_t *x, const int16_t *y, const int64_t *offsets,
+                               int64_t B, float *pred, lms_stream_t stream);
+/* loss gradient of the current weights (grads: device, param_count floats; loss: device float) */
+LMS_API int lms_setnet_backward(lms_setnet *net, const int16_t *x, const int16_t *y, const int64_t *offsets,
+                                int64_t B, const float *targets, float intercept_weight, float *grads,
+                                float *loss, lms_stream_t stream);
+/* one Adam step (beta 0.9 / 0.999) on the loss of the batch */
+LMS_API int lms_setnet_train_step(lms_setnet *net, const int16_t *x, const int16_t *y, const int64_t *offsets,
+                                  int64_t B, const float *targets, float intercept_weight, float lr,
+                                  float *loss, lms_stream_t stream);
+/* checkpoint: weights and optimiser state (synchronous) */
+LMS_API int lms_setnet_save(const lms_setnet *net, const char *path);
+LMS_API int lms_setnet_load(lms_setnet *net, const char *path);
+/* the network predicts the slope of one set, branch-and-bound takes it as its seed */
+LMS_API int lms_fit_learned(lms_setnet *net, const void *x, const void *y, int64_t n, int64_t h,
+                            const lms_options *opt, lms_result *out, lms_bnb_stats *stats,
+                            lms_stream_t stream);
 
 /*
  * lms_workspace_size -- device bytes one lms_fit of this size needs.

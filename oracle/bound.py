@@ -1,0 +1,32 @@
+"""Branch-and-bound bound oracle (exact rationals, pure Python/numpy).
+
+TEST INFRASTRUCTURE ONLY.  For a slope interval [a, b] every projection
+z_k(s) = y_k - s x_k is linear in s, so it lies between
+lo_k = min(z_k(a), z_k(b)) and hi_k = max(z_k(a), z_k(b)) on the interval.
+Order statistics are monotone in each argument, so the m-th smallest
+projection at any s in [a, b] lies in [lo_(m), hi_(m)] (sorted separately),
+and the narrowest window of h projections is at least
+    LB = max(0, min over a' of lo_(a'+h-1) - hi_(a')).
+At a single slope (a = b) LB equals w(s) (Sec. 3.1: the slab height).
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+
+
+def lower_bound(xs, ys, h, a: Fraction, b: Fraction) -> Fraction:
+    lo, hi = [], []
+    for x, y in zip(xs, ys):
+        za, zb = Fraction(y) - a * x, Fraction(y) - b * x
+        lo.append(min(za, zb))
+        hi.append(max(za, zb))
+    lo.sort()
+    hi.sort()
+    n = len(lo)
+    m = min(lo[k + h - 1] - hi[k] for k in range(n - h + 1))
+    return max(Fraction(0), m)
+
+
+def width_at(xs, ys, h, s: Fraction) -> Fraction:
+    z = sorted(Fraction(y) - s * x for x, y in zip(xs, ys))
+    return min(z[k + h - 1] - z[k] for k in range(len(z) - h + 1))

@@ -78,7 +78,9 @@ struct Choice {
     int algo;
     SweepPlan sweep;
     int plain_warps;
+    int sms;
     size_t bytes;
+    size_t bnb_off;   // offset of the branch-and-bound scratch
 };
 
 int plain_warps_for(int n, int sms)
@@ -97,17 +99,22 @@ int choose(int n, int h, int dtype, const lms_options *opt, int dev, Choice &c)
     const int algo_req = opt ? opt->algorithm : LMS_ALGO_AUTO;
     int algo = algo_req;
     if (algo == LMS_ALGO_AUTO) algo = (n <= 256) ? LMS_ALGO_PLAIN : LMS_ALGO_SWEEP;
-    if (algo == LMS_ALGO_BNB) return LMS_ERR_UNSUPPORTED;
     const int sms = sm_count(dev);
     c.algo = algo;
+    c.sms = sms;
+    c.bnb_off = 0;
     if (algo == LMS_ALGO_PLAIN) {
         if (n > 1024) return LMS_ERR_UNSUPPORTED;
         c.plain_warps = plain_warps_for(n, sms);
         c.bytes = ((size_t)c.plain_warps * sizeof(Cand) + 255) / 256 * 256;
-    } else if (algo == LMS_ALGO_SWEEP) {
+    } else if (algo == LMS_ALGO_SWEEP || algo == LMS_ALGO_BNB) {
         if (n > 32768) return LMS_ERR_UNSUPPORTED;
         sweep_plan_configure(c.sweep, n, h, sms, opt ? opt->sweepers : 0, opt ? opt->buckets : 0);
         c.bytes = sweep_plan_bytes(n, c.sweep.W, c.sweep.C, c.sweep.S);
+        if (algo == LMS_ALGO_BNB) {
+            c.bnb_off = c.bytes;
+            c.bytes += bnb_extra_bytes(n, sms);
+        }
     } else {
         return LMS_ERR_ARG;
     }
@@ -126,7 +133,8 @@ int check_args(const void *x, const void *y, int64_t n, int64_t &h, int32_t dtyp
     if (opt) {
         if (opt->algorithm < LMS_ALGO_AUTO || opt->algorithm > LMS_ALGO_BNB) return LMS_ERR_ARG;
         if (opt->sweepers < 0 || opt->buckets < 0) return LMS_ERR_ARG;
-        for (int k = 0; k < 5; ++k)
+        if (opt->seed_mode < 0 || opt->seed_mode > 1) return LMS_ERR_ARG;
+        for (int k = 0; k < 4; ++k)
             if (opt->reserved[k]) return LMS_ERR_ARG;
     }
     if (dtype == LMS_F32) return LMS_ERR_UNSUPPORTED;
@@ -150,6 +158,9 @@ int run_fit(const void *x, const void *y, int n, int h, int dtype, const lms_opt
     }
     SweepPlan p = c.sweep;
     sweep_plan_carve(p, ws_in);
+    if (c.algo == LMS_ALGO_BNB)
+        return run_bnb(p, (const short *)x, (const short *)y, nullptr, opt ? opt->seed_mode : 0, out, nullptr,
+                       static_cast<unsigned char *>(ws_in) + c.bnb_off, c.sms, st);
     if (launch_sweep(p, (const short *)x, (const short *)y, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (launch_argmin(p.cands, 2 * p.W, out, LMS_ALGO_SWEEP, p.meta + 3, st) != cudaSuccess)
         return LMS_ERR_CUDA;
@@ -208,6 +219,29 @@ int lms_fit_host(const void *x, const void *y, int64_t n, int64_t h, int32_t dty
         return LMS_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
     return LMS_OK;
+}
+
+int lms_fit_bnb(const void *x, const void *y, int64_t n, int64_t h, const float *seed_slope,
+                const lms_options *opt, lms_result *out, lms_bnb_stats *stats, lms_stream_t stream)
+{
+    lms_options o = opt ? *opt : lms_options{};
+    o.algorithm = LMS_ALGO_BNB;
+    int rc = check_args(x, y, n, h, LMS_I16, &o, out);
+    if (rc) return rc;
+    int dev;
+    if (current_device(dev)) return LMS_ERR_CUDA;
+    Choice c;
+    rc = choose((int)n, (int)h, LMS_I16, &o, dev, c);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    rc = workspace(c.bytes, st, &ws);
+    if (rc) return rc;
+    SweepPlan p = c.sweep;
+    sweep_plan_carve(p, ws);
+    cudaGetLastError();
+    return run_bnb(p, (const short *)x, (const short *)y, seed_slope, o.seed_mode, out, stats,
+                   static_cast<unsigned char *>(ws) + c.bnb_off, c.sms, st);
 }
 
 size_t lms_workspace_size(int64_t n, int32_t dtype, const lms_options *opt)

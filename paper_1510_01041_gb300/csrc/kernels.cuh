@@ -69,6 +69,17 @@ size_t sweep_plan_bytes(int n, int W, int C, int S);
 void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int want_b);
 void sweep_plan_carve(SweepPlan &p, void *ws);
 cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cudaStream_t st);
+// the two halves of launch_sweep: bucket counts and starts (prepare), then
+// scatter of the kept buckets' events, bucket sorts and the sweep (finish)
+cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short *y, cudaStream_t st);
+// plan = false: the caller has written the sweeper ranges itself
+cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan);
+const long long *sorted_sample(const SweepPlan &p);
+
+// ---------------------------------------------------------------- branch and bound
+size_t bnb_extra_bytes(int n, int sms);
+int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pred_dev, int seed_mode, lms_result *out,
+            lms_bnb_stats *stats, void *extra, int sms, cudaStream_t st);
 
 // ---------------------------------------------------------------- argmin
 cudaError_t launch_argmin(const Cand *cands, int count, lms_result *out, int algorithm, const int *err,

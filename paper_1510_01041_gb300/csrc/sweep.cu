@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const int *__restr
                                                               const int *__restrict__ meta,
                                                               unsigned *__restrict__ hist,
                                                               const unsigned *__restrict__ base,
-                                                              unsigned *__restrict__ ev)
+                                                              unsigned *__restrict__ ev,
+                                                              const unsigned char *__restrict__ keep)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const int *__restr
             int dy, dx;
             if (!pair_slope(pi, s_tile[jl0 + jj], dy, dx)) continue;
             const int b = bucket_of(s_bnd, P2, slope_key(dy, dx));
+            if (SCATTER && keep && !keep[b]) continue;
             const unsigned slot = atomicAdd(&s_cnt[b], 1u);
             if (SCATTER) ev[slot] = ev_pack(i, j, false);
         }
@@ -905,7 +907,14 @@ void sweep_plan_carve(SweepPlan &p, void *ws)
     p.cands = (Cand *)take((size_t)2 * p.W * sizeof(Cand));
 }
 
-cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cudaStream_t st)
+const long long *sorted_sample(const SweepPlan &p)
+{
+    int rounds = 0;
+    for (int width = SORT_CHUNK; width < p.S; width <<= 1) ++rounds;
+    return (rounds & 1) ? p.skeys2 : p.skeys;
+}
+
+cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short *y, cudaStream_t st)
 {
     const int n = p.n;
     { StageTimer _t(STAGE_PACK, st); k_pack<<<(n + 255) / 256, 256, 0, st>>>(x, y, n, p.xy); }
@@ -919,16 +928,23 @@ cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cud
     { StageTimer _t(STAGE_SPLITTERS, st); k_splitters<<<1, 1024, 0, st>>>(src, p.S, p.B, p.bnd, p.meta); }
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
     cudaFuncSetAttribute(k_bucket_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    cudaFuncSetAttribute(k_bucket_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    { StageTimer _t(STAGE_COUNT_PAIRS, st); k_bucket_pairs<false><<<p.C, CNT_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.meta, p.hist, nullptr, nullptr); }
+    { StageTimer _t(STAGE_COUNT_PAIRS, st); k_bucket_pairs<false><<<p.C, CNT_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.meta, p.hist, nullptr, nullptr, nullptr); }
     { StageTimer _t(STAGE_PREFIX, st); k_bucket_prefix<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.hist, p.C, p.meta, p.base); }
     { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta); }
-    { StageTimer _t(STAGE_SCATTER, st); k_bucket_pairs<true><<<p.C, CNT_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.meta, p.hist, p.base, p.ev); }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan)
+{
+    const int n = p.n;
+    const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
+    cudaFuncSetAttribute(k_bucket_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
+    { StageTimer _t(STAGE_SCATTER, st); k_bucket_pairs<true><<<p.C, CNT_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep); }
     const size_t seg_smem = (size_t)SEG_CAP * 12;
     cudaFuncSetAttribute(k_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
     { StageTimer _t(STAGE_SEGSORT, st); k_segsort<<<p.C, 1024, seg_smem, st>>>(p.xy, p.ev, p.base, p.bnd, p.meta, p.oversize); }
     { StageTimer _t(STAGE_SEGSORT_BIG, st); k_segsort_big<<<p.C, 1024, 0, st>>>(p.xy, p.ev, p.base, p.meta, p.oversize); }
-    { StageTimer _t(STAGE_PLAN, st); k_plan<<<(p.W + 255) / 256, 256, 0, st>>>(p.base, p.meta, p.W, p.range); }
+    if (plan) { StageTimer _t(STAGE_PLAN, st); k_plan<<<(p.W + 255) / 256, 256, 0, st>>>(p.base, p.meta, p.W, p.range); }
     int P = 1;
     while (P < n) P <<= 1;
     const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)P * 8 : 0;
@@ -952,6 +968,13 @@ cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cud
         k_sweep<false><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta + 3);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cudaStream_t st)
+{
+    cudaError_t e = launch_sweep_prepare(p, x, y, st);
+    if (e != cudaSuccess) return e;
+    return launch_sweep_finish(p, nullptr, st, true);
 }
 
 }  // namespace lms

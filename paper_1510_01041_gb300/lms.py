@@ -28,7 +28,8 @@ assert RESULT_DTYPE.itemsize == 88
 
 class Options(ctypes.Structure):
     _fields_ = [("algorithm", ctypes.c_int32), ("sweepers", ctypes.c_int32),
-                ("buckets", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("buckets", ctypes.c_int32), ("seed_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class LmsError(RuntimeError):
@@ -80,11 +81,15 @@ def version() -> str:
     return lib().lms_version().decode()
 
 
-def options(algorithm: str = "auto", sweepers: int = 0, buckets: int = 0) -> Options:
+SEED_MODES = {"quantiles": 0, "angles": 1}
+
+
+def options(algorithm: str = "auto", sweepers: int = 0, buckets: int = 0, seed_mode: str = "quantiles") -> Options:
     o = Options()
     o.algorithm = ALGOS[algorithm]
     o.sweepers = int(sweepers)
     o.buckets = int(buckets)
+    o.seed_mode = SEED_MODES[seed_mode]
     return o
 
 
@@ -215,3 +220,179 @@ def profile_read() -> dict:
 
 def launch_count() -> int:
     return int(_prof_sigs().lms_launch_count())
+
+
+# ------------------------------------------------------------------ branch and bound
+class BnbStats(ctypes.Structure):
+    _fields_ = [("events_total", ctypes.c_int64), ("events_swept", ctypes.c_int64),
+                ("nodes_evaluated", ctypes.c_int64), ("nodes_pruned", ctypes.c_int64),
+                ("buckets_total", ctypes.c_int32), ("buckets_swept", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("seeded", ctypes.c_int32),
+                ("upper_bound", ctypes.c_double)]
+
+
+def fit_bnb(x, y, h: int = 0, seed=None, out=None, stream=None, sweepers: int = 0, buckets: int = 0,
+            seed_mode: str = "quantiles"):
+    """Exact LMS by branch-and-bound (lms_fit_bnb).  ``seed``: a CUDA float32
+    tensor holding a predicted slope, or None.  Returns (out, stats dict)."""
+    import torch
+    L = lib()
+    if not getattr(L, "_bnb_ready", False):
+        L.lms_fit_bnb.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_void_p, ctypes.POINTER(Options), ctypes.c_void_p,
+                                  ctypes.POINTER(BnbStats), ctypes.c_void_p]
+        L.lms_fit_bnb.restype = ctypes.c_int
+        L._bnb_ready = True
+    if x.dtype != torch.int16 or not x.is_cuda:
+        raise TypeError("fit_bnb takes int16 CUDA tensors")
+    x = x.contiguous()
+    y = y.contiguous()
+    if out is None:
+        out = torch.empty(RESULT_DTYPE.itemsize, dtype=torch.uint8, device=x.device)
+    st = BnbStats()
+    sp = ctypes.c_void_p(seed.data_ptr()) if seed is not None else ctypes.c_void_p(0)
+    opt = options("bnb", sweepers, buckets, seed_mode)
+    rc = L.lms_fit_bnb(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(), int(h), sp,
+                       ctypes.byref(opt), ctypes.c_void_p(out.data_ptr()), ctypes.byref(st),
+                       _stream_handle(stream))
+    if rc != LMS_OK:
+        raise LmsError(rc, "lms_fit_bnb")
+    return out, {f: getattr(st, f) for f, _ in BnbStats._fields_}
+
+
+# ------------------------------------------------------------------ learned slope proposal
+def _setnet_sigs():
+    L = lib()
+    if not getattr(L, "_setnet_ready", False):
+        vp, i64, f32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_float
+        L.lms_setnet_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]
+        L.lms_setnet_create.restype = ctypes.c_int
+        L.lms_setnet_destroy.argtypes = [vp]
+        L.lms_setnet_destroy.restype = None
+        L.lms_setnet_param_count.restype = ctypes.c_int64
+        L.lms_setnet_params.argtypes = [vp, vp, i64, ctypes.c_int32]
+        L.lms_setnet_params.restype = ctypes.c_int
+        L.lms_setnet_forward.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+        L.lms_setnet_forward.restype = ctypes.c_int
+        L.lms_setnet_backward.argtypes = [vp, vp, vp, vp, i64, vp, f32, vp, vp, vp]
+        L.lms_setnet_backward.restype = ctypes.c_int
+        L.lms_setnet_train_step.argtypes = [vp, vp, vp, vp, i64, vp, f32, f32, vp, vp]
+        L.lms_setnet_train_step.restype = ctypes.c_int
+        L.lms_setnet_save.argtypes = [vp, ctypes.c_char_p]
+        L.lms_setnet_save.restype = ctypes.c_int
+        L.lms_setnet_load.argtypes = [vp, ctypes.c_char_p]
+        L.lms_setnet_load.restype = ctypes.c_int
+        L.lms_fit_learned.argtypes = [vp, vp, vp, i64, i64, ctypes.POINTER(Options), vp,
+                                      ctypes.POINTER(BnbStats), vp]
+        L.lms_fit_learned.restype = ctypes.c_int
+        L._setnet_ready = True
+    return L
+
+
+class SetNet:
+    """Handle of the device set network (lms_setnet_*)."""
+
+    def __init__(self, seed: int = 1):
+        self.L = _setnet_sigs()
+        h = ctypes.c_void_p()
+        rc = self.L.lms_setnet_create(ctypes.c_uint64(seed), ctypes.byref(h))
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_setnet_create")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.L.lms_setnet_destroy(self.h)
+            self.h = None
+
+    @property
+    def nparam(self) -> int:
+        return int(self.L.lms_setnet_param_count())
+
+    def get_params(self):
+        a = np.zeros(self.nparam, dtype=np.float32)
+        rc = self.L.lms_setnet_params(self.h, ctypes.c_void_p(a.ctypes.data), a.size, 0)
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_setnet_params")
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        rc = self.L.lms_setnet_params(self.h, ctypes.c_void_p(a.ctypes.data), a.size, 1)
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_setnet_params")
+
+    def forward(self, x, y, offsets, stream=None):
+        """CUDA int16 x, y and int64 offsets[B+1] -> CUDA float32 [B, 4]
+        (angle, normalised intercept, slope, intercept)."""
+        import torch
+        B = offsets.numel() - 1
+        pred = torch.empty((B, 4), dtype=torch.float32, device=x.device)
+        rc = self.L.lms_setnet_forward(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                       ctypes.c_void_p(offsets.data_ptr()), B, ctypes.c_void_p(pred.data_ptr()),
+                                       _stream_handle(stream))
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_setnet_forward")
+        return pred
+
+    def backward(self, x, y, offsets, targets, lam: float, stream=None):
+        import torch
+        B = offsets.numel() - 1
+        g = torch.empty(self.nparam, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        rc = self.L.lms_setnet_backward(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                        ctypes.c_void_p(offsets.data_ptr()), B,
+                                        ctypes.c_void_p(targets.data_ptr()), float(lam),
+                                        ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                        _stream_handle(stream))
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_setnet_backward")
+        return loss, g
+
+    def train_step(self, x, y, offsets, targets, lam: float, lr: float, loss=None, stream=None):
+        import torch
+        B = offsets.numel() - 1
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        rc = self.L.lms_setnet_train_step(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                          ctypes.c_void_p(offsets.data_ptr()), B,
+                                          ctypes.c_void_p(targets.data_ptr()), float(lam), float(lr),
+                                          ctypes.c_void_p(loss.data_ptr()), _stream_handle(stream))
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_setnet_train_step")
+        return loss
+
+    def save(self, path: str):
+        rc = self.L.lms_setnet_save(self.h, path.encode())
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_setnet_save")
+
+    def load(self, path: str):
+        rc = self.L.lms_setnet_load(self.h, path.encode())
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_setnet_load")
+        return self
+
+    def fit(self, x, y, h: int = 0, out=None, stream=None):
+        """lms_fit_learned: predict the slope, then exact branch-and-bound."""
+        import torch
+        if out is None:
+            out = torch.empty(RESULT_DTYPE.itemsize, dtype=torch.uint8, device=x.device)
+        st = BnbStats()
+        opt = options("bnb")
+        rc = self.L.lms_fit_learned(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                    x.numel(), int(h), ctypes.byref(opt), ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.byref(st), _stream_handle(stream))
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_fit_learned")
+        return out, {f: getattr(st, f) for f, _ in BnbStats._fields_}
+
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "setnet.bin")
+
+
+def pretrained(path: str = WEIGHTS, seed: int = 1) -> SetNet:
+    """The set network with the weights trained by train_setnet.py."""
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path}: run python -m paper_1510_01041_gb300.train_setnet")
+    return SetNet(seed).load(path)

@@ -1,0 +1,42 @@
+"""The branch-and-bound lower bound is sound (never above the true narrowest
+window at any candidate slope inside the interval) and exact on a point
+interval; pinned by brute force over the candidate slopes (Sec. 3.1, 3.3)."""
+from fractions import Fraction
+
+import numpy as np
+
+from oracle import bound, tiny
+
+
+def test_bound_sound_and_tight():
+    rng = np.random.default_rng(3)
+    for trial in range(60):
+        n = int(rng.integers(4, 14))
+        xs = rng.integers(-50, 50, n).tolist()
+        ys = rng.integers(-50, 50, n).tolist()
+        h = n // 2 + 1
+        pts = list(zip(xs, ys))
+        S = tiny.candidate_slopes(pts)
+        if len(S) < 2:
+            continue
+        i, j = sorted(rng.choice(len(S), 2, replace=False).tolist())
+        a, b = S[i], S[j]
+        lb = bound.lower_bound(xs, ys, h, a, b)
+        inside = [s for s in S if a <= s <= b]
+        assert lb <= min(bound.width_at(xs, ys, h, s) for s in inside)
+        # and at any real slope of the interval
+        for t in (Fraction(1, 3), Fraction(1, 2), Fraction(5, 7)):
+            s = a + (b - a) * t
+            assert lb <= bound.width_at(xs, ys, h, s)
+        assert bound.lower_bound(xs, ys, h, a, a) == bound.width_at(xs, ys, h, a)
+
+
+def test_width_matches_subset_definition():
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        n = int(rng.integers(3, 8))
+        xs = rng.integers(-9, 9, n).tolist()
+        ys = rng.integers(-9, 9, n).tolist()
+        s = Fraction(int(rng.integers(-20, 20)), int(rng.integers(1, 7)))
+        h = n // 2 + 1
+        assert bound.width_at(xs, ys, h, s) == tiny.window_width_at(list(zip(xs, ys)), h, s)[0]
