@@ -599,6 +599,71 @@ __device__ __forceinline__ int load_xy(const int *s_xy, const int *__restrict__ 
 __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 constexpr int RUN_LANE_MAX = 24;   // runs up to this length are handled by one lane
+constexpr unsigned HEAVY_MIN = 64; // groups at least this long are processed whole
+constexpr unsigned short MARK = 0x8000, START = 0x4000, IDMASK = 0x3fff;
+
+// A whole group of equal slopes [g0, g1) at once (n <= 16384, so point
+// indices leave the two top bits of an order entry free).  Every position
+// holding a point of the group is marked; each maximal block of marked
+// positions with equal projections is a run (points on one line of the
+// group's slope); the lane that owns a run's first position reverses it and
+// re-scores the window starting at the run and the window ending at it.
+// Three passes separated by warp barriers: mark, flag run starts, reverse.
+// No pass writes what another lane of the same pass reads, except mark bits
+// that never change a point index or a projection.
+template <bool XY_SMEM>
+__device__ void heavy_group(unsigned short *order, unsigned short *pos, const int *s_xy,
+                            const int *__restrict__ g_xy, int n, int h, const unsigned *__restrict__ ev,
+                            unsigned g0, unsigned g1, int lane, Cand &best)
+{
+    auto XY = [&](int k) { return load_xy<XY_SMEM>(s_xy, g_xy, k); };
+    const unsigned e0 = ev[g0];
+    int dy, dx;
+    pair_slope(XY(ev_i(e0)), XY(ev_j(e0)), dy, dx);
+    const unsigned gmin = ((unsigned)ev_i(e0) << 16) | (unsigned)ev_j(e0);
+    for (unsigned q = g0 + lane; q < g1; q += 32) {
+        const unsigned e = ev[q];
+        order[pos[ev_i(e)]] |= MARK;
+        order[pos[ev_j(e)]] |= MARK;
+    }
+    __syncwarp();
+    const int chunk = (n + 31) / 32;
+    const int c0 = lane * chunk, c1 = min(n, c0 + chunk);
+    auto key_at = [&](int p) { return proj(XY(order[p] & IDMASK), dy, dx); };
+    for (int p = c0; p < c1; ++p) {
+        if (!(order[p] & MARK)) continue;
+        const long long K = key_at(p);
+        if (p > 0 && (order[p - 1] & MARK) && key_at(p - 1) == K) continue;
+        order[p] |= START;
+    }
+    __syncwarp();
+    for (int p = c0; p < c1; ++p) {
+        if (!(order[p] & START)) continue;
+        const long long K = key_at(p);
+        int q = p;
+        while (q + 1 < n && (order[q + 1] & MARK) && key_at(q + 1) == K) ++q;
+        for (int u = p, v = q; u <= v; ++u, --v) {
+            const unsigned short ou = order[u] & IDMASK, ov = order[v] & IDMASK;
+            order[u] = ov;
+            order[v] = ou;
+            pos[ov] = (unsigned short)u;
+            pos[ou] = (unsigned short)v;
+        }
+        Cand c;
+        c.dy = dy; c.dx = dx; c.i = (int)(gmin >> 16); c.j = (int)(gmin & 0xffffu);
+        if (p + h - 1 < n) {
+            const long long kt = proj(XY(order[p + h - 1] & IDMASK), dy, dx);
+            c.w = kt - K; c.t = K + kt;
+            if (cand_better(c, best)) best = c;
+        }
+        if (q - h + 1 >= 0) {
+            const long long kb = proj(XY(order[q - h + 1] & IDMASK), dy, dx);
+            c.w = K - kb; c.t = kb + K;
+            if (cand_better(c, best)) best = c;
+        }
+    }
+    __syncwarp();
+}
 
 // One warp per sweeper; each lane takes one of up to 32 consecutive events.
 //
@@ -644,6 +709,7 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
     if (w >= W) return;
     const unsigned start = range[2 * w], end = range[2 * w + 1];
     auto XY = [&](int k) { return load_xy<XY_SMEM>(s_xy, g_xy, k); };
+    const bool HEAVY_OK = n <= (int)IDMASK + 1;
     Cand best = cand_empty();
     auto offer = [&](long long wd, long long t, int dy, int dx, unsigned pr) {
         // cheap reject on the width alone before the full lexicographic test
@@ -671,6 +737,26 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
             const unsigned e = e_cur;
             const bool is_start = valid && !ev_cont(e);
             const unsigned smask = __ballot_sync(FULL, is_start);
+            // ---- a long group of one slope starting here: process it whole
+            if (HEAVY_OK && smask == 1u && navail == 32u && __shfl_sync(FULL, ev_cont(e_nxt) ? 1 : 0, 0)) {
+                unsigned g1 = k + 33;
+                for (;;) {
+                    const unsigned q = g1 + lane;
+                    const bool c = q < end && ev_cont(ev[q]);
+                    const unsigned bal = __ballot_sync(FULL, c);
+                    if (bal == FULL) { g1 += 32; continue; }
+                    g1 += __ffs(~bal) - 1;
+                    break;
+                }
+                if (g1 - k >= HEAVY_MIN) {
+                    heavy_group<XY_SMEM>(order, pos, s_xy, g_xy, n, h, ev, k, g1, lane, best);
+                    carried = 0xffffffffu;
+                    k = g1;
+                    e_cur = (k + lane < end) ? ev[k + lane] : 0u;
+                    e_nxt = (k + 32 + lane < end) ? ev[k + 32 + lane] : 0u;
+                    continue;
+                }
+            }
             const unsigned le = smask & lanemask_le;
             const int gfirst = le ? 31 - __clz(le) : -1;
             const unsigned pairv = ((unsigned)ev_i(e) << 16) | (unsigned)ev_j(e);
