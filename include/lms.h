@@ -184,6 +184,31 @@ LMS_API int lms_fit_learned(lms_setnet *net, const void *x, const void *y, int64
                             lms_stream_t stream);
 
 /*
+ * Batched fits of many point sets of uneven size (not in the paper: its
+ * Hough application runs one LMS per accumulator peak; this runs them all).
+ * lms_batch_plan_create sizes everything from the host offsets once: sets
+ * with at most plain_max_n points (0 = 256, at most 256) go to one
+ * persistent plain kernel over (set, run of slopes) work items in three
+ * size classes; larger sets (up to 32768 points) each get the exact sweep,
+ * spread over `streams` internal streams (0 = 8).  It allocates the plan's
+ * device memory and waits for the device.
+ *   offsets_host  B + 1 offsets of the sets in the x/y arrays (host).
+ *   h_host        per-set order statistic (NULL: floor(n/2) + 1 each).
+ * lms_fit_batched enqueues one batch on `stream` (forking to the plan's
+ * streams and joining back with events): it allocates nothing and does not
+ * synchronise, so it can be captured into a CUDA graph.  x, y: device int16
+ * arrays; offsets_dev: device copy of the offsets; out: B device records.
+ * One plan must not run two batches concurrently (they share its memory).
+ */
+typedef struct lms_batch_plan lms_batch_plan;
+LMS_API int lms_batch_plan_create(const int64_t *offsets_host, int64_t B, const int32_t *h_host,
+                                  int32_t plain_max_n, int32_t streams, lms_batch_plan **plan);
+LMS_API int lms_batch_plan_destroy(lms_batch_plan *plan);
+LMS_API size_t lms_batch_plan_bytes(const lms_batch_plan *plan);
+LMS_API int lms_fit_batched(lms_batch_plan *plan, const void *x, const void *y, const int64_t *offsets_dev,
+                            lms_result *out, lms_stream_t stream);
+
+/*
  * lms_workspace_size -- device bytes one lms_fit of this size needs.
  * lms_set_workspace  -- install a caller-owned device buffer (NULL restores
  *                       the internal one).  The buffer must stay valid and

@@ -1,0 +1,85 @@
+"""Autotuner for batched fits: picks the size threshold between the plain
+kernel classes and the sweep, and the number of sweep streams, by timing
+CUDA-graph replays of a batch plan on the caller's own sets.  Results are
+cached per (device name, size histogram) in autotune_cache.json next to
+this file.
+
+    from paper_1510_01041_gb300 import autotune
+    plan, cfg = autotune.tuned_plan(offsets, x, y, offsets_dev)
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import numpy as np
+
+from . import lms
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
+PLAIN_MAX = (64, 128, 256)
+STREAMS = (8, 16, 32, 48)
+
+
+def _key(offsets, device_name):
+    sizes = np.diff(np.asarray(offsets, dtype=np.int64))
+    hist = np.histogram(np.log2(np.maximum(sizes, 2)), bins=16, range=(1, 17))[0]
+    h = hashlib.sha1(hist.tobytes() + device_name.encode()).hexdigest()[:16]
+    return f"{device_name}:{sizes.size}:{h}"
+
+
+def _time_plan(plan, x, y, od, reps=2):
+    import torch
+    out = torch.empty((plan.B, lms.RESULT_DTYPE.itemsize), dtype=torch.uint8, device=x.device)
+    plan.fit(x, y, od, out=out)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.fit(x, y, od, out=out, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        g.replay()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t) / reps, g, out
+
+
+def tune(offsets, x, y, offsets_dev, candidates=None):
+    """Time every candidate (plain_max_n, streams); returns the best config."""
+    import torch
+    cands = candidates or [(p, s) for p in PLAIN_MAX for s in STREAMS]
+    results = []
+    for pm, ns in cands:
+        plan = lms.BatchPlan(offsets, plain_max_n=pm, streams=ns)
+        dt, _, _ = _time_plan(plan, x, y, offsets_dev, reps=1)
+        results.append(dict(plain_max_n=pm, streams=ns, seconds=dt))
+        del plan
+        torch.cuda.synchronize()
+    best = min(results, key=lambda r: r["seconds"])
+    return best, results
+
+
+def tuned_plan(offsets, x, y, offsets_dev, use_cache=True):
+    import torch
+    key = _key(offsets, torch.cuda.get_device_name(x.device))
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        try:
+            cache = json.load(open(CACHE))
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        cfg = cache[key]
+    else:
+        cfg, _ = tune(offsets, x, y, offsets_dev)
+        cache[key] = cfg
+        try:
+            json.dump(cache, open(CACHE, "w"), indent=1)
+        except OSError:
+            pass
+    return lms.BatchPlan(offsets, plain_max_n=cfg["plain_max_n"], streams=cfg["streams"]), cfg

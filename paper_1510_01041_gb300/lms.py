@@ -396,3 +396,54 @@ def pretrained(path: str = WEIGHTS, seed: int = 1) -> SetNet:
     if not os.path.exists(path):
         raise FileNotFoundError(f"{path}: run python -m paper_1510_01041_gb300.train_setnet")
     return SetNet(seed).load(path)
+
+
+# ------------------------------------------------------------------ batched fits
+class BatchPlan:
+    """lms_batch_plan for a fixed list of set sizes (CSR offsets)."""
+
+    def __init__(self, offsets, h=None, plain_max_n: int = 0, streams: int = 0):
+        L = lib()
+        if not getattr(L, "_batch_ready", False):
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+            L.lms_batch_plan_create.argtypes = [vp, i64, vp, i32, i32, ctypes.POINTER(ctypes.c_void_p)]
+            L.lms_batch_plan_create.restype = ctypes.c_int
+            L.lms_batch_plan_destroy.argtypes = [vp]
+            L.lms_batch_plan_destroy.restype = ctypes.c_int
+            L.lms_batch_plan_bytes.argtypes = [vp]
+            L.lms_batch_plan_bytes.restype = ctypes.c_size_t
+            L.lms_fit_batched.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.lms_fit_batched.restype = ctypes.c_int
+            L._batch_ready = True
+        self.L = L
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.B = self.offsets.size - 1
+        hh = None if h is None else np.ascontiguousarray(h, dtype=np.int32)
+        handle = ctypes.c_void_p()
+        rc = L.lms_batch_plan_create(ctypes.c_void_p(self.offsets.ctypes.data), self.B,
+                                     ctypes.c_void_p(hh.ctypes.data) if hh is not None else None,
+                                     int(plain_max_n), int(streams), ctypes.byref(handle))
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_batch_plan_create")
+        self.h = handle
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.L.lms_batch_plan_destroy(self.h)
+            self.h = None
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.L.lms_batch_plan_bytes(self.h))
+
+    def fit(self, x, y, offsets_dev, out=None, stream=None):
+        """Enqueue the batch; returns a uint8 CUDA tensor of B lms_result records."""
+        import torch
+        if out is None:
+            out = torch.empty((self.B, RESULT_DTYPE.itemsize), dtype=torch.uint8, device=x.device)
+        rc = self.L.lms_fit_batched(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                    ctypes.c_void_p(offsets_dev.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                    _stream_handle(stream))
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_fit_batched")
+        return out
