@@ -209,6 +209,35 @@ LMS_API int lms_fit_batched(lms_batch_plan *plan, const void *x, const void *y, 
                             lms_result *out, lms_stream_t stream);
 
 /*
+ * Line detection: standard Hough transform + exact LMS of every peak's
+ * supporting points (Sec. 5).  For each of B binary images (device, uint8,
+ * B x H x W, nonzero = edge pixel) with image-centre coordinates
+ * (x - W/2, y - H/2): every edge pixel votes for theta_t = pi t / n_theta,
+ * t < n_theta, in rho bin floor(x cos_t + y sin_t + n_rho/2) (clamped to
+ * [0, n_rho); products and the sum each rounded to float, no fused
+ * multiply-add); the top_k peaks per image are taken greedily in the order
+ * (votes desc, t asc, rho asc), skipping bins within +-nms_theta and
+ * +-nms_rho of a taken peak; the points within band_px of each peak's line
+ * (rho at the bin centre) are fitted by exact LMS, with x and y swapped for
+ * near-vertical peaks (|sin| < |cos|).
+ *   cos_sin   optional device table of n_theta (cos, sin) float pairs; NULL:
+ *             computed on the host as cos/sin in double rounded to float.
+ *   acc_out   optional device int32 [B][n_theta][n_rho] receiving the votes.
+ *   out       host array of B * top_k lms_line (peaks in greedy order).
+ * Synchronous; allocates its scratch.
+ */
+typedef struct {
+    int32_t theta_index, rho_index, votes;   /* the peak; theta_index = -1 if the image had fewer peaks */
+    int32_t transposed;                      /* 1: x and y swapped before the fit */
+    int32_t npoints;                         /* points within the band */
+    int32_t pad[3];
+    lms_result fit;                          /* status LMS_ERR_ARG if fewer than 2 points */
+} lms_line;
+LMS_API int lms_hough_refine(const uint8_t *edges, int64_t B, int32_t H, int32_t W, int32_t n_theta,
+                             int32_t n_rho, int32_t top_k, float band_px, int32_t nms_theta, int32_t nms_rho,
+                             const float *cos_sin, int32_t *acc_out, lms_line *out, lms_stream_t stream);
+
+/*
  * lms_workspace_size -- device bytes one lms_fit of this size needs.
  * lms_set_workspace  -- install a caller-owned device buffer (NULL restores
  *                       the internal one).  The buffer must stay valid and

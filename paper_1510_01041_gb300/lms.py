@@ -447,3 +447,44 @@ class BatchPlan:
         if rc != LMS_OK:
             raise LmsError(rc, "lms_fit_batched")
         return out
+
+
+# ------------------------------------------------------------------ Hough + LMS
+class _LmsResultC(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in ("w_num", "w_den", "s_num", "s_den", "t_num", "t_den")] + \
+               [(name, ctypes.c_double) for name in ("theta1", "theta2", "med_sq")] + \
+               [(name, ctypes.c_int32) for name in ("i", "j", "status", "algorithm")]
+
+
+class LmsLine(ctypes.Structure):
+    _fields_ = [("theta_index", ctypes.c_int32), ("rho_index", ctypes.c_int32), ("votes", ctypes.c_int32),
+                ("transposed", ctypes.c_int32), ("npoints", ctypes.c_int32), ("pad", ctypes.c_int32 * 3),
+                ("fit", _LmsResultC)]
+
+
+def hough_refine(edges, n_theta=1024, n_rho=2896, top_k=32, band_px=4.0, nms_theta=5, nms_rho=5,
+                 cos_sin=None, acc_out=None, stream=None):
+    """lms_hough_refine on a CUDA uint8 tensor [B, H, W]; returns a list of
+    B * top_k dicts (peak, band size, transposed flag, exact LMS fit)."""
+    L = lib()
+    if not getattr(L, "_hough_ready", False):
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.lms_hough_refine.argtypes = [vp, i64, i32, i32, i32, i32, i32, ctypes.c_float, i32, i32, vp, vp, vp, vp]
+        L.lms_hough_refine.restype = ctypes.c_int
+        L._hough_ready = True
+    B, H, W = edges.shape
+    edges = edges.contiguous()
+    out = (LmsLine * (B * top_k))()
+    rc = L.lms_hough_refine(ctypes.c_void_p(edges.data_ptr()), B, H, W, n_theta, n_rho, top_k, float(band_px),
+                            nms_theta, nms_rho,
+                            ctypes.c_void_p(cos_sin.data_ptr()) if cos_sin is not None else None,
+                            ctypes.c_void_p(acc_out.data_ptr()) if acc_out is not None else None,
+                            ctypes.byref(out), _stream_handle(stream))
+    if rc != LMS_OK:
+        raise LmsError(rc, "lms_hough_refine")
+    res = []
+    for ln in out:
+        d = {f: getattr(ln, f) for f in ("theta_index", "rho_index", "votes", "transposed", "npoints")}
+        d["fit"] = {f: getattr(ln.fit, f) for f, _ in _LmsResultC._fields_}
+        res.append(d)
+    return res
