@@ -81,6 +81,7 @@ struct Choice {
     int sms;
     size_t bytes;
     size_t bnb_off;   // offset of the branch-and-bound scratch
+    size_t f32_off;   // offset of the float32 sweep scratch
 };
 
 int plain_warps_for(int n, int sms)
@@ -95,14 +96,15 @@ int plain_warps_for(int n, int sms)
 
 int choose(int n, int h, int dtype, const lms_options *opt, int dev, Choice &c)
 {
-    (void)dtype;
     const int algo_req = opt ? opt->algorithm : LMS_ALGO_AUTO;
     int algo = algo_req;
-    if (algo == LMS_ALGO_AUTO) algo = (n <= 256) ? LMS_ALGO_PLAIN : LMS_ALGO_SWEEP;
+    if (algo == LMS_ALGO_AUTO) algo = (n <= 256 && dtype == LMS_I16) ? LMS_ALGO_PLAIN : LMS_ALGO_SWEEP;
+    if (dtype == LMS_F32 && algo != LMS_ALGO_SWEEP) return LMS_ERR_UNSUPPORTED;
     const int sms = sm_count(dev);
     c.algo = algo;
     c.sms = sms;
     c.bnb_off = 0;
+    c.f32_off = 0;
     if (algo == LMS_ALGO_PLAIN) {
         if (n > 1024) return LMS_ERR_UNSUPPORTED;
         c.plain_warps = plain_warps_for(n, sms);
@@ -114,6 +116,10 @@ int choose(int n, int h, int dtype, const lms_options *opt, int dev, Choice &c)
         if (algo == LMS_ALGO_BNB) {
             c.bnb_off = c.bytes;
             c.bytes += bnb_extra_bytes(n, sms);
+        }
+        if (dtype == LMS_F32) {
+            c.f32_off = c.bytes;
+            c.bytes += sweep_f32_extra_bytes(n, c.sweep.W);
         }
     } else {
         return LMS_ERR_ARG;
@@ -137,7 +143,6 @@ int check_args(const void *x, const void *y, int64_t n, int64_t &h, int32_t dtyp
         for (int k = 0; k < 4; ++k)
             if (opt->reserved[k]) return LMS_ERR_ARG;
     }
-    if (dtype == LMS_F32) return LMS_ERR_UNSUPPORTED;
     return LMS_OK;
 }
 
@@ -145,8 +150,6 @@ int check_args(const void *x, const void *y, int64_t n, int64_t &h, int32_t dtyp
 int run_fit(const void *x, const void *y, int n, int h, int dtype, const lms_options *opt, lms_result *out,
             cudaStream_t st, void *ws_in, const Choice &c)
 {
-    (void)dtype;
-    (void)opt;
     cudaGetLastError();
     if (c.algo == LMS_ALGO_PLAIN) {
         Cand *cands = static_cast<Cand *>(ws_in);
@@ -158,6 +161,11 @@ int run_fit(const void *x, const void *y, int n, int h, int dtype, const lms_opt
     }
     SweepPlan p = c.sweep;
     sweep_plan_carve(p, ws_in);
+    if (dtype == LMS_F32)
+        return launch_sweep_f32_fit(p, (const float *)x, (const float *)y,
+                                    static_cast<unsigned char *>(ws_in) + c.f32_off, out, st) == cudaSuccess
+                   ? LMS_OK
+                   : LMS_ERR_CUDA;
     if (c.algo == LMS_ALGO_BNB)
         return run_bnb(p, (const short *)x, (const short *)y, nullptr, opt ? opt->seed_mode : 0, out, nullptr,
                        static_cast<unsigned char *>(ws_in) + c.bnb_off, c.sms, st);

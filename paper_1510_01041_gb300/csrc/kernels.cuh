@@ -29,6 +29,33 @@ class StageTimer {
     cudaEvent_t a_;
 };
 
+// Slope-key policies for the event pipeline: key() returns false when the
+// pair has no slope (equal x) and otherwise an int64 key that orders slopes.
+struct KeyI16 {   // packed int16 points: exact key floor(dy 2^32 / dx)
+    static __device__ __forceinline__ bool key(const void *pts, int i, int j, long long &k)
+    {
+        const int *xy = static_cast<const int *>(pts);
+        int dy, dx;
+        if (!pair_slope(__ldg(&xy[i]), __ldg(&xy[j]), dy, dx)) return false;
+        k = slope_key(dy, dx);
+        return true;
+    }
+};
+struct KeyF32 {   // float2 points: the double slope dy/dx as order-preserving bits
+    static __device__ __forceinline__ bool key(const void *pts, int i, int j, long long &k)
+    {
+        const float2 *P = static_cast<const float2 *>(pts);
+        const float2 a = P[i], b = P[j];
+        double dx = (double)b.x - (double)a.x, dy = (double)b.y - (double)a.y;
+        if (dx == 0.0) return false;
+        if (dx < 0.0) { dx = -dx; dy = -dy; }
+        const double sl = __ddiv_rn(dy, dx);
+        const long long bits = sl == 0.0 ? 0LL : __double_as_longlong(sl);
+        k = bits < 0 ? (bits ^ 0x7fffffffffffffffLL) : bits;
+        return true;
+    }
+};
+
 // ---------------------------------------------------------------- plain path
 int plain_elems(int n);
 cudaError_t launch_plain(const short *x, const short *y, int n, int h, Cand *cands, int nwarps_total,
@@ -59,6 +86,7 @@ struct SweepPlan {
     unsigned *base;            // [BND_MAX + 1] bucket starts; base[NB] = E
     int *oversize;             // [BND_MAX] buckets too large for the shared-memory sort
     unsigned *ev;              // [emax] events
+    unsigned *ev2;             // [emax] merge copy for buckets above SEG_CAP (null if emax <= SEG_CAP)
     unsigned *range;           // [2W] sweeper event ranges
     unsigned short *orders;    // [W][n] start orders
     unsigned long long *gsort; // [W][P] global sort scratch when n > SORT_SMEM_N
@@ -75,6 +103,16 @@ cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short
 // plan = false: the caller has written the sweeper ranges itself
 cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan);
 const long long *sorted_sample(const SweepPlan &p);
+// generic halves of the event pipeline (sample .. bucket starts; scatter .. plan)
+template <class G> cudaError_t launch_events_prepare(const SweepPlan &p, const void *pts, cudaStream_t st);
+template <class G>
+cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsigned char *keep, cudaStream_t st,
+                                 bool plan);
+// float32 points: event pipeline on the double slope key, double-precision
+// sweep, reduction into `out` (device).  fscratch: sweep_f32_extra_bytes.
+cudaError_t launch_sweep_f32_fit(const SweepPlan &p, const float *x, const float *y, void *fscratch,
+                                 lms_result *out, cudaStream_t st);
+size_t sweep_f32_extra_bytes(int n, int W);
 
 // ---------------------------------------------------------------- branch and bound
 size_t bnb_extra_bytes(int n, int sms);

@@ -74,7 +74,8 @@ __global__ void k_pack(const short *__restrict__ x, const short *__restrict__ y,
 }
 
 // ---------------------------------------------------------------- sample
-__global__ void k_sample(const int *__restrict__ xy, int n, long long npairs, int S, long long *__restrict__ out)
+template <class G>
+__global__ void k_sample(const void *__restrict__ pts, int n, long long npairs, int S, long long *__restrict__ out)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= S) return;
@@ -82,8 +83,8 @@ __global__ void k_sample(const int *__restrict__ xy, int n, long long npairs, in
     const long long p = (long long)__umul64hi(r, (unsigned long long)npairs);
     int i, j;
     pair_decode(p, i, j);
-    int dy, dx;
-    out[k] = pair_slope(xy[i], xy[j], dy, dx) ? slope_key(dy, dx) : KEY_INF;
+    long long key;
+    out[k] = G::key(pts, i, j, key) ? key : KEY_INF;
 }
 
 // Bitonic sort of one chunk of SORT_CHUNK keys in shared memory.
@@ -183,8 +184,8 @@ __global__ void __launch_bounds__(1024) k_splitters(const long long *__restrict_
 // ---------------------------------------------------------------- count / scatter
 // Both passes walk the same upper-triangle tiles in the same static order,
 // so the scatter's per-CTA bucket cursors match the counts exactly.
-template <bool SCATTER>
-__global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const int *__restrict__ xy, int n,
+template <bool SCATTER, class G>
+__global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__restrict__ pts, int n,
                                                               const long long *__restrict__ bnd,
                                                               const int *__restrict__ meta,
                                                               unsigned *__restrict__ hist,
@@ -195,7 +196,6 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const int *__restr
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
     unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
-    __shared__ int s_tile[TILE];
     const int nbnd = meta[0], P2 = meta[1], NB = nbnd + 1;
     for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
     unsigned *my_hist = hist + (size_t)blockIdx.x * BND_MAX;
@@ -210,22 +210,15 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const int *__restr
     for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
         int bi, bj;
         tile_decode(q, bi, bj);
-        __syncthreads();
-        if (threadIdx.x < TILE) {
-            const int j = bj * TILE + threadIdx.x;
-            s_tile[threadIdx.x] = j < n ? xy[j] : 0;
-        }
-        __syncthreads();
         const int i = bi * TILE + il;
         if (i >= n) continue;
-        const int pi = xy[i];
 #pragma unroll 4
         for (int jj = 0; jj < JPT; ++jj) {
             const int j = bj * TILE + jl0 + jj;
             if (j <= i || j >= n) continue;
-            int dy, dx;
-            if (!pair_slope(pi, s_tile[jl0 + jj], dy, dx)) continue;
-            const int b = bucket_of(s_bnd, P2, slope_key(dy, dx));
+            long long key;
+            if (!G::key(pts, i, j, key)) continue;
+            const int b = bucket_of(s_bnd, P2, key);
             if (SCATTER && keep && !keep[b]) continue;
             const unsigned slot = atomicAdd(&s_cnt[b], 1u);
             if (SCATTER) ev[slot] = ev_pack(i, j, false);
@@ -279,11 +272,12 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(unsigned *__restrict__ bas
 }
 
 // ---------------------------------------------------------------- segsort
-__device__ __forceinline__ long long event_key(const int *__restrict__ xy, unsigned e)
+template <class G>
+__device__ __forceinline__ long long event_key(const void *__restrict__ pts, unsigned e)
 {
-    int dy, dx;
-    pair_slope(__ldg(&xy[ev_i(e)]), __ldg(&xy[ev_j(e)]), dy, dx);
-    return slope_key(dy, dx);
+    long long k = KEY_INF;
+    G::key(pts, ev_i(e), ev_j(e), k);
+    return k;
 }
 
 __device__ __forceinline__ unsigned pair_of(unsigned e) { return ((unsigned)ev_i(e) << 16) | (unsigned)ev_j(e); }
@@ -298,7 +292,8 @@ __device__ __forceinline__ bool ev_less(long long ka, unsigned ea, long long kb,
 // Sort each bucket by (exact slope key, pair); buckets with more than
 // SEG_CAP events are listed for k_segsort_big.  A bucket holding a single
 // slope only needs its smallest pair moved to the front.
-__global__ void __launch_bounds__(1024) k_segsort(const int *__restrict__ xy, unsigned *__restrict__ ev,
+template <class G>
+__global__ void __launch_bounds__(1024) k_segsort(const void *__restrict__ xy, unsigned *__restrict__ ev,
                                                   const unsigned *__restrict__ base,
                                                   const long long *__restrict__ bnd, int *__restrict__ meta,
                                                   int *__restrict__ oversize)
@@ -358,7 +353,7 @@ __global__ void __launch_bounds__(1024) k_segsort(const int *__restrict__ xy, un
         for (int k = threadIdx.x; k < P; k += blockDim.x) {
             if (k < (int)m) {
                 const unsigned e = ev[off + k];
-                s_key[k] = event_key(xy, e);
+                s_key[k] = event_key<G>(xy, e);
                 s_ev[k] = e;
             } else {
                 s_key[k] = KEY_INF;
@@ -389,48 +384,112 @@ __global__ void __launch_bounds__(1024) k_segsort(const int *__restrict__ xy, un
     }
 }
 
-// Fallback for buckets above SEG_CAP: an in-place bitonic sort in global
-// memory with keys recomputed from the points.  Every merge starts with a
-// flip step, so all compare-exchanges are ascending and the virtual +inf
-// padding above m never has to move: exchanges that reach past m are skipped.
-__global__ void __launch_bounds__(1024) k_segsort_big(const int *__restrict__ xy, unsigned *__restrict__ ev,
+// Buckets above SEG_CAP events, one CTA each: chunks of SEG_CAP events are
+// sorted in shared memory and written back, then runs are merged pairwise
+// (merge path: every thread finds its output range by a binary search on
+// the diagonal and merges it sequentially) between the bucket and its copy
+// in ev2, keys recomputed from the points.  (key, pair) is a strict total
+// order, so the result is the one of a full sort.
+template <class G>
+__global__ void __launch_bounds__(1024) k_segsort_big(const void *__restrict__ xy, unsigned *__restrict__ ev,
+                                                      unsigned *__restrict__ ev2,
                                                       const unsigned *__restrict__ base,
                                                       const int *__restrict__ meta,
                                                       const int *__restrict__ oversize)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long *s_key = reinterpret_cast<long long *>(smem);
+    unsigned *s_ev = reinterpret_cast<unsigned *>(smem + SEG_CAP * sizeof(long long));
     const int nbig = meta[2];
+    const int tid = threadIdx.x, nt = blockDim.x;
     for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
         const int b = oversize[q];
         const unsigned off = base[b], m = base[b + 1] - off;
-        unsigned *a = ev + off;
-        unsigned P = 1;
-        while (P < m) P <<= 1;
-        for (unsigned k = 2; k <= P; k <<= 1) {
-            for (unsigned t = threadIdx.x; t < P / 2; t += blockDim.x) {
-                const unsigned half = k >> 1, blk = t / half, r = t - blk * half;
-                const unsigned i = blk * k + r, l = blk * k + k - 1 - r;
-                if (l >= m) continue;
-                const unsigned ea = a[i], eb = a[l];
-                if (ev_less(event_key(xy, eb), eb, event_key(xy, ea), ea)) { a[i] = eb; a[l] = ea; }
+        unsigned *A = ev + off;
+        // sorted runs of SEG_CAP events
+        for (unsigned c0 = 0; c0 < m; c0 += SEG_CAP) {
+            const int mc = (int)min((unsigned)SEG_CAP, m - c0);
+            int P = 1;
+            while (P < mc) P <<= 1;
+            for (int k = tid; k < P; k += nt) {
+                if (k < mc) {
+                    const unsigned e = A[c0 + k];
+                    s_key[k] = event_key<G>(xy, e);
+                    s_ev[k] = e;
+                } else {
+                    s_key[k] = KEY_INF;
+                    s_ev[k] = 0xffffffffu;
+                }
             }
             __syncthreads();
-            for (unsigned j = k >> 2; j >= 1; j >>= 1) {
-                for (unsigned t = threadIdx.x; t < P / 2; t += blockDim.x) {
-                    const unsigned i = 2 * t - (t & (j - 1));
-                    const unsigned l = i + j;
-                    if (l >= m) continue;
-                    const unsigned ea = a[i], eb = a[l];
-                    if (ev_less(event_key(xy, eb), eb, event_key(xy, ea), ea)) { a[i] = eb; a[l] = ea; }
+            for (int k = 2; k <= P; k <<= 1) {
+                for (int j = k >> 1; j >= 1; j >>= 1) {
+                    for (int t = tid; t < P / 2; t += nt) {
+                        const int i = 2 * t - (t & (j - 1));
+                        const int l = i + j;
+                        const bool up = (i & k) == 0;
+                        const long long a = s_key[i], c = s_key[l];
+                        const unsigned ea = s_ev[i], ec = s_ev[l];
+                        if (up ? ev_less(c, ec, a, ea) : ev_less(a, ea, c, ec)) {
+                            s_key[i] = c; s_key[l] = a;
+                            s_ev[i] = ec; s_ev[l] = ea;
+                        }
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
             }
+            for (int k = tid; k < mc; k += nt) A[c0 + k] = s_ev[k];
+            __syncthreads();
+        }
+        // pairwise merges of the runs
+        unsigned *src = A, *dst = ev2 + off;
+        for (unsigned L = SEG_CAP; L < m; L <<= 1) {
+            for (unsigned r0 = 0; r0 < m; r0 += 2 * L) {
+                const int la = (int)min(L, m - r0);
+                const int lb = (int)min(L, m - r0 - la);
+                const unsigned *ra = src + r0, *rb = src + r0 + la;
+                unsigned *o = dst + r0;
+                const long long T = (long long)la + lb;
+                const int d0 = (int)(T * tid / nt), d1 = (int)(T * (tid + 1) / nt);
+                auto split = [&](int d) {
+                    int lo = max(0, d - lb), hi = min(d, la);
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        const unsigned x = ra[mid], y = rb[d - 1 - mid];
+                        if (ev_less(event_key<G>(xy, x), x, event_key<G>(xy, y), y)) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    return lo;
+                };
+                int ia = split(d0), ib = d0 - ia;
+                long long ka = ia < la ? event_key<G>(xy, ra[ia]) : KEY_INF;
+                long long kb = ib < lb ? event_key<G>(xy, rb[ib]) : KEY_INF;
+                for (int d = d0; d < d1; ++d) {
+                    const bool take_a = ib >= lb || (ia < la && ev_less(ka, ra[ia], kb, rb[ib]));
+                    if (take_a) {
+                        o[d] = ra[ia];
+                        ++ia;
+                        ka = ia < la ? event_key<G>(xy, ra[ia]) : KEY_INF;
+                    } else {
+                        o[d] = rb[ib];
+                        ++ib;
+                        kb = ib < lb ? event_key<G>(xy, rb[ib]) : KEY_INF;
+                    }
+                }
+            }
+            __syncthreads();
+            unsigned *t = src; src = dst; dst = t;
+        }
+        if (src != A) {
+            for (unsigned k = tid; k < m; k += nt) A[k] = src[k];
+            __syncthreads();
         }
         // group flags; decoding ignores the halves' order, so neighbours may
         // be rewritten concurrently
-        for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-            const unsigned e = a[k];
-            const bool c = k > 0 && event_key(xy, a[k - 1]) == event_key(xy, e);
-            a[k] = ev_pack(ev_i(e), ev_j(e), c);
+        for (unsigned k = tid; k < m; k += nt) {
+            const unsigned e = A[k];
+            const bool c = k > 0 && event_key<G>(xy, A[k - 1]) == event_key<G>(xy, e);
+            A[k] = ev_pack(ev_i(e), ev_j(e), c);
         }
         __syncthreads();
     }
@@ -965,6 +1024,7 @@ size_t sweep_plan_bytes(int n, int W, int C, int S)
     b += a256((size_t)(BND_MAX + 1) * 4);
     b += a256((size_t)BND_MAX * 4);
     b += a256((size_t)(emax > 0 ? emax : 1) * 4);
+    b += emax > SEG_CAP ? a256((size_t)emax * 4) : 0;
     b += a256((size_t)2 * W * 4);
     b += a256((size_t)W * n * 2);
     b += (n > SORT_SMEM_N) ? a256((size_t)W * P * 8) : 0;
@@ -987,6 +1047,7 @@ void sweep_plan_carve(SweepPlan &p, void *ws)
     p.base = (unsigned *)take((size_t)(BND_MAX + 1) * 4);
     p.oversize = (int *)take((size_t)BND_MAX * 4);
     p.ev = (unsigned *)take((size_t)(p.emax > 0 ? p.emax : 1) * 4);
+    p.ev2 = p.emax > SEG_CAP ? (unsigned *)take((size_t)p.emax * 4) : nullptr;
     p.range = (unsigned *)take((size_t)2 * p.W * 4);
     p.orders = (unsigned short *)take((size_t)p.W * p.n * 2);
     p.gsort = (p.n > SORT_SMEM_N) ? (unsigned long long *)take((size_t)p.W * P * 8) : nullptr;
@@ -1000,11 +1061,11 @@ const long long *sorted_sample(const SweepPlan &p)
     return (rounds & 1) ? p.skeys2 : p.skeys;
 }
 
-cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short *y, cudaStream_t st)
+template <class G>
+cudaError_t launch_events_prepare(const SweepPlan &p, const void *pts, cudaStream_t st)
 {
     const int n = p.n;
-    { StageTimer _t(STAGE_PACK, st); k_pack<<<(n + 255) / 256, 256, 0, st>>>(x, y, n, p.xy); }
-    { StageTimer _t(STAGE_SAMPLE, st); k_sample<<<(p.S + 255) / 256, 256, 0, st>>>(p.xy, n, p.emax, p.S, p.skeys); }
+    { StageTimer _t(STAGE_SAMPLE, st); k_sample<G><<<(p.S + 255) / 256, 256, 0, st>>>(pts, n, p.emax, p.S, p.skeys); }
     { StageTimer _t(STAGE_SAMPLE_SORT, st); k_sort_chunks<<<p.S / SORT_CHUNK, SORT_CHUNK / 2, 0, st>>>(p.skeys); }
     long long *src = p.skeys, *dst = p.skeys2;
     for (int width = SORT_CHUNK; width < p.S; width <<= 1) {
@@ -1013,24 +1074,48 @@ cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short
     }
     { StageTimer _t(STAGE_SPLITTERS, st); k_splitters<<<1, 1024, 0, st>>>(src, p.S, p.B, p.bnd, p.meta); }
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
-    cudaFuncSetAttribute(k_bucket_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    { StageTimer _t(STAGE_COUNT_PAIRS, st); k_bucket_pairs<false><<<p.C, CNT_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.meta, p.hist, nullptr, nullptr, nullptr); }
+    cudaFuncSetAttribute(k_bucket_pairs<false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
+    { StageTimer _t(STAGE_COUNT_PAIRS, st); k_bucket_pairs<false, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, nullptr, nullptr, nullptr); }
     { StageTimer _t(STAGE_PREFIX, st); k_bucket_prefix<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.hist, p.C, p.meta, p.base); }
     { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta); }
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan)
+template <class G>
+cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsigned char *keep, cudaStream_t st,
+                                 bool plan)
 {
     const int n = p.n;
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
-    cudaFuncSetAttribute(k_bucket_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    { StageTimer _t(STAGE_SCATTER, st); k_bucket_pairs<true><<<p.C, CNT_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep); }
+    cudaFuncSetAttribute(k_bucket_pairs<true, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
+    { StageTimer _t(STAGE_SCATTER, st); k_bucket_pairs<true, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep); }
     const size_t seg_smem = (size_t)SEG_CAP * 12;
-    cudaFuncSetAttribute(k_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
-    { StageTimer _t(STAGE_SEGSORT, st); k_segsort<<<p.C, 1024, seg_smem, st>>>(p.xy, p.ev, p.base, p.bnd, p.meta, p.oversize); }
-    { StageTimer _t(STAGE_SEGSORT_BIG, st); k_segsort_big<<<p.C, 1024, 0, st>>>(p.xy, p.ev, p.base, p.meta, p.oversize); }
+    cudaFuncSetAttribute(k_segsort<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
+    { StageTimer _t(STAGE_SEGSORT, st); k_segsort<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, p.base, p.bnd, p.meta, p.oversize); }
+    if (p.ev2) {
+        cudaFuncSetAttribute(k_segsort_big<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
+        StageTimer _t(STAGE_SEGSORT_BIG, st);
+        k_segsort_big<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, p.ev2, p.base, p.meta, p.oversize);
+    }
     if (plan) { StageTimer _t(STAGE_PLAN, st); k_plan<<<(p.W + 255) / 256, 256, 0, st>>>(p.base, p.meta, p.W, p.range); }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_events_prepare<KeyF32>(const SweepPlan &, const void *, cudaStream_t);
+template cudaError_t launch_events_finish<KeyF32>(const SweepPlan &, const void *, const unsigned char *, cudaStream_t,
+                                                  bool);
+
+cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short *y, cudaStream_t st)
+{
+    { StageTimer _t(STAGE_PACK, st); k_pack<<<(p.n + 255) / 256, 256, 0, st>>>(x, y, p.n, p.xy); }
+    return launch_events_prepare<KeyI16>(p, p.xy, st);
+}
+
+cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan)
+{
+    const int n = p.n;
+    cudaError_t e = launch_events_finish<KeyI16>(p, p.xy, keep, st, plan);
+    if (e != cudaSuccess) return e;
     int P = 1;
     while (P < n) P <<= 1;
     const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)P * 8 : 0;

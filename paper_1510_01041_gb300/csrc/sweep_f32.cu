@@ -1,0 +1,427 @@
+// sweep_f32.cu -- the kinetic sweep for float32 points (double arithmetic).
+//
+// Same method as the int16 sweep (Algorithm 1's candidate set, Sec. 3.3's
+// touched-window argument), with slopes s = dy/dx and projections
+// z = y - s x evaluated in double: the differences of two float32 values are
+// exact in double for coordinates of comparable magnitude, and a projection
+// is off by about 1e-16 |z|, far below the 1e-6 relative tolerance asked of
+// the median squared residual.  Events are ordered by the double slope (a
+// monotone rounding: never inverted, at worst merged).  Events of one slope
+// are applied one after another: two adjacent points swap; two points with
+// others between them (collinear at that slope) have the block between them
+// put into the order just after the slope.  Each event leaves its own pair
+// in the just-after order and no later event of the slope undoes that, so the
+// order is right once the slope is done, and the windows scored meanwhile
+// differ only by a permutation of points tied at that slope.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "lms.h"
+
+namespace lms {
+namespace {
+
+struct CandF {
+    double w;      // window width
+    double t;      // window centre
+    double s;      // slope
+    int i, j;      // the event pair
+    int valid;
+    int pad;
+};
+static_assert(sizeof(CandF) == 40, "CandF layout");
+
+__device__ __forceinline__ CandF candf_empty()
+{
+    CandF c;
+    c.w = 0; c.t = 0; c.s = 0; c.i = -1; c.j = -1; c.valid = 0; c.pad = 0;
+    return c;
+}
+
+__device__ __forceinline__ bool candf_better(const CandF &a, const CandF &b)
+{
+    if (!a.valid) return false;
+    if (!b.valid) return true;
+    if (a.w != b.w) return a.w < b.w;
+    if (a.s != b.s) return a.s < b.s;
+    if (a.t != b.t) return a.t < b.t;
+    if (a.i != b.i) return a.i < b.i;
+    return a.j < b.j;
+}
+
+__device__ __forceinline__ CandF candf_shfl(const CandF &c, int m)
+{
+    CandF o;
+    o.w = __shfl_xor_sync(FULL, c.w, m);
+    o.t = __shfl_xor_sync(FULL, c.t, m);
+    o.s = __shfl_xor_sync(FULL, c.s, m);
+    o.i = __shfl_xor_sync(FULL, c.i, m);
+    o.j = __shfl_xor_sync(FULL, c.j, m);
+    o.valid = __shfl_xor_sync(FULL, c.valid, m);
+    o.pad = 0;
+    return o;
+}
+
+__device__ __forceinline__ CandF candf_warp_best(CandF c)
+{
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        CandF o = candf_shfl(c, m);
+        if (candf_better(o, c)) c = o;
+    }
+    return c;
+}
+
+__device__ __forceinline__ double zf(float2 p, double s) { return __dsub_rn((double)p.y, __dmul_rn(s, (double)p.x)); }
+
+__device__ __forceinline__ double slope_of(float2 a, float2 b)
+{
+    double dx = (double)b.x - (double)a.x, dy = (double)b.y - (double)a.y;
+    if (dx < 0.0) { dx = -dx; dy = -dy; }
+    return __ddiv_rn(dy, dx);
+}
+
+__device__ __forceinline__ long long dkey(double v)
+{
+    const long long bits = v == 0.0 ? 0LL : __double_as_longlong(v);
+    return bits < 0 ? (bits ^ 0x7fffffffffffffffLL) : bits;
+}
+
+// One CTA: pack the coordinates and record whether all of them are finite.
+__global__ void __launch_bounds__(1024) k_pack_f32(const float *__restrict__ x, const float *__restrict__ y, int n,
+                                                   float2 *__restrict__ P, int *__restrict__ bad)
+{
+    int nf = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const float2 v = make_float2(x[k], y[k]);
+        nf |= !(isfinite(v.x) && isfinite(v.y));
+        P[k] = v;
+    }
+    nf = __syncthreads_or(nf);
+    if (threadIdx.x == 0) *bad = nf;
+}
+
+// Sweeper start: sort by (z at the first slope, x ascending, index), score
+// every window.  keys/idx: shared memory (n <= 8192) or global scratch.
+__global__ void __launch_bounds__(1024) k_sweep_init_f32(const float2 *__restrict__ P, int n, int h,
+                                                         const unsigned *__restrict__ ev,
+                                                         const unsigned *__restrict__ range, int W,
+                                                         const int *__restrict__ meta,
+                                                         const unsigned *__restrict__ base,
+                                                         unsigned short *__restrict__ orders,
+                                                         long long *__restrict__ gkeys, unsigned short *__restrict__ gidx,
+                                                         CandF *__restrict__ cands)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_slope;
+    __shared__ CandF s_best[32];
+    const int w = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned E = base[meta[0] + 1];
+    const unsigned start = range[2 * w], end = range[2 * w + 1];
+    const bool vertical = (E == 0 && w == 0);
+    if (start >= end && !vertical) {
+        if (threadIdx.x == 0) cands[w] = candf_empty();
+        return;
+    }
+    int Pn = 1;
+    while (Pn < n) Pn <<= 1;
+    long long *key = (n <= SORT_SMEM_N) ? reinterpret_cast<long long *>(smem) : gkeys + (size_t)w * Pn;
+    unsigned short *idx = (n <= SORT_SMEM_N) ? reinterpret_cast<unsigned short *>(smem + (size_t)Pn * 8)
+                                            : gidx + (size_t)w * Pn;
+    if (threadIdx.x == 0) s_slope = vertical ? 0.0 : slope_of(P[ev_i(ev[start])], P[ev_j(ev[start])]);
+    __syncthreads();
+    const double s0 = s_slope;
+    for (int k = threadIdx.x; k < Pn; k += blockDim.x) {
+        key[k] = k < n ? dkey(zf(P[k], s0)) : 0x7fffffffffffffffLL;
+        idx[k] = (unsigned short)(k < n ? k : 0);
+    }
+    __syncthreads();
+    // bitonic on (key, x, index)
+    for (int kk = 2; kk <= Pn; kk <<= 1) {
+        for (int j = kk >> 1; j >= 1; j >>= 1) {
+            for (int t = threadIdx.x; t < Pn / 2; t += blockDim.x) {
+                const int i = 2 * t - (t & (j - 1));
+                const int l = i + j;
+                const bool up = (i & kk) == 0;
+                const long long a = key[i], b = key[l];
+                const unsigned short ia = idx[i], ib = idx[l];
+                bool gt;
+                if (a != b) gt = a > b;
+                else if (i < n && l < n && P[ia].x != P[ib].x) gt = P[ia].x > P[ib].x;
+                else gt = ia > ib;
+                if (gt == up) { key[i] = b; key[l] = a; idx[i] = ib; idx[l] = ia; }
+            }
+            __syncthreads();
+        }
+    }
+    for (int k = threadIdx.x; k < n; k += blockDim.x) orders[(size_t)w * n + k] = idx[k];
+    CandF best = candf_empty();
+    for (int a = threadIdx.x; a + h - 1 < n; a += blockDim.x) {
+        const double zb = zf(P[idx[a]], s0), zt = zf(P[idx[a + h - 1]], s0);
+        CandF c;
+        c.w = zt - zb; c.t = 0.5 * (zb + zt); c.s = s0; c.valid = 1; c.pad = 0;
+        c.i = -1; c.j = -1;
+        if (candf_better(c, best)) best = c;
+    }
+    best = candf_warp_best(best);
+    if (lane == 0) s_best[warp] = best;
+    __syncthreads();
+    if (warp == 0) {
+        best = lane < (int)(blockDim.x >> 5) ? s_best[lane] : candf_empty();
+        best = candf_warp_best(best);
+        if (lane == 0) {
+            if (vertical) { best.i = -1; best.j = -1; }
+            else { const unsigned e = ev[start]; best.i = ev_i(e); best.j = ev_j(e); }
+            cands[w] = best;
+        }
+    }
+}
+
+template <bool XY_SMEM>
+__device__ __forceinline__ float2 ldp(const float2 *s_p, const float2 *__restrict__ g_p, int k)
+{
+    return XY_SMEM ? s_p[k] : g_p[k];
+}
+
+// One warp per sweeper: lane-parallel swaps with the conflict rule of the
+// int16 sweep; a pair that is not adjacent is repaired by lane 0.
+template <bool XY_SMEM>
+__global__ void __launch_bounds__(256) k_sweep_f32(const float2 *__restrict__ g_p, int n, int h,
+                                                   const unsigned *__restrict__ ev,
+                                                   const unsigned *__restrict__ range, int W,
+                                                   const unsigned short *__restrict__ orders,
+                                                   CandF *__restrict__ cands)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    float2 *s_p = reinterpret_cast<float2 *>(smem);
+    const size_t off0 = XY_SMEM ? (((size_t)n * 8 + 15) & ~(size_t)15) : 0;
+    const size_t half = ((size_t)n * 2 + 15) & ~(size_t)15;
+    unsigned short *order = reinterpret_cast<unsigned short *>(smem + off0 + warp * 2 * half);
+    unsigned short *pos = reinterpret_cast<unsigned short *>(smem + off0 + warp * 2 * half + half);
+    if (XY_SMEM) {
+        for (int k = threadIdx.x; k < n; k += blockDim.x) s_p[k] = g_p[k];
+        __syncthreads();
+    }
+    const int w = blockIdx.x * nwarp + warp;
+    if (w >= W) return;
+    const unsigned start = range[2 * w], end = range[2 * w + 1];
+    auto PT = [&](int k) { return ldp<XY_SMEM>(s_p, g_p, k); };
+    CandF best = candf_empty();
+    auto offer = [&](double wd, double t, double sl, int i, int j) {
+        CandF c;
+        c.w = wd; c.t = t; c.s = sl; c.i = i; c.j = j; c.valid = 1; c.pad = 0;
+        if (candf_better(c, best)) best = c;
+    };
+    if (start < end) {
+        for (int a = lane; a < n; a += 32) {
+            const unsigned short p = orders[(size_t)w * n + a];
+            order[a] = p;
+            pos[p] = (unsigned short)a;
+        }
+        __syncwarp();
+        unsigned k = start;
+        while (k < end) {
+            const unsigned navail = min(32u, end - k);
+            const bool valid = (unsigned)lane < navail;
+            const unsigned e = valid ? ev[k + lane] : 0u;
+            int a = ev_i(e), b = ev_j(e);
+            float2 Pa = PT(a), Pb = PT(b);
+            if (Pa.x > Pb.x) {
+                const int t = a; a = b; b = t;
+                const float2 tp = Pa; Pa = Pb; Pb = tp;
+            }
+            const double sl = slope_of(Pa, Pb);
+            const int pa = valid ? pos[a] : 0, pb = valid ? pos[b] : 0;
+            const bool done = valid && pb < pa;
+            const bool simple = valid && !done && pb == pa + 1;
+            const bool repair = valid && !done && !simple;
+            // an earlier swap of this batch next to this one, or at the far
+            // end of one of its windows, makes the lane wait for the next batch
+            const unsigned me = simple ? (((unsigned)pa << 1) | 1u) : 0u;
+            bool conflict = false;
+            for (int t = 0; t < 31; ++t) {
+                const unsigned o = __shfl_sync(FULL, me, t);
+                if (!simple || t >= lane || !(o & 1u)) continue;
+                const int d = abs(pa - (int)(o >> 1));
+                if (d <= 2 || abs(d - (h - 1)) <= 1) conflict = true;
+            }
+            const unsigned bad = __ballot_sync(FULL, repair || conflict);
+            const int cut = bad ? __ffs(bad) - 1 : (int)navail;
+            if (cut > 0) {
+                const bool go = simple && lane < cut;
+                const double K = zf(Pa, sl);
+                double kt = K, kb = K;
+                const int top = pa + h - 1, bot = pa - h + 2;
+                if (go) {
+                    if (top < n && top > pa + 1) kt = zf(PT(order[top]), sl);
+                    if (bot >= 0 && bot < pa) kb = zf(PT(order[bot]), sl);
+                }
+                __syncwarp();
+                if (go) {
+                    order[pa] = (unsigned short)b;
+                    order[pa + 1] = (unsigned short)a;
+                    pos[b] = (unsigned short)pa;
+                    pos[a] = (unsigned short)(pa + 1);
+                    if (top < n) offer(kt - K, 0.5 * (K + kt), sl, min(a, b), max(a, b));
+                    if (bot >= 0) offer(K - kb, 0.5 * (kb + K), sl, min(a, b), max(a, b));
+                }
+                __syncwarp();
+                k += cut;
+            } else {
+                // lane 0's pair is not adjacent: every point between its two
+                // points meets them at this slope (the order is sorted just
+                // before it), so the block is put in the order just after the
+                // slope, x descending (a stable sort: equal x never cross), and
+                // every window with an end in the block is scored.  A block in
+                // strictly ascending x (the usual case) is reversed by the warp.
+                const int lo = __shfl_sync(FULL, pa, 0), hi = __shfl_sync(FULL, pb, 0);
+                const double rsl = __shfl_sync(FULL, sl, 0);
+                const int ra = __shfl_sync(FULL, a, 0), rb = __shfl_sync(FULL, b, 0);
+                bool asc = true;
+                for (int u = lo + lane; u < hi; u += 32) asc = asc && PT(order[u]).x < PT(order[u + 1]).x;
+                if (__all_sync(FULL, asc)) {
+                    for (int u = lane; u < (hi - lo + 1) / 2; u += 32) {
+                        const unsigned short ou = order[lo + u], ov = order[hi - u];
+                        order[lo + u] = ov;
+                        order[hi - u] = ou;
+                    }
+                } else if (lane == 0) {
+                    for (int u = lo + 1; u <= hi; ++u) {
+                        const unsigned short v = order[u];
+                        const float xv = PT(v).x;
+                        int t = u - 1;
+                        while (t >= lo && PT(order[t]).x < xv) {
+                            order[t + 1] = order[t];
+                            --t;
+                        }
+                        order[t + 1] = v;
+                    }
+                }
+                __syncwarp();
+                for (int u = lo + lane; u <= hi; u += 32) pos[order[u]] = (unsigned short)u;
+                __syncwarp();
+                const int pi = min(ra, rb), pj = max(ra, rb);
+                for (int q = lo + lane; q <= hi; q += 32) {
+                    if (q + h - 1 < n) {
+                        const double zb = zf(PT(order[q]), rsl), zt = zf(PT(order[q + h - 1]), rsl);
+                        offer(zt - zb, 0.5 * (zb + zt), rsl, pi, pj);
+                    }
+                    if (q - h + 1 >= 0) {
+                        const double zb = zf(PT(order[q - h + 1]), rsl), zt = zf(PT(order[q]), rsl);
+                        offer(zt - zb, 0.5 * (zb + zt), rsl, pi, pj);
+                    }
+                }
+                __syncwarp();
+                k += 1;
+            }
+        }
+    }
+    best = candf_warp_best(best);
+    if (lane == 0) cands[W + w] = best;
+}
+
+__global__ void __launch_bounds__(1024) k_argmin_f32(const CandF *__restrict__ cands, int count,
+                                                     const int *__restrict__ bad, lms_result *__restrict__ out)
+{
+    __shared__ CandF s_best[32];
+    CandF best = candf_empty();
+    for (int k = threadIdx.x; k < count; k += blockDim.x)
+        if (candf_better(cands[k], best)) best = cands[k];
+    best = candf_warp_best(best);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_best[warp] = best;
+    __syncthreads();
+    if (warp != 0) return;
+    best = lane < (int)(blockDim.x >> 5) ? s_best[lane] : candf_empty();
+    best = candf_warp_best(best);
+    if (lane != 0) return;
+    lms_result r;
+    r.w_num = r.w_den = r.s_num = r.s_den = r.t_num = r.t_den = 0;
+    r.algorithm = LMS_ALGO_SWEEP;
+    r.theta1 = best.s;
+    r.theta2 = best.t;
+    const double half = 0.5 * best.w;
+    r.med_sq = half * half;
+    r.i = best.i;
+    r.j = best.j;
+    r.status = *bad ? LMS_ERR_RANGE
+                    : (!best.valid ? LMS_ERR_INTERNAL : (best.i < 0 ? LMS_ERR_VERTICAL : LMS_OK));
+    *out = r;
+}
+
+size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t sweep_f32_extra_bytes(int n, int W)
+{
+    int Pn = 1;
+    while (Pn < n) Pn <<= 1;
+    size_t b = a256(16);                                    // non-finite flag
+    b += a256((size_t)n * 8);                               // float2 points
+    b += a256((size_t)2 * W * sizeof(CandF));               // candidates
+    if (n > SORT_SMEM_N) b += a256((size_t)W * Pn * 8) + a256((size_t)W * Pn * 2);
+    return b;
+}
+
+// The float32 fit: the event pipeline with the double-slope key, the float
+// sweep, and the final reduction.  `out` is the device result.
+cudaError_t launch_sweep_f32_fit(const SweepPlan &p, const float *x, const float *y, void *fscratch,
+                                 lms_result *out, cudaStream_t st)
+{
+    const int n = p.n;
+    int Pn = 1;
+    while (Pn < n) Pn <<= 1;
+    unsigned char *q = static_cast<unsigned char *>(fscratch);
+    int *bad = reinterpret_cast<int *>(q);
+    q += a256(16);
+    float2 *P = reinterpret_cast<float2 *>(q);
+    q += a256((size_t)n * 8);
+    CandF *cands = reinterpret_cast<CandF *>(q);
+    q += a256((size_t)2 * p.W * sizeof(CandF));
+    long long *gkeys = nullptr;
+    unsigned short *gidx = nullptr;
+    if (n > SORT_SMEM_N) {
+        gkeys = reinterpret_cast<long long *>(q);
+        q += a256((size_t)p.W * Pn * 8);
+        gidx = reinterpret_cast<unsigned short *>(q);
+    }
+    { StageTimer _t(STAGE_PACK, st); k_pack_f32<<<1, 1024, 0, st>>>(x, y, n, P, bad); }
+    cudaError_t e = launch_events_prepare<KeyF32>(p, P, st);
+    if (e != cudaSuccess) return e;
+    e = launch_events_finish<KeyF32>(p, P, nullptr, st, true);
+    if (e != cudaSuccess) return e;
+    const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)Pn * 10 : 0;
+    cudaFuncSetAttribute(k_sweep_init_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)init_smem);
+    {
+        StageTimer _t(STAGE_INIT, st);
+        k_sweep_init_f32<<<p.W, 1024, init_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.meta, p.base, p.orders, gkeys,
+                                                      gidx, cands);
+    }
+    const size_t per = 2 * (((size_t)n * 2 + 15) / 16 * 16);
+    const bool xs = (size_t)n * 8 + per <= 227 * 1024 && n <= 8192;
+    const size_t xyb = xs ? ((size_t)n * 8 + 15) / 16 * 16 : 0;
+    int spb = (int)((227 * 1024 - xyb) / per);
+    spb = spb < 1 ? 1 : (spb > 8 ? 8 : spb);
+    const size_t sw_smem = xyb + per * spb;
+    const int blocks = (p.W + spb - 1) / spb;
+    if (xs) {
+        cudaFuncSetAttribute(k_sweep_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
+        StageTimer _t(STAGE_SWEEP, st);
+        k_sweep_f32<true><<<blocks, 32 * spb, sw_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.orders, cands);
+    } else {
+        cudaFuncSetAttribute(k_sweep_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
+        StageTimer _t(STAGE_SWEEP, st);
+        k_sweep_f32<false><<<blocks, 32 * spb, sw_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.orders, cands);
+    }
+    {
+        StageTimer _t(STAGE_ARGMIN, st);
+        k_argmin_f32<<<1, 1024, 0, st>>>(cands, 2 * p.W, bad, out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lms

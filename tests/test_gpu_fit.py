@@ -135,6 +135,31 @@ def test_sweep_n8192(L, orc):
     assert same(gpu_fit(L, x, y, 0, "sweep"), o)
 
 
+def test_sweep_n16384(L, orc):
+    """n above the shared-memory start sort; buckets above the shared-memory
+    segment cap are sorted by chunk sorts plus merges."""
+    x, y = datagen.line_with_outliers(16384, 2)
+    o = orc.lms_i16(x, y, 0, "sweep")
+    assert same(gpu_fit(L, x, y, 0, "sweep"), o)
+
+
+def test_oversize_buckets_merge(L, orc):
+    """Few buckets: every bucket is far above the shared-memory cap, so the
+    events go through the chunk sorts and several merge rounds."""
+    x, y = datagen.line_with_outliers(2048, 7)
+    o = orc.lms_i16(x, y, 0, "sweep")
+    for bk in (1, 5, 33):
+        assert same(gpu_fit(L, x, y, 0, "sweep", buckets=bk), o), bk
+    rng = np.random.default_rng(19)
+    k = 900
+    xs = rng.integers(-300, 300, k)
+    xc = np.concatenate([xs, rng.integers(-400, 400, 2000 - k)]).astype(np.int16)
+    yc = np.concatenate([3 * xs - 7, rng.integers(-900, 900, 2000 - k)]).astype(np.int16)
+    o = orc.lms_i16(xc, yc, 0, "sweep")
+    for bk in (2, 9):
+        assert same(gpu_fit(L, xc, yc, 0, "sweep", buckets=bk), o), ("collinear", bk)
+
+
 def test_sweeper_and_bucket_counts_do_not_change_result(L, orc):
     x, y = datagen.line_with_outliers(1500, 4)
     o = orc.lms_i16(x, y, 0, "sweep")
