@@ -170,7 +170,7 @@ int run_fit(const void *x, const void *y, int n, int h, int dtype, const lms_opt
         return run_bnb(p, (const short *)x, (const short *)y, nullptr, opt ? opt->seed_mode : 0, out, nullptr,
                        static_cast<unsigned char *>(ws_in) + c.bnb_off, c.sms, st);
     if (launch_sweep(p, (const short *)x, (const short *)y, st) != cudaSuccess) return LMS_ERR_CUDA;
-    if (launch_argmin(p.cands, 2 * p.W, out, LMS_ALGO_SWEEP, p.meta + 3, st) != cudaSuccess)
+    if (launch_argmin(p.cands, p.W + p.G, out, LMS_ALGO_SWEEP, p.meta + 3, st) != cudaSuccess)
         return LMS_ERR_CUDA;
     return LMS_OK;
 }

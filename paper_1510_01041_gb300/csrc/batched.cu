@@ -442,7 +442,7 @@ int lms_fit_batched(lms_batch_plan *p, const void *xv, const void *yv, const int
         sweep_plan_configure(sp, n, p->hval[i], sms, 0, 0);
         sweep_plan_carve(sp, p->ws[s]);
         if (launch_sweep(sp, x + a, y + a, p->streams[s]) != cudaSuccess) return LMS_ERR_CUDA;
-        if (launch_argmin(sp.cands, 2 * sp.W, out + i, LMS_ALGO_SWEEP, sp.meta + 3, p->streams[s]) != cudaSuccess)
+        if (launch_argmin(sp.cands, sp.W + sp.G, out + i, LMS_ALGO_SWEEP, sp.meta + 3, p->streams[s]) != cudaSuccess)
             return LMS_ERR_CUDA;
     }
     for (int s = 0; s < p->nstreams; ++s) {

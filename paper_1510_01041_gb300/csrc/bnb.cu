@@ -175,6 +175,7 @@ __global__ void k_min_ub(const long long *__restrict__ w, int nk, long long *__r
     if (threadIdx.x == 0) *ub = m;
 }
 
+constexpr unsigned long long BNB_MIN_RANGE = 512;   // events per swept range, at least
 constexpr double PRED_WINDOW = 0.35;   // radians around a predicted slope angle
 
 // Seed slopes.  With a predicted slope: half of them evenly spaced quantiles
@@ -396,41 +397,40 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         if (keepv[b]) { run += base[b + 1] - base[b]; ++kept_buckets; }
     }
     kbase[NB] = run;
-    // sweeper ranges: whole buckets, never across a dropped bucket (the
-    // kinetic order must see every event between its first and last slope)
+    // ranges: pieces of about `target` events inside each run of consecutive
+    // kept buckets (a range never spans a dropped bucket: the kinetic order
+    // must see every event between its first and last slope); the device
+    // then moves every bound forward to the next start of a group of equal
+    // slopes.  About one range per sweeping warp, but at least
+    // BNB_MIN_RANGE events each, so that a range's start sort pays off.
     std::vector<unsigned> rng(2 * (size_t)p.W, 0u);
     {
-        std::vector<std::pair<int, int>> runs;
+        std::vector<std::pair<unsigned, unsigned>> runs;
         for (int b = 0; b < NB;) {
             if (!keepv[b] || base[b + 1] == base[b]) { ++b; continue; }
             int e = b + 1;
             while (e < NB && keepv[e]) ++e;
-            runs.push_back({b, e});
+            runs.push_back({kbase[b], kbase[e]});
             b = e;
         }
-        unsigned long long target = std::max<unsigned long long>(1, (unsigned long long)run / p.W);
+        unsigned long long target = std::max<unsigned long long>(BNB_MIN_RANGE, ((unsigned long long)run + p.G - 1) / p.G);
         for (;;) {
-            int used = 0;
-            bool fits = true;
-            for (const auto &r : runs) {
-                int b = r.first;
-                while (b < r.second) {
-                    int e = b + 1;
-                    while (e < r.second && kbase[e] - kbase[b] < target) ++e;
-                    if (used >= p.W) { fits = false; break; }
-                    rng[2 * used] = kbase[b];
-                    rng[2 * used + 1] = kbase[e];
-                    ++used;
-                    b = e;
-                }
-                if (!fits) break;
-            }
-            if (fits) {
-                for (int w = used; w < p.W; ++w) { rng[2 * w] = run; rng[2 * w + 1] = run; }
-                break;
-            }
+            unsigned long long count = 0;
+            for (const auto &r : runs) count += (r.second - r.first + target - 1) / target;
+            if (count <= (unsigned long long)p.W) break;
             target *= 2;
         }
+        size_t used = 0;
+        for (const auto &r : runs) {
+            const unsigned long long len = r.second - r.first;
+            const unsigned long long pieces = (len + target - 1) / target;
+            for (unsigned long long k = 0; k < pieces; ++k) {
+                rng[2 * used] = r.first + (unsigned)(len * k / pieces);
+                rng[2 * used + 1] = r.first + (unsigned)(len * (k + 1) / pieces);
+                ++used;
+            }
+        }
+        for (size_t w = used; w < (size_t)p.W; ++w) { rng[2 * w] = run; rng[2 * w + 1] = run; }
     }
     if (cudaMemcpyAsync(p.base, kbase.data(), sizeof(unsigned) * (NB + 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return LMS_ERR_CUDA;
@@ -438,7 +438,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     if (cudaMemcpyAsync(p.range, rng.data(), sizeof(unsigned) * 2 * p.W, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return LMS_ERR_CUDA;
     if (launch_sweep_finish(p, keep, st, false) != cudaSuccess) return LMS_ERR_CUDA;
-    if (launch_argmin(p.cands, 2 * p.W, out, LMS_ALGO_BNB, p.meta + 3, st) != cudaSuccess) return LMS_ERR_CUDA;
+    if (launch_argmin(p.cands, p.W + p.G, out, LMS_ALGO_BNB, p.meta + 3, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
     if (stats) {
         stats->events_total = E;

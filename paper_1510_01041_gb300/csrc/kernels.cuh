@@ -72,8 +72,9 @@ struct SweepPlan {
     int S;             // sampled pairs (power of two, >= 1024)
     int B;             // target number of quantile buckets
     int C;             // CTAs of the count / scatter passes
-    int W;             // sweepers
-    int spb;           // sweepers (warps) per sweep CTA
+    int W;             // slope ranges (each starts with a sort of the points)
+    int G;             // sweeping warps of the persistent sweep kernel (G < W + spb)
+    int spb;           // sweeping warps per sweep CTA
     bool xy_smem;      // sweep CTAs keep all points in shared memory
     long long emax;    // n (n - 1) / 2
     // device buffers
@@ -81,16 +82,16 @@ struct SweepPlan {
     long long *skeys;          // [S] sampled slope keys
     long long *skeys2;         // [S] merge ping-pong
     long long *bnd;            // [BND_MAX] bucket boundaries, padded with INT64_MAX
-    int *meta;                 // [8] 0 nbnd, 1 P2, 2 oversize count, 3 error flags
+    int *meta;                 // [16] 0 nbnd, 1 P2, 2 oversize count, 3 error flags, 4 range counter
     unsigned *hist;            // [C][BND_MAX] per-CTA bucket counts, then offsets
     unsigned *base;            // [BND_MAX + 1] bucket starts; base[NB] = E
     int *oversize;             // [BND_MAX] buckets too large for the shared-memory sort
     unsigned *ev;              // [emax] events
     unsigned *ev2;             // [emax] merge copy for buckets above SEG_CAP (null if emax <= SEG_CAP)
-    unsigned *range;           // [2W] sweeper event ranges
+    unsigned *range;           // [2W] range event bounds
     unsigned short *orders;    // [W][n] start orders
     unsigned long long *gsort; // [W][P] global sort scratch when n > SORT_SMEM_N
-    Cand *cands;               // [2W] init + sweep candidates
+    Cand *cands;               // [W + G] range-start + sweeping-warp candidates
 };
 
 size_t sweep_plan_bytes(int n, int W, int C, int S);
@@ -100,7 +101,8 @@ cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cud
 // the two halves of launch_sweep: bucket counts and starts (prepare), then
 // scatter of the kept buckets' events, bucket sorts and the sweep (finish)
 cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short *y, cudaStream_t st);
-// plan = false: the caller has written the sweeper ranges itself
+// plan = false: the caller has written the range bounds (any event offsets
+// inside runs of kept buckets); they are moved to group starts on the device
 cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan);
 const long long *sorted_sample(const SweepPlan &p);
 // generic halves of the event pipeline (sample .. bucket starts; scatter .. plan)

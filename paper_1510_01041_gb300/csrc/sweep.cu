@@ -38,6 +38,8 @@ constexpr long long KEY_INF = 0x7fffffffffffffffLL;
 constexpr int TILE = 64;          // pair tile edge of the count / scatter passes
 constexpr int CNT_THREADS = 512;  // threads of a count / scatter CTA
 constexpr int SORT_CHUNK = 1024;  // sample keys sorted per shared-memory chunk
+constexpr int RANGE_FACTOR = 4;   // slope ranges per sweeping warp (dynamic load balance)
+constexpr long long MIN_RANGE_EVENTS = 512;
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
 {
@@ -496,21 +498,59 @@ __global__ void __launch_bounds__(1024) k_segsort_big(const void *__restrict__ x
 }
 
 // ---------------------------------------------------------------- plan
-// Sweeper w takes the buckets whose first event falls in [E w / W, E (w+1) / W).
-__global__ void k_plan(const unsigned *__restrict__ base, const int *__restrict__ meta, int W,
-                       unsigned *__restrict__ range)
+constexpr unsigned SNAP_SCAN = 4096;   // events searched for a group start before the bucket end is taken
+
+// First event at or after t that starts a group of equal slopes (t itself if
+// it does), found by one warp inside t's bucket.  A group never spans two
+// buckets, so the bucket's end is always a valid answer; it is taken when no
+// start turns up within SNAP_SCAN events.  Every lane returns the same value.
+__device__ unsigned snap_group_start(const unsigned *__restrict__ ev, const unsigned *__restrict__ base, int NB,
+                                     unsigned t, int lane)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= W) return;
+    const unsigned E = base[NB];
+    if (t >= E) return E;
+    int lo = 0, hi = NB;   // base[lo] <= t < base[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (base[mid] <= t) lo = mid; else hi = mid;
+    }
+    const unsigned be = base[hi];
+    for (unsigned q = t; q < be && q - t < SNAP_SCAN; q += 32) {
+        const unsigned u = q + lane;
+        const unsigned bal = __ballot_sync(FULL, u < be && !ev_cont(ev[u]));
+        if (bal) return q + __ffs(bal) - 1;
+    }
+    return be;
+}
+
+// Range r covers the events [s(E r / W), s(E (r + 1) / W)), s = the snap to
+// a group start above: equal event counts up to the group granularity.  One
+// warp per range.
+__global__ void k_plan(const unsigned *__restrict__ ev, const unsigned *__restrict__ base,
+                       const int *__restrict__ meta, int W, unsigned *__restrict__ range)
+{
+    const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (r >= W) return;
     const int NB = meta[0] + 1;
     const unsigned E = base[NB];
-    auto lb = [&](unsigned long long t) {
-        int lo = 0, hi = NB;
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (base[mid] < t) lo = mid + 1; else hi = mid; }
-        return base[lo];
-    };
-    range[2 * w] = lb((unsigned long long)E * w / W);
-    range[2 * w + 1] = (w == W - 1) ? E : lb((unsigned long long)E * (w + 1) / W);
+    const unsigned a = snap_group_start(ev, base, NB, (unsigned)((unsigned long long)E * r / W), lane);
+    const unsigned b = (r == W - 1) ? E
+                                    : snap_group_start(ev, base, NB, (unsigned)((unsigned long long)E * (r + 1) / W), lane);
+    if (lane == 0) {
+        range[2 * r] = a;
+        range[2 * r + 1] = b;
+    }
+}
+
+// Caller-written range bounds (any event offsets) moved to group starts, one
+// warp per bound; equal bounds move alike, so adjacent ranges stay adjacent.
+__global__ void k_snap_ranges(const unsigned *__restrict__ ev, const unsigned *__restrict__ base,
+                              const int *__restrict__ meta, int count, unsigned *__restrict__ range)
+{
+    const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (k >= count) return;
+    const unsigned v = snap_group_start(ev, base, meta[0] + 1, range[k], lane);
+    if (lane == 0) range[k] = v;
 }
 
 // ---------------------------------------------------------------- init
@@ -531,23 +571,30 @@ __device__ void cta_bitonic_u64(unsigned long long *a, int P)
     }
 }
 
-// Packed sort word: (key + 2^33) << 16 | point index; ascending words sort by
-// key (then index).  |key| <= 2^32 for int16 points.
-__device__ __forceinline__ unsigned long long order_word(long long key, int k)
+// Packed sort word of one point at the start slope: (key + 2^32) in bits
+// 63..31, (x + 2^15) in bits 30..15, point index in bits 14..0.  Ascending
+// words order the points by projection, then x ascending, then index: the
+// order just before the slope (a line of that slope lists its points by
+// increasing x).  For int16 points |key| < 2^32 and n <= 32768, so the
+// fields never overlap.
+__device__ __forceinline__ unsigned long long order_word(long long key, int x, int k)
 {
-    return ((unsigned long long)(key + (1LL << 33)) << 16) | (unsigned)k;
+    return ((unsigned long long)(key + (1LL << 32)) << 31) | ((unsigned long long)(unsigned)(x + 32768) << 15) |
+           (unsigned long long)(unsigned)k;
 }
-__device__ __forceinline__ long long word_key(unsigned long long w) { return (long long)(w >> 16) - (1LL << 33); }
+__device__ __forceinline__ long long word_key(unsigned long long w) { return (long long)(w >> 31) - (1LL << 32); }
+__device__ __forceinline__ int word_index(unsigned long long w) { return (int)(w & 0x7fffu); }
 
 __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy, int n, int h,
                                                      const unsigned *__restrict__ ev,
                                                      const unsigned *__restrict__ range, int W,
-                                                     const int *__restrict__ meta,
+                                                     int *__restrict__ meta_mut,
                                                      const unsigned *__restrict__ base,
                                                      unsigned short *__restrict__ orders,
                                                      unsigned long long *__restrict__ gsort,
                                                      Cand *__restrict__ cands)
 {
+    const int *meta = meta_mut;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_w[32];
     __shared__ int s_a[32];
@@ -558,6 +605,7 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
     const unsigned E = base[meta[0] + 1];
     const unsigned start = range[2 * w], end = range[2 * w + 1];
     const bool vertical = (E == 0 && w == 0);
+    if (w == 0 && threadIdx.x == 0) meta_mut[4] = 0;   // range counter of k_sweep
     if (start >= end && !vertical) {
         if (threadIdx.x == 0) cands[w] = cand_empty();
         return;
@@ -575,33 +623,18 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
     }
     __syncthreads();
     const int dy = s_slope[0], dx = s_slope[1];
-    for (int k = threadIdx.x; k < P; k += blockDim.x)
-        a[k] = k < n ? order_word(proj(xy[k], dy, dx), k) : ~0ull;
-    __syncthreads();
-    cta_bitonic_u64(a, P);
-    // runs of equal projections at the first slope: x ascending, then index
-    // (the order just before that slope)
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        const long long kq = word_key(a[q]);
-        if ((q > 0 && word_key(a[q - 1]) == kq) || q + 1 >= n || word_key(a[q + 1]) != kq) continue;
-        int r = q + 1;
-        while (r + 1 < n && word_key(a[r + 1]) == kq) ++r;
-        for (int u = q + 1; u <= r; ++u) {
-            const unsigned long long v = a[u];
-            const int xv = px(xy[v & 0xffffu]);
-            int t = u - 1;
-            while (t >= q) {
-                const int xt = px(xy[a[t] & 0xffffu]);
-                if (xt < xv || (xt == xv && (a[t] & 0xffffu) < (v & 0xffffu))) break;
-                a[t + 1] = a[t];
-                --t;
-            }
-            a[t + 1] = v;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        if (k < n) {
+            const int pk = xy[k];
+            a[k] = order_word(proj(pk, dy, dx), px(pk), k);
+        } else {
+            a[k] = ~0ull;
         }
     }
     __syncthreads();
+    cta_bitonic_u64(a, P);
     for (int k = threadIdx.x; k < n; k += blockDim.x)
-        orders[(size_t)w * n + k] = (unsigned short)(a[k] & 0xffffu);
+        orders[(size_t)w * n + k] = (unsigned short)word_index(a[k]);
     // every window at the first slope
     long long bw = KEY_INF;
     int ba = 0x7fffffff;
@@ -658,70 +691,207 @@ __device__ __forceinline__ int load_xy(const int *s_xy, const int *__restrict__ 
 __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 constexpr int RUN_LANE_MAX = 24;   // runs up to this length are handled by one lane
-constexpr unsigned HEAVY_MIN = 64; // groups at least this long are processed whole
-constexpr unsigned short MARK = 0x8000, START = 0x4000, IDMASK = 0x3fff;
 
-// A whole group of equal slopes [g0, g1) at once (n <= 16384, so point
-// indices leave the two top bits of an order entry free).  Every position
-// holding a point of the group is marked; each maximal block of marked
-// positions with equal projections is a run (points on one line of the
-// group's slope); the lane that owns a run's first position reverses it and
-// re-scores the window starting at the run and the window ending at it.
-// Three passes separated by warp barriers: mark, flag run starts, reverse.
-// No pass writes what another lane of the same pass reads, except mark bits
-// that never change a point index or a projection.
+// A whole group of one slope dy/dx in one pass over the positions, for
+// groups of about n/4 events or more.  Two points with equal projections at
+// the slope and different x are joined by an event of the group, so every
+// maximal block of two or more positions with equal projections is one line
+// of that slope (plus duplicates of its points, whose order is immaterial);
+// the group reverses exactly these blocks.  The warp slides a window of 32
+// positions over the order (lane l holds position p0 + l), compares each
+// key with its neighbours' by shuffles, and finds the blocks ending inside
+// the window; each is reversed by the whole warp and its two windows are
+// re-scored.  A block never reaches past its end, so the next window's
+// entries can be fetched before this window's blocks are rewritten.
 template <bool XY_SMEM>
-__device__ void heavy_group(unsigned short *order, unsigned short *pos, const int *s_xy,
-                            const int *__restrict__ g_xy, int n, int h, const unsigned *__restrict__ ev,
-                            unsigned g0, unsigned g1, int lane, Cand &best)
+__device__ void heavy_scan(unsigned short *order, unsigned short *pos, const int *s_xy,
+                           const int *__restrict__ g_xy, int n, int h, int dy, int dx, unsigned gmin, int lane,
+                           Cand &best)
+{
+    auto XY = [&](int k) { return load_xy<XY_SMEM>(s_xy, g_xy, k); };
+    Cand c;
+    c.dy = dy; c.dx = dx; c.i = (int)(gmin >> 16); c.j = (int)(gmin & 0xffffu);
+    int open = -1;                 // start of a block still open at p0 (warp-uniform)
+    long long kprev = 0;           // key at p0 - 1 (p0 > 0)
+    int idx = lane < n ? order[lane] : 0;
+    int nidx = 32 + lane < n ? order[32 + lane] : 0;
+    int p32 = 32 < n ? order[32] : 0;
+    for (int p0 = 0; p0 < n; p0 += 32) {
+        const int p = p0 + lane;
+        const long long k = p < n ? proj(XY(idx), dy, dx) : 0;
+        const long long k32 = p0 + 32 < n ? proj(XY(p32), dy, dx) : 0;
+        // prefetch the next window (its entries are not rewritten below)
+        idx = nidx;
+        nidx = p0 + 64 + lane < n ? order[p0 + 64 + lane] : 0;
+        p32 = p0 + 64 < n ? order[p0 + 64] : 0;
+        long long kn = __shfl_down_sync(FULL, k, 1);
+        if (lane == 31) kn = k32;
+        long long kp = __shfl_up_sync(FULL, k, 1);
+        if (lane == 0) kp = kprev;
+        const bool eq_next = p + 1 < n && kn == k;
+        const bool eq_prev = p > 0 && p < n && kp == k;
+        unsigned starts = __ballot_sync(FULL, eq_next && !eq_prev);
+        unsigned ends = __ballot_sync(FULL, eq_prev && !eq_next);
+        while (ends) {
+            const int el = __ffs(ends) - 1;
+            ends &= ends - 1;
+            const unsigned before = starts & ((2u << el) - 1u);
+            int s0;
+            if (before) {
+                const int sl = 31 - __clz(before);
+                s0 = p0 + sl;
+                starts &= ~(1u << sl);
+            } else {
+                s0 = open;
+            }
+            const int e0 = p0 + el;
+            open = -1;
+            if (s0 < 0) continue;   // an end always follows its start; never taken
+            const long long K = __shfl_sync(FULL, k, el);
+            const int len = e0 - s0 + 1;
+            for (int t = lane; t < len / 2; t += 32) {
+                const unsigned short u = order[s0 + t], v = order[e0 - t];
+                order[s0 + t] = v;
+                order[e0 - t] = u;
+            }
+            __syncwarp();
+            for (int t = lane; t < len; t += 32) pos[order[s0 + t]] = (unsigned short)(s0 + t);
+            if (lane == 0) {
+                if (s0 + h - 1 < n) {
+                    const long long kt = proj(XY(order[s0 + h - 1]), dy, dx);
+                    c.w = kt - K; c.t = K + kt;
+                    if (cand_better(c, best)) best = c;
+                }
+                if (e0 - h + 1 >= 0) {
+                    const long long kb = proj(XY(order[e0 - h + 1]), dy, dx);
+                    c.w = K - kb; c.t = kb + K;
+                    if (cand_better(c, best)) best = c;
+                }
+            }
+            __syncwarp();
+        }
+        if (starts) open = p0 + 31 - __clz(starts);
+        kprev = __shfl_sync(FULL, k, 31);
+    }
+    __syncwarp();
+}
+
+// Slope of event e as (dy, dx), dx > 0.
+template <bool XY_SMEM>
+__device__ __forceinline__ void event_slope(const int *s_xy, const int *__restrict__ g_xy, unsigned e, int &dy,
+                                            int &dx)
+{
+    pair_slope(load_xy<XY_SMEM>(s_xy, g_xy, ev_i(e)), load_xy<XY_SMEM>(s_xy, g_xy, ev_j(e)), dy, dx);
+}
+
+// End of the group of equal slopes dy0/dx0 that starts at g0 and holds at
+// least the events [g0, known).  Events are in slope order, so "same slope"
+// holds on [g0, g1) and fails on [g1, end): a galloping search (lane l
+// probes known + 32 (2^l - 1)), then 33-way bisections, all lanes at once.
+template <bool XY_SMEM>
+__device__ unsigned group_end(const int *s_xy, const int *__restrict__ g_xy, const unsigned *__restrict__ ev,
+                              unsigned known, unsigned end, int dy0, int dx0, int lane)
+{
+    auto same = [&](unsigned q) {
+        int dy, dx;
+        event_slope<XY_SMEM>(s_xy, g_xy, ev[q], dy, dx);
+        return (long long)dy * dx0 == (long long)dy0 * dx;
+    };
+    // lo: last index known inside the group; hi: first index known outside
+    unsigned lo = known - 1, hi = end;
+    {
+        const unsigned long long off = 32ull * ((1ull << lane) - 1ull);
+        const unsigned long long q = (unsigned long long)known + off;
+        const bool in = q < hi && same((unsigned)q);
+        const unsigned bal = __ballot_sync(FULL, in);
+        const unsigned out = __ballot_sync(FULL, q < hi && !in);
+        if (bal) lo = (unsigned)(known + 32ull * ((1ull << (31 - __clz(bal))) - 1ull));
+        if (out) hi = (unsigned)(known + 32ull * ((1ull << (__ffs(out) - 1)) - 1ull));
+    }
+    while (hi - lo > 1) {
+        const unsigned span = hi - lo;
+        const unsigned q = lo + (unsigned)(((unsigned long long)span * (lane + 1)) / 33);
+        const bool valid = q > lo && q < hi;
+        const bool in = valid && same(q);
+        const unsigned bal = __ballot_sync(FULL, in);
+        const unsigned out = __ballot_sync(FULL, valid && !in);
+        if (bal) lo = __shfl_sync(FULL, q, 31 - __clz(bal));
+        if (out) hi = __shfl_sync(FULL, q, __ffs(out) - 1);
+        if (!bal && !out) break;   // span < 33 with no probe strictly inside: cannot happen for span > 1
+    }
+    return hi;
+}
+
+// A whole group of equal slopes [g0, g1) in work proportional to its
+// length (any n).  In the order just before the slope, the points of each
+// line of that slope fill a block of consecutive positions (they project
+// alike), x ascending.  Exactly one event of the group joins the block's
+// first point a to the first point above it with a larger x; the lane that
+// reads that event reverses the block (the order just after the slope) and
+// re-scores the window starting at the block and the window ending at it.
+// Events are examined 32 at a time (reads only, then a warp barrier), then
+// the claiming lanes rewrite their blocks (disjoint) and the warp waits
+// again.  An event whose block was reversed earlier sees b below a and is
+// skipped.  The window-end keys read during the rewrites do not depend on
+// the order inside other blocks: all points of a block project alike.
+template <bool XY_SMEM>
+__device__ void group_claims(unsigned short *order, unsigned short *pos, const int *s_xy,
+                             const int *__restrict__ g_xy, int n, int h, const unsigned *__restrict__ ev,
+                             unsigned g0, unsigned g1, int lane, Cand &best)
 {
     auto XY = [&](int k) { return load_xy<XY_SMEM>(s_xy, g_xy, k); };
     const unsigned e0 = ev[g0];
     int dy, dx;
     pair_slope(XY(ev_i(e0)), XY(ev_j(e0)), dy, dx);
-    const unsigned gmin = ((unsigned)ev_i(e0) << 16) | (unsigned)ev_j(e0);
-    for (unsigned q = g0 + lane; q < g1; q += 32) {
-        const unsigned e = ev[q];
-        order[pos[ev_i(e)]] |= MARK;
-        order[pos[ev_j(e)]] |= MARK;
-    }
-    __syncwarp();
-    const int chunk = (n + 31) / 32;
-    const int c0 = lane * chunk, c1 = min(n, c0 + chunk);
-    auto key_at = [&](int p) { return proj(XY(order[p] & IDMASK), dy, dx); };
-    for (int p = c0; p < c1; ++p) {
-        if (!(order[p] & MARK)) continue;
-        const long long K = key_at(p);
-        if (p > 0 && (order[p - 1] & MARK) && key_at(p - 1) == K) continue;
-        order[p] |= START;
-    }
-    __syncwarp();
-    for (int p = c0; p < c1; ++p) {
-        if (!(order[p] & START)) continue;
-        const long long K = key_at(p);
-        int q = p;
-        while (q + 1 < n && (order[q + 1] & MARK) && key_at(q + 1) == K) ++q;
-        for (int u = p, v = q; u <= v; ++u, --v) {
-            const unsigned short ou = order[u] & IDMASK, ov = order[v] & IDMASK;
-            order[u] = ov;
-            order[v] = ou;
-            pos[ov] = (unsigned short)u;
-            pos[ou] = (unsigned short)v;
+    Cand c;
+    c.dy = dy; c.dx = dx; c.i = ev_i(e0); c.j = ev_j(e0);
+    unsigned e_next = (g0 + lane < g1) ? ev[g0 + lane] : 0u;
+    for (unsigned c0 = g0; c0 < g1; c0 += 32) {
+        const unsigned q = c0 + lane;
+        const unsigned e = e_next;
+        e_next = (q + 32 < g1) ? ev[q + 32] : 0u;
+        bool claim = false;
+        int pa = 0, pb = 0;
+        long long K = 0;
+        if (q < g1) {
+            int Pa = XY(ev_i(e)), Pb = XY(ev_j(e));
+            int a = ev_i(e), b = ev_j(e);
+            if (px(Pa) > px(Pb)) {
+                const int t = a; a = b; b = t;
+                const int tp = Pa; Pa = Pb; Pb = tp;
+            }
+            pa = pos[a];
+            pb = pos[b];
+            if (pa < pb) {
+                K = proj(Pa, dy, dx);
+                claim = (pa == 0 || proj(XY(order[pa - 1]), dy, dx) != K) &&
+                        (pb == pa + 1 || px(XY(order[pb - 1])) == px(Pa));
+            }
         }
-        Cand c;
-        c.dy = dy; c.dx = dx; c.i = (int)(gmin >> 16); c.j = (int)(gmin & 0xffffu);
-        if (p + h - 1 < n) {
-            const long long kt = proj(XY(order[p + h - 1] & IDMASK), dy, dx);
-            c.w = kt - K; c.t = K + kt;
-            if (cand_better(c, best)) best = c;
+        __syncwarp();
+        if (claim) {
+            int hi = pb;
+            while (hi + 1 < n && proj(XY(order[hi + 1]), dy, dx) == K) ++hi;
+            for (int u = pa, v = hi; u < v; ++u, --v) {
+                const unsigned short ou = order[u], ov = order[v];
+                order[u] = ov;
+                order[v] = ou;
+                pos[ov] = (unsigned short)u;
+                pos[ou] = (unsigned short)v;
+            }
+            if (pa + h - 1 < n) {
+                const long long kt = proj(XY(order[pa + h - 1]), dy, dx);
+                c.w = kt - K; c.t = K + kt;
+                if (cand_better(c, best)) best = c;
+            }
+            if (hi - h + 1 >= 0) {
+                const long long kb = proj(XY(order[hi - h + 1]), dy, dx);
+                c.w = K - kb; c.t = kb + K;
+                if (cand_better(c, best)) best = c;
+            }
         }
-        if (q - h + 1 >= 0) {
-            const long long kb = proj(XY(order[q - h + 1] & IDMASK), dy, dx);
-            c.w = K - kb; c.t = kb + K;
-            if (cand_better(c, best)) best = c;
-        }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
 // One warp per sweeper; each lane takes one of up to 32 consecutive events.
@@ -751,10 +921,12 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
                                                const unsigned *__restrict__ ev,
                                                const unsigned *__restrict__ range, int W,
                                                const unsigned short *__restrict__ orders,
-                                               Cand *__restrict__ cands, int *__restrict__ err)
+                                               Cand *__restrict__ cands, int *__restrict__ meta)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    int *err = meta + 3;
+    unsigned *next_range = reinterpret_cast<unsigned *>(meta + 4);
     int *s_xy = reinterpret_cast<int *>(smem);
     const size_t off0 = XY_SMEM ? align16((size_t)n * 4) : 0;
     const size_t half = align16((size_t)n * 2);
@@ -764,11 +936,11 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
         for (int k = threadIdx.x; k < n; k += blockDim.x) s_xy[k] = g_xy[k];
         __syncthreads();
     }
-    const int w = blockIdx.x * nwarp + warp;
-    if (w >= W) return;
-    const unsigned start = range[2 * w], end = range[2 * w + 1];
+    const int g = blockIdx.x * nwarp + warp;   // this sweeping warp
+    // the residue test of the conflict check needs h - 1 >= 8 and n <= 3 (h - 1)
+    const int H = h - 1;
+    const bool fold_ok = H >= 8 && n <= 3 * H;
     auto XY = [&](int k) { return load_xy<XY_SMEM>(s_xy, g_xy, k); };
-    const bool HEAVY_OK = n <= (int)IDMASK + 1;
     Cand best = cand_empty();
     auto offer = [&](long long wd, long long t, int dy, int dx, unsigned pr) {
         // cheap reject on the width alone before the full lexicographic test
@@ -778,7 +950,15 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
         c.i = (int)(pr >> 16); c.j = (int)(pr & 0xffffu);
         if (cand_better(c, best)) best = c;
     };
-    if (start < end) {
+    // ranges are taken in slope order from a shared counter until none is left
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(next_range, 1u);
+        w = __shfl_sync(FULL, w, 0);
+        if (w >= (unsigned)W) break;
+        const unsigned start = range[2 * w], end = range[2 * w + 1];
+        if (start >= end) continue;
+        __syncwarp();
         for (int a = lane; a < n; a += 32) {
             const unsigned short p = orders[(size_t)w * n + a];
             order[a] = p;
@@ -786,6 +966,7 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
         }
         __syncwarp();
         const unsigned lanemask_le = 0xffffffffu >> (31 - lane);
+        const unsigned lanemask_lt = lanemask_le >> 1;
         unsigned carried = 0xffffffffu;   // smallest pair of the group open at k
         unsigned k = start;
         unsigned e_cur = (k + lane < end) ? ev[k + lane] : 0u;
@@ -797,24 +978,22 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
             const bool is_start = valid && !ev_cont(e);
             const unsigned smask = __ballot_sync(FULL, is_start);
             // ---- a long group of one slope starting here: process it whole
-            if (HEAVY_OK && smask == 1u && navail == 32u && __shfl_sync(FULL, ev_cont(e_nxt) ? 1 : 0, 0)) {
-                unsigned g1 = k + 33;
-                for (;;) {
-                    const unsigned q = g1 + lane;
-                    const bool c = q < end && ev_cont(ev[q]);
-                    const unsigned bal = __ballot_sync(FULL, c);
-                    if (bal == FULL) { g1 += 32; continue; }
-                    g1 += __ffs(~bal) - 1;
-                    break;
-                }
-                if (g1 - k >= HEAVY_MIN) {
-                    heavy_group<XY_SMEM>(order, pos, s_xy, g_xy, n, h, ev, k, g1, lane, best);
-                    carried = 0xffffffffu;
-                    k = g1;
-                    e_cur = (k + lane < end) ? ev[k + lane] : 0u;
-                    e_nxt = (k + 32 + lane < end) ? ev[k + 32 + lane] : 0u;
-                    continue;
-                }
+            if (smask == 1u && navail == 32u && __shfl_sync(FULL, ev_cont(e_nxt) ? 1 : 0, 0)) {
+                const unsigned e0 = __shfl_sync(FULL, e, 0);
+                int gdy, gdx;
+                event_slope<XY_SMEM>(s_xy, g_xy, e0, gdy, gdx);
+                const unsigned g1 = group_end<XY_SMEM>(s_xy, g_xy, ev, k + 33, end, gdy, gdx, lane);
+                // one pass over the positions pays off for groups of about n/4 events or more
+                if (g1 - k >= (unsigned)n / 4)
+                    heavy_scan<XY_SMEM>(order, pos, s_xy, g_xy, n, h, gdy, gdx,
+                                        ((unsigned)ev_i(e0) << 16) | (unsigned)ev_j(e0), lane, best);
+                else
+                    group_claims<XY_SMEM>(order, pos, s_xy, g_xy, n, h, ev, k, g1, lane, best);
+                carried = 0xffffffffu;
+                k = g1;
+                e_cur = (k + lane < end) ? ev[k + lane] : 0u;
+                e_nxt = (k + 32 + lane < end) ? ev[k + 32 + lane] : 0u;
+                continue;
             }
             const unsigned le = smask & lanemask_le;
             const int gfirst = le ? 31 - __clz(le) : -1;
@@ -824,19 +1003,31 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
             // ---- analysis (reads only)
             int a = ev_i(e), b = ev_j(e);
             int Pa = XY(a), Pb = XY(b);
+            int pa = valid ? pos[a] : 0, pb = valid ? pos[b] : 0;
             if (px(Pa) > px(Pb)) {
                 const int t = a; a = b; b = t;
                 const int tp = Pa; Pa = Pb; Pb = tp;
+                const int tq = pa; pa = pb; pb = tq;
             }
             const int dx = px(Pb) - px(Pa), dy = py(Pb) - py(Pa);
-            const int pa = valid ? pos[a] : 0, pb = valid ? pos[b] : 0;
             const bool done = valid && pb < pa;
+            const bool live = valid && !done;
             const long long K = proj(Pa, dy, dx);
+            // outer neighbours and, for a simple swap, the two window ends, all
+            // read at once
+            const int top0 = pa + h - 1, bot0 = pb - h + 1;
+            const bool rd_t = live && top0 < n && top0 > pb, rd_b = live && bot0 >= 0 && bot0 < pa;
+            const int i_lo = (live && pa > 0) ? order[pa - 1] : 0;
+            const int i_hi = (live && pb < n - 1) ? order[pb + 1] : 0;
+            const int i_t = rd_t ? order[top0] : 0;
+            const int i_b = rd_b ? order[bot0] : 0;
+            const bool lo_eq = live && pa > 0 && proj(XY(i_lo), dy, dx) == K;
+            const bool hi_eq = live && pb < n - 1 && proj(XY(i_hi), dy, dx) == K;
+            long long kt = rd_t ? proj(XY(i_t), dy, dx) : K;
+            long long kb = rd_b ? proj(XY(i_b), dy, dx) : K;
             int lo = pa, hi = pb;
             bool simple = false, run = false, longrun = false, interior_bad = false;
-            if (valid && !done) {
-                const bool lo_eq = pa > 0 && proj(XY(order[pa - 1]), dy, dx) == K;
-                const bool hi_eq = pb < n - 1 && proj(XY(order[pb + 1]), dy, dx) == K;
+            if (live) {
                 if (pb == pa + 1 && !lo_eq && !hi_eq) {
                     simple = true;
                 } else {
@@ -854,6 +1045,10 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
                     // this batch is still to move a point in between, the lane waits
                     for (int q = pa + 1; q < pb && !longrun; ++q)
                         if (proj(XY(order[q]), dy, dx) != K) { interior_bad = true; break; }
+                    // window ends of the whole run
+                    const int top = lo + h - 1, bot = hi - h + 1;
+                    kt = (top < n && top > hi) ? proj(XY(order[top]), dy, dx) : K;
+                    kb = (bot >= 0 && bot < lo) ? proj(XY(order[bot]), dy, dx) : K;
                 }
             }
             // one leader per run: the lowest lane with the same group and run start
@@ -864,9 +1059,40 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
             const bool leader = run && !longrun && lane == __ffs(peers) - 1;
             const bool act = simple || leader;
             // ---- conflicts with earlier active lanes of other groups
-            const unsigned me = act ? (((unsigned)lo << 16) | ((unsigned)(hi - lo) << 6) | (unsigned)(gfirst + 1)) : 0xffffffffu;
+            // A later lane must not read a position an earlier lane of another
+            // slope rewrites: its outer neighbours [lo - 1, hi + 1] and its window
+            // ends lo + h - 1, hi - h + 1.  (Lanes of one slope never disturb each
+            // other: they rewrite disjoint runs and the keys they read do not
+            // depend on the order inside a run.)
+            const unsigned actm = __ballot_sync(FULL, act);
+            const unsigned runm = __ballot_sync(FULL, act && !simple);
             bool conflict = false;
-            {
+            if (runm == 0 && fold_ok) {
+                // All active lanes are simple swaps [p, p + 1].  With H = h - 1,
+                // earlier e and later l conflict only if e - l lies in [-2, 2]
+                // (neighbours), [H - 1, H] (l's window top) or [-H, 1 - H] (l's
+                // window bottom): in every case e - l = -2..2 modulo H.  So the
+                // residues f = p mod H of conflicting lanes are within 2 of each
+                // other, cyclically, and then share a cell of width 4 in one of
+                // three grids: f / 4, (f + 2) / 4, ((f + 2) mod H) / 4 (the last
+                // catches pairs across the wrap).  Lanes sharing a cell are
+                // treated as conflicting: a superset, so the cut stays safe.
+                int f = pa;
+                if (f >= H) f -= H;
+                if (f >= H) f -= H;
+                int f2 = f + 2;
+                const unsigned none = 0x40000000u | (unsigned)lane;
+                const unsigned cA = act ? (unsigned)(f >> 2) : none;
+                const unsigned cB = act ? (unsigned)(f2 >> 2) : none;
+                if (f2 >= H) f2 -= H;
+                const unsigned cC = act ? (unsigned)(f2 >> 2) : none;
+                const unsigned grp = __match_any_sync(FULL, (unsigned)(gfirst + 1));
+                const unsigned nearm = __match_any_sync(FULL, cA) | __match_any_sync(FULL, cB) |
+                                       __match_any_sync(FULL, cC);
+                conflict = act && (nearm & actm & ~grp & lanemask_lt) != 0u;
+            } else {
+                const unsigned me = act ? (((unsigned)lo << 16) | ((unsigned)(hi - lo) << 6) | (unsigned)(gfirst + 1))
+                                        : 0xffffffffu;
                 const int top = lo + h - 1, bot = hi - h + 1;
                 for (int t = 0; t < 31; ++t) {
                     const unsigned o = __shfl_sync(FULL, me, t);
@@ -877,17 +1103,16 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
                 }
             }
             const unsigned bad = __ballot_sync(FULL, longrun || interior_bad || conflict);
-            const int cut = bad ? __ffs(bad) - 1 : (int)navail;
+            int cut = bad ? __ffs(bad) - 1 : (int)navail;
+            // a group that starts inside the batch and runs past its end is left
+            // to the next batch, which processes it whole
+            if (smask > 1u && navail == 32u && __shfl_sync(FULL, ev_cont(e_nxt) ? 1 : 0, 0))
+                cut = min(cut, 31 - __clz(smask));
             int advance;
             if (cut > 0) {
                 // ---- parallel events: window reads, then the rewrites
                 const bool go = act && lane < cut;
-                long long kt = K, kb = K;
                 const int top = lo + h - 1, bot = hi - h + 1;
-                if (go) {
-                    if (top < n && top > hi) kt = proj(XY(order[top]), dy, dx);
-                    if (bot >= 0 && bot < lo) kb = proj(XY(order[bot]), dy, dx);
-                }
                 __syncwarp();
                 if (go) {
                     if (simple) {
@@ -971,7 +1196,7 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
         }
     }
     best = warp_best(best);
-    if (lane == 0) cands[W + w] = best;
+    if (lane == 0) cands[W + g] = best;
 }
 
 }  // namespace
@@ -979,24 +1204,51 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
 // ---------------------------------------------------------------- host side
 static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Shared memory of one sweep CTA: the points (when kept on chip) plus the
+// order and position arrays of each of its sweeping warps.
+static size_t sweep_smem_bytes(int n, bool xy_smem, int spb)
+{
+    const size_t per = 2 * (((size_t)n * 2 + 15) / 16 * 16);
+    const size_t xyb = xy_smem ? ((size_t)n * 4 + 15) / 16 * 16 : 0;
+    return xyb + per * spb;
+}
+
 void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int want_b)
 {
     p.n = n;
     p.h = h;
     p.emax = (long long)n * (n - 1) / 2;
     p.xy_smem = n <= 16384;
-    // sweepers per CTA limited by shared memory (order + pos + bitmap each)
+    // sweeping warps per CTA limited by shared memory (order + pos each)
     const size_t per = 2 * (((size_t)n * 2 + 15) / 16 * 16);
     const size_t xyb = p.xy_smem ? ((size_t)n * 4 + 15) / 16 * 16 : 0;
     const size_t cap = 227 * 1024;
     int spb = (int)((cap - xyb) / per);
     spb = spb < 1 ? 1 : (spb > 8 ? 8 : spb);
     p.spb = spb;
-    long long w = want_w > 0 ? want_w : (long long)sms * spb;
-    const long long by_events = p.emax / 1024 + 1;      // at least ~1K events per sweeper
+    // resident sweep CTAs per SM (the sweep kernel is persistent)
+    const size_t sw_smem = sweep_smem_bytes(n, p.xy_smem, spb);
+    int per_sm = 0;
+    if (p.xy_smem) {
+        cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<true>, 32 * spb, sw_smem);
+    } else {
+        cudaFuncSetAttribute(k_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<false>, 32 * spb, sw_smem);
+    }
+    cudaGetLastError();
+    if (per_sm < 1) per_sm = 1;
+    const long long g_full = (long long)sms * per_sm * spb;
+    // slope ranges: RANGE_FACTOR per sweeping warp, handed out dynamically, at
+    // least MIN_RANGE_EVENTS events each so that a range's start sort pays off
+    long long w = want_w > 0 ? want_w : RANGE_FACTOR * g_full;
+    const long long by_events = p.emax / MIN_RANGE_EVENTS + 1;
     if (want_w <= 0 && w > by_events) w = by_events;
     if (w < 1) w = 1;
     p.W = (int)w;
+    long long blocks = (w + spb - 1) / spb;
+    if (blocks > (long long)sms * per_sm) blocks = (long long)sms * per_sm;
+    p.G = (int)(blocks * spb);
     // buckets: ~4K events each, at least 8 samples per bucket
     long long B = want_b > 0 ? want_b : p.emax / 4096 + 1;
     if (B > BND_MAX / 2) B = BND_MAX / 2;
@@ -1028,7 +1280,7 @@ size_t sweep_plan_bytes(int n, int W, int C, int S)
     b += a256((size_t)2 * W * 4);
     b += a256((size_t)W * n * 2);
     b += (n > SORT_SMEM_N) ? a256((size_t)W * P * 8) : 0;
-    b += a256((size_t)2 * W * sizeof(Cand));
+    b += a256((size_t)(2 * W + 8) * sizeof(Cand));
     return b;
 }
 
@@ -1051,7 +1303,7 @@ void sweep_plan_carve(SweepPlan &p, void *ws)
     p.range = (unsigned *)take((size_t)2 * p.W * 4);
     p.orders = (unsigned short *)take((size_t)p.W * p.n * 2);
     p.gsort = (p.n > SORT_SMEM_N) ? (unsigned long long *)take((size_t)p.W * P * 8) : nullptr;
-    p.cands = (Cand *)take((size_t)2 * p.W * sizeof(Cand));
+    p.cands = (Cand *)take((size_t)(2 * p.W + 8) * sizeof(Cand));
 }
 
 const long long *sorted_sample(const SweepPlan &p)
@@ -1097,7 +1349,11 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
         StageTimer _t(STAGE_SEGSORT_BIG, st);
         k_segsort_big<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, p.ev2, p.base, p.meta, p.oversize);
     }
-    if (plan) { StageTimer _t(STAGE_PLAN, st); k_plan<<<(p.W + 255) / 256, 256, 0, st>>>(p.base, p.meta, p.W, p.range); }
+    {
+        StageTimer _t(STAGE_PLAN, st);
+        if (plan) k_plan<<<(p.W + 7) / 8, 256, 0, st>>>(p.ev, p.base, p.meta, p.W, p.range);
+        else k_snap_ranges<<<(2 * p.W + 7) / 8, 256, 0, st>>>(p.ev, p.base, p.meta, 2 * p.W, p.range);
+    }
     return cudaGetLastError();
 }
 
@@ -1125,18 +1381,16 @@ cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, c
         k_sweep_init<<<p.W, 1024, init_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.meta, p.base, p.orders,
                                                   p.gsort, p.cands);
     }
-    const size_t per = 2 * (((size_t)n * 2 + 15) / 16 * 16);
-    const size_t xyb = p.xy_smem ? ((size_t)n * 4 + 15) / 16 * 16 : 0;
-    const size_t sw_smem = xyb + per * p.spb;
-    const int blocks = (p.W + p.spb - 1) / p.spb;
+    const size_t sw_smem = sweep_smem_bytes(n, p.xy_smem, p.spb);
+    const int blocks = p.G / p.spb;
     if (p.xy_smem) {
         cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
         StageTimer _t(STAGE_SWEEP, st);
-        k_sweep<true><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta + 3);
+        k_sweep<true><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta);
     } else {
         cudaFuncSetAttribute(k_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
         StageTimer _t(STAGE_SWEEP, st);
-        k_sweep<false><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta + 3);
+        k_sweep<false><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta);
     }
     return cudaGetLastError();
 }
