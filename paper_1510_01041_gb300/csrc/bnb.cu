@@ -113,9 +113,12 @@ __global__ void __launch_bounds__(1024) k_score_dyadic(const int *__restrict__ x
         }
         long long *a = in_smem ? reinterpret_cast<long long *>(smem) : gscratch + (size_t)blockIdx.x * 2 * P;
         const int xc = *xcp;
-        for (int k = threadIdx.x; k < P; k += blockDim.x) a[k] = k < n ? zscaled(xy[k], xc, K) : I64_MAX;
-        __syncthreads();
-        cta_bitonic_i64(a, P);
+        auto z = [&](int k) { return k < n ? zscaled(xy[k], xc, K) : I64_MAX; };
+        if (!in_smem || !cta_fill_sort_any(a, P < (int)blockDim.x ? (int)blockDim.x : P, z)) {
+            for (int k = threadIdx.x; k < P; k += blockDim.x) a[k] = z(k);
+            __syncthreads();
+            cta_bitonic_i64(a, P);
+        }
         const long long w = cta_min_window(a, a, n, h);
         if (threadIdx.x == 0) out[q] = w;
         __syncthreads();
@@ -141,22 +144,25 @@ __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, in
             if (threadIdx.x == 0) { prune[q] = 0; lb_out[q] = 0; }
             continue;
         }
+        const int Ps = (in_smem && P < (int)blockDim.x) ? (int)blockDim.x : P;
         long long *lo = in_smem ? reinterpret_cast<long long *>(smem) : gscratch + (size_t)blockIdx.x * 2 * P;
-        long long *hi = lo + P;
+        long long *hi = lo + Ps;
         const int xc = *xcp;
-        for (int k = threadIdx.x; k < P; k += blockDim.x) {
-            if (k < n) {
-                const long long z1 = zscaled(xy[k], xc, Klo), z2 = zscaled(xy[k], xc, Khi);
-                lo[k] = min(z1, z2);
-                hi[k] = max(z1, z2);
-            } else {
-                lo[k] = I64_MAX;
-                hi[k] = I64_MAX;
+        auto zlo = [&](int k) {
+            return k < n ? min(zscaled(xy[k], xc, Klo), zscaled(xy[k], xc, Khi)) : I64_MAX;
+        };
+        auto zhi = [&](int k) {
+            return k < n ? max(zscaled(xy[k], xc, Klo), zscaled(xy[k], xc, Khi)) : I64_MAX;
+        };
+        if (!in_smem || !cta_fill_sort_any(lo, Ps, zlo) || !cta_fill_sort_any(hi, Ps, zhi)) {
+            for (int k = threadIdx.x; k < P; k += blockDim.x) {
+                lo[k] = zlo(k);
+                hi[k] = zhi(k);
             }
+            __syncthreads();
+            cta_bitonic_i64(lo, P);
+            cta_bitonic_i64(hi, P);
         }
-        __syncthreads();
-        cta_bitonic_i64(lo, P);
-        cta_bitonic_i64(hi, P);
         long long lb = cta_min_window(lo, hi, n, h);
         if (lb < 0) lb = 0;
         if (threadIdx.x == 0) {
@@ -302,8 +308,9 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         StageTimer _t(STAGE_OTHER, st);
         k_pick_seeds<<<1, 128, 0, st>>>(sorted_sample(p), p.S, pred_dev, seed_mode, BNB_SEEDS, seed_keys);
     }
-    const size_t one_sort = (n <= SORT_SMEM_N) ? (size_t)P * 8 : 0;
-    const size_t two_sorts = (n <= SORT_SMEM_N) ? (size_t)2 * P * 8 : 0;
+    const int Ps = P < 1024 ? 1024 : P;   // the shared-memory sorts fill whole 1024-thread CTAs
+    const size_t one_sort = (n <= SORT_SMEM_N) ? (size_t)Ps * 8 : 0;
+    const size_t two_sorts = (n <= SORT_SMEM_N) ? (size_t)2 * Ps * 8 : 0;
     cudaFuncSetAttribute(k_score_dyadic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one_sort);
     cudaFuncSetAttribute(k_node_lb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_sorts);
     {

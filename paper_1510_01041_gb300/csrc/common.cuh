@@ -146,4 +146,92 @@ __device__ __forceinline__ void pair_decode(long long p, int &i, int &j)
     i = (int)(p - (long long)jj * (jj - 1) / 2);
 }
 
+// Ascending bitonic sort of P = IPT * blockDim.x words, held IPT per thread
+// in v (thread t holds positions t IPT .. t IPT + IPT - 1).  A step whose
+// partner position (position ^ j) lies in the same thread runs in registers,
+// one whose partner lies in another lane of the warp runs by shuffles, and
+// only steps across warps pass through the shared scratch s (P words).  For
+// the pair at positions i < i ^ j of merge size k the smaller value goes to
+// i when i & k == 0 and to i ^ j otherwise.  Every thread of the CTA calls
+// it; s may be reused once it returns.
+template <int IPT, class T>
+__device__ __forceinline__ void cta_sort_blocked(T (&v)[IPT], T *s, int P)
+{
+    const int t = threadIdx.x, lane = t & 31;
+    const int base = t * IPT;
+    for (int k = 2; k <= P; k <<= 1) {
+        int j = k >> 1;
+        if (j >= 32 * IPT) {
+#pragma unroll
+            for (int r = 0; r < IPT; ++r) s[base + r] = v[r];
+            __syncthreads();
+            for (; j >= 32 * IPT; j >>= 1) {
+                for (int q = t; q < P / 2; q += blockDim.x) {
+                    const int i = 2 * q - (q & (j - 1)), l = i + j;
+                    const bool up = (i & k) == 0;
+                    const T a = s[i], b = s[l];
+                    if ((a > b) == up) { s[i] = b; s[l] = a; }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int r = 0; r < IPT; ++r) v[r] = s[base + r];
+            __syncthreads();
+        }
+        for (; j >= IPT; j >>= 1) {
+            const int m = j / IPT;
+            const bool lower = (lane & m) == 0;
+#pragma unroll
+            for (int r = 0; r < IPT; ++r) {
+                const T o = __shfl_xor_sync(FULL, v[r], m);
+                const bool up = ((base + r) & k) == 0;
+                v[r] = (lower == up) ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
+            }
+        }
+#pragma unroll
+        for (int jj = IPT / 2; jj >= 1; jj >>= 1) {
+            if (jj < k) {
+#pragma unroll
+                for (int r = 0; r < IPT; ++r) {
+                    if ((r & jj) == 0) {
+                        const bool up = ((base + r) & k) == 0;
+                        const T a = v[r], b = v[r ^ jj];
+                        if ((a > b) == up) { v[r] = b; v[r ^ jj] = a; }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Fills P = IPT * blockDim.x words with fill(position), sorts them and
+// leaves the ascending result in s.
+template <int IPT, class T, class F>
+__device__ __forceinline__ void cta_fill_sort(T *s, int P, F fill)
+{
+    T v[IPT];
+    const int base = threadIdx.x * IPT;
+#pragma unroll
+    for (int r = 0; r < IPT; ++r) v[r] = fill(base + r);
+    cta_sort_blocked<IPT>(v, s, P);
+#pragma unroll
+    for (int r = 0; r < IPT; ++r) s[base + r] = v[r];
+    __syncthreads();
+}
+
+// The same for P / blockDim.x in {1, 2, 4, 8, 16} (P a power of two, at least
+// blockDim.x); returns false (nothing done) for other sizes.
+template <class T, class F>
+__device__ bool cta_fill_sort_any(T *s, int P, F fill)
+{
+    switch (P / (int)blockDim.x) {
+        case 1: cta_fill_sort<1>(s, P, fill); return true;
+        case 2: cta_fill_sort<2>(s, P, fill); return true;
+        case 4: cta_fill_sort<4>(s, P, fill); return true;
+        case 8: cta_fill_sort<8>(s, P, fill); return true;
+        case 16: cta_fill_sort<16>(s, P, fill); return true;
+        default: return false;
+    }
+}
+
 }  // namespace lms

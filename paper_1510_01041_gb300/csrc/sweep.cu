@@ -351,6 +351,27 @@ __global__ void __launch_bounds__(1024) k_segsort(const void *__restrict__ xy, u
         }
         int P = 1;
         while (P < (int)m) P <<= 1;
+        // An interior bucket holds keys in [bnd[b - 1], bnd[b]); when that span
+        // is below 2^32, (key - bnd[b - 1]) << 32 | pair is one word that
+        // orders events by (key, pair), sorted in registers.
+        if (b > 0 && b < NB - 1 && (unsigned long long)(bnd[b] - bnd[b - 1]) <= 0xffffffffull) {
+            const long long klo = bnd[b - 1];
+            unsigned long long *w = reinterpret_cast<unsigned long long *>(smem);
+            auto word = [&](int k) {
+                if (k >= (int)m) return ~0ull;
+                const unsigned e = ev[off + k];
+                return ((unsigned long long)(event_key<G>(xy, e) - klo) << 32) | pair_of(e);
+            };
+            __syncthreads();
+            if (cta_fill_sort_any(w, P < (int)blockDim.x ? (int)blockDim.x : P, word)) {
+                for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
+                    const unsigned long long v = w[k];
+                    const bool cont = k > 0 && (w[k - 1] >> 32) == (v >> 32);
+                    ev[off + k] = ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), cont);
+                }
+                continue;
+            }
+        }
         __syncthreads();
         for (int k = threadIdx.x; k < P; k += blockDim.x) {
             if (k < (int)m) {
@@ -623,16 +644,16 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
     }
     __syncthreads();
     const int dy = s_slope[0], dx = s_slope[1];
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
-        if (k < n) {
-            const int pk = xy[k];
-            a[k] = order_word(proj(pk, dy, dx), px(pk), k);
-        } else {
-            a[k] = ~0ull;
-        }
+    auto word = [&](int k) {
+        if (k >= n) return ~0ull;
+        const int pk = xy[k];
+        return order_word(proj(pk, dy, dx), px(pk), k);
+    };
+    if (n > SORT_SMEM_N || !cta_fill_sort_any(a, P < (int)blockDim.x ? (int)blockDim.x : P, word)) {
+        for (int k = threadIdx.x; k < P; k += blockDim.x) a[k] = word(k);
+        __syncthreads();
+        cta_bitonic_u64(a, P);
     }
-    __syncthreads();
-    cta_bitonic_u64(a, P);
     for (int k = threadIdx.x; k < n; k += blockDim.x)
         orders[(size_t)w * n + k] = (unsigned short)word_index(a[k]);
     // every window at the first slope
@@ -691,6 +712,20 @@ __device__ __forceinline__ int load_xy(const int *s_xy, const int *__restrict__ 
 __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 constexpr int RUN_LANE_MAX = 24;   // runs up to this length are handled by one lane
+#ifndef SWEEP_SERIAL_DEFAULT
+#define SWEEP_SERIAL_DEFAULT false
+#endif
+constexpr bool SWEEP_SERIAL = SWEEP_SERIAL_DEFAULT;   // every batch one event at a time
+#ifndef SWEEP_SERIAL_BELOW
+#define SWEEP_SERIAL_BELOW 6
+#endif
+#ifndef SWEEP_SERIAL_CHUNKS
+#define SWEEP_SERIAL_CHUNKS 2
+#endif
+// A parallel batch costs about as much as several events applied one at a time:
+// after a batch that advanced fewer than SERIAL_BELOW events, the next
+// SERIAL_CHUNKS batches are applied one event at a time.
+constexpr int SERIAL_BELOW = SWEEP_SERIAL_BELOW, SERIAL_CHUNKS = SWEEP_SERIAL_CHUNKS;
 
 // A whole group of one slope dy/dx in one pass over the positions, for
 // groups of about n/4 events or more.  Two points with equal projections at
@@ -894,6 +929,108 @@ __device__ void group_claims(unsigned short *order, unsigned short *pos, const i
     }
 }
 
+// One event applied exactly, with the order just before its slope in place.
+// Every lane of the warp computes the same values and stores the same words,
+// so consecutive events need no barrier; only the cooperative reversal of a
+// run (three or more collinear points) is fenced by warp barriers.
+//   done    b already sits below a: its run was reversed by an earlier
+//           event of the same slope; nothing to do
+//   simple  a, b adjacent and both outer neighbours project elsewhere: swap
+//   run     the block of positions projecting like a (found by ballots
+//           around [pa, pb]) is reversed: the order just after the slope
+// The window starting at the lower rewritten position and the window
+// ending at the upper one are re-scored (Sec. 3.3: an optimal bracelet has a
+// point at one of its ends).
+template <bool XY_SMEM>
+__device__ __forceinline__ void serial_event(unsigned short *order, unsigned short *pos, const int *s_xy,
+                                             const int *__restrict__ g_xy, int n, int h, unsigned e, unsigned gmin,
+                                             int lane, Cand &best, int *err)
+{
+    auto XY = [&](int k) { return load_xy<XY_SMEM>(s_xy, g_xy, k); };
+    int a = ev_i(e), b = ev_j(e);
+    int Pa = XY(a), Pb = XY(b);
+    int pa = pos[a], pb = pos[b];
+    if (px(Pa) > px(Pb)) {
+        const int t = a; a = b; b = t;
+        const int tp = Pa; Pa = Pb; Pb = tp;
+        const int tq = pa; pa = pb; pb = tq;
+    }
+    if (pb < pa) return;
+    const int dx = px(Pb) - px(Pa), dy = py(Pb) - py(Pa);
+    const long long K = proj(Pa, dy, dx);
+    const int top0 = pa + h - 1, bot0 = pb - h + 1;
+    const bool rd_t = top0 < n && top0 > pb, rd_b = bot0 >= 0 && bot0 < pa;
+    const int i_lo = pa > 0 ? order[pa - 1] : 0;
+    const int i_hi = pb < n - 1 ? order[pb + 1] : 0;
+    const int i_t = rd_t ? order[top0] : 0;
+    const int i_b = rd_b ? order[bot0] : 0;
+    const bool lo_eq = pa > 0 && proj(XY(i_lo), dy, dx) == K;
+    const bool hi_eq = pb < n - 1 && proj(XY(i_hi), dy, dx) == K;
+    Cand c;
+    c.dy = dy; c.dx = dx; c.i = (int)(gmin >> 16); c.j = (int)(gmin & 0xffffu);
+    auto offer = [&](long long wd, long long t) {
+        if (best.dx != 0 && wd * (long long)best.dx > best.w * (long long)dx) return;
+        c.w = wd; c.t = t;
+        if (cand_better(c, best)) best = c;
+    };
+    if (pb == pa + 1 && !lo_eq && !hi_eq) {
+        const long long kt = rd_t ? proj(XY(i_t), dy, dx) : K;
+        const long long kb = rd_b ? proj(XY(i_b), dy, dx) : K;
+        order[pa] = (unsigned short)b;
+        order[pb] = (unsigned short)a;
+        pos[b] = (unsigned short)pa;
+        pos[a] = (unsigned short)pb;
+        if (top0 < n) offer(kt - K, K + kt);
+        if (bot0 >= 0) offer(K - kb, kb + K);
+        return;
+    }
+    // a run: extend [pa, pb] over every neighbour projecting like a
+    int lo = pa, hi = pb;
+    if (lo_eq) {
+        lo = pa - 1;
+        for (;;) {
+            const int q = lo - 1 - lane;
+            const unsigned bal = __ballot_sync(FULL, q >= 0 && proj(XY(order[q]), dy, dx) == K);
+            if (bal == FULL) { lo -= 32; continue; }
+            lo -= __ffs(~bal) - 1;
+            break;
+        }
+    }
+    if (hi_eq) {
+        hi = pb + 1;
+        for (;;) {
+            const int q = hi + 1 + lane;
+            const unsigned bal = __ballot_sync(FULL, q < n && proj(XY(order[q]), dy, dx) == K);
+            if (bal == FULL) { hi += 32; continue; }
+            hi += __ffs(~bal) - 1;
+            break;
+        }
+    }
+    bool broken = false;
+    for (int q = pa + 1 + lane; q < pb; q += 32)
+        if (proj(XY(order[q]), dy, dx) != K) broken = true;
+    if (__any_sync(FULL, broken) && lane == 0) atomicOr(err, 2);
+    const int len = hi - lo + 1;
+    __syncwarp();
+    for (int t = lane; t < len / 2; t += 32) {
+        const unsigned short u = order[lo + t], v = order[hi - t];
+        order[lo + t] = v;
+        order[hi - t] = u;
+    }
+    __syncwarp();
+    for (int t = lane; t < len; t += 32) pos[order[lo + t]] = (unsigned short)(lo + t);
+    __syncwarp();
+    const int top = lo + h - 1, bot = hi - h + 1;
+    if (top < n) {
+        const long long kt = top > hi ? proj(XY(order[top]), dy, dx) : K;
+        offer(kt - K, K + kt);
+    }
+    if (bot >= 0) {
+        const long long kb = bot < lo ? proj(XY(order[bot]), dy, dx) : K;
+        offer(K - kb, kb + K);
+    }
+}
+
 // One warp per sweeper; each lane takes one of up to 32 consecutive events.
 //
 // Invariant: between two event slopes the order is sorted by projection, and
@@ -916,7 +1053,7 @@ __device__ void group_claims(unsigned short *order, unsigned short *pos, const i
 // lane's [lo - 1, hi + 1] or one of its window ends lo + h - 1, hi - h + 1;
 // the batch is cut before the first such lane.  All reads of a batch happen
 // before its writes.
-template <bool XY_SMEM>
+template <bool XY_SMEM, bool SERIAL = SWEEP_SERIAL>
 __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int n, int h,
                                                const unsigned *__restrict__ ev,
                                                const unsigned *__restrict__ range, int W,
@@ -968,6 +1105,7 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
         const unsigned lanemask_le = 0xffffffffu >> (31 - lane);
         const unsigned lanemask_lt = lanemask_le >> 1;
         unsigned carried = 0xffffffffu;   // smallest pair of the group open at k
+        int serial_left = SERIAL ? 1 << 30 : 0;   // batches still to be applied one event at a time
         unsigned k = start;
         unsigned e_cur = (k + lane < end) ? ev[k + lane] : 0u;
         unsigned e_nxt = (k + 32 + lane < end) ? ev[k + 32 + lane] : 0u;
@@ -993,6 +1131,29 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
                 k = g1;
                 e_cur = (k + lane < end) ? ev[k + lane] : 0u;
                 e_nxt = (k + 32 + lane < end) ? ev[k + 32 + lane] : 0u;
+                continue;
+            }
+            if (serial_left > 0) {
+                // the events in order, one at a time; a group that starts inside
+                // the batch and runs past its end is left to the next batch,
+                // which processes it whole
+                --serial_left;
+                int cnt = (int)navail;
+                if (smask > 1u && navail == 32u && __shfl_sync(FULL, ev_cont(e_nxt) ? 1 : 0, 0))
+                    cnt = 31 - __clz(smask);
+                for (int i = 0; i < cnt; ++i) {
+                    const unsigned ei = __shfl_sync(FULL, e, i);
+                    if (!ev_cont(ei)) carried = ((unsigned)ev_i(ei) << 16) | (unsigned)ev_j(ei);
+                    serial_event<XY_SMEM>(order, pos, s_xy, g_xy, n, h, ei, carried, lane, best, err);
+                }
+                const int src = (lane + cnt) & 31;
+                const unsigned c1 = __shfl_sync(FULL, e_cur, src);
+                const unsigned c2 = __shfl_sync(FULL, e_nxt, src);
+                const bool from_cur = lane + cnt < 32;
+                k += cnt;
+                e_cur = from_cur ? c1 : c2;
+                const unsigned q = k + 32 + lane;
+                e_nxt = from_cur ? c2 : ((q < end) ? ev[q] : 0u);
                 continue;
             }
             const unsigned le = smask & lanemask_le;
@@ -1184,6 +1345,9 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
                 advance = 1;
             }
             carried = __shfl_sync(FULL, gmin, advance - 1);
+            // chains of events that share points cut batches short; there one
+            // event at a time is cheaper than a parallel step
+            if (advance < SERIAL_BELOW) serial_left = SERIAL_CHUNKS;
             // slide the 64-event window by `advance`
             const int src = (lane + advance) & 31;
             const unsigned c1 = __shfl_sync(FULL, e_cur, src);
@@ -1374,7 +1538,7 @@ cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, c
     if (e != cudaSuccess) return e;
     int P = 1;
     while (P < n) P <<= 1;
-    const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)P * 8 : 0;
+    const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)(P < 1024 ? 1024 : P) * 8 : 0;
     cudaFuncSetAttribute(k_sweep_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)init_smem);
     {
         StageTimer _t(STAGE_INIT, st);
