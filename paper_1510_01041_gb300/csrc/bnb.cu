@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
@@ -274,6 +275,8 @@ size_t bnb_extra_bytes(int n, int sms)
     b += a256((size_t)BND_MAX);                      // prune flags
     b += a256((size_t)BND_MAX * 8);                  // node lower bounds
     b += a256((size_t)BND_MAX);                      // keep mask
+    b += a256((size_t)BND_MAX * 4);                  // sampled pairs per bucket
+    b += a256((size_t)PRE_MAX * sizeof(float2));     // slope pre-filter of the restricted pair passes
     b += (n > SORT_SMEM_N) ? a256((size_t)grid * 2 * P * 8) : 0;
     return b;
 }
@@ -294,12 +297,15 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     unsigned char *prune = (unsigned char *)take(BND_MAX);
     long long *lbv = (long long *)take((size_t)BND_MAX * 8);
     unsigned char *keep = (unsigned char *)take(BND_MAX);
+    unsigned *scount = (unsigned *)take((size_t)BND_MAX * 4);
+    float2 *pre = (float2 *)take((size_t)PRE_MAX * sizeof(float2));
     int P = 1;
     while (P < n) P <<= 1;
     long long *gscr = (n > SORT_SMEM_N) ? (long long *)take((size_t)2 * sms * 2 * P * 8) : nullptr;
     const int grid = 2 * sms;
 
-    if (launch_sweep_prepare(p, x, y, st) != cudaSuccess) return LMS_ERR_CUDA;
+    if (launch_sweep_sample(p, x, y, st) != cudaSuccess) return LMS_ERR_CUDA;
+    if (launch_sample_counts(p, scount, st) != cudaSuccess) return LMS_ERR_CUDA;
     {
         StageTimer _t(STAGE_OTHER, st);
         k_x_center<<<1, 1024, 0, st>>>(p.xy, n, xc);
@@ -322,26 +328,31 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         StageTimer _t(STAGE_OTHER, st);
         k_min_ub<<<1, 32, 0, st>>>(seed_w, BNB_SEEDS, ub);
     }
-    // bucket structure to the host
+    // bucket structure to the host; the tree weighs buckets by sampled pairs
+    // (the buckets are quantile ranges of the sample), so no pass over all
+    // pairs is needed before the bounds have pruned
     int meta[4];
     long long ub_host = 0;
     if (cudaMemcpyAsync(meta, p.meta, sizeof(meta), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (cudaMemcpyAsync(&ub_host, ub, sizeof(ub_host), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
     const int NB = meta[0] + 1;
+    std::vector<unsigned> cnt(NB);
     std::vector<unsigned> base(NB + 1);
     std::vector<long long> bnd(NB > 1 ? NB - 1 : 1);
-    if (cudaMemcpy(base.data(), p.base, sizeof(unsigned) * (NB + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpy(cnt.data(), scount, sizeof(unsigned) * NB, cudaMemcpyDeviceToHost) != cudaSuccess)
         return LMS_ERR_CUDA;
     if (NB > 1 && cudaMemcpy(bnd.data(), p.bnd, sizeof(long long) * (NB - 1), cudaMemcpyDeviceToHost) != cudaSuccess)
         return LMS_ERR_CUDA;
+    base[0] = 0;
+    for (int b = 0; b < NB; ++b) base[b + 1] = base[b] + cnt[b];
     const unsigned E = base[NB];
     std::vector<unsigned char> keepv(NB, 0);
     // first level: equal-event ranges of buckets
     struct Node { int b0, b1; };
     std::vector<Node> nodes;
     {
-        const int m0 = std::min(NB, BNB_FIRST_NODES);
+        const int m0 = std::min(NB, std::max(BNB_FIRST_NODES, sms));
         int prev = 0;
         for (int k = 1; k <= m0; ++k) {
             const unsigned long long target = (unsigned long long)E * k / m0;
@@ -382,28 +393,77 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
             if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
         }
         evaluated += nn;
+        // survivors split into F children of about equal sampled events, F
+        // chosen so that the next level about fills the SMs (fewer levels,
+        // each a host round trip)
+        int split = 0;
+        for (int k = 0; k < nn; ++k)
+            if (!hp[k] && nodes[k].b1 - nodes[k].b0 > 1) ++split;
+        const int F = split ? std::max(2, std::min(16, sms / split)) : 2;
         std::vector<Node> next;
         for (int k = 0; k < nn; ++k) {
             const Node nd = nodes[k];
             if (hp[k]) { ++pruned; continue; }
             if (nd.b1 - nd.b0 == 1) { keepv[nd.b0] = 1; continue; }
-            // split at the bucket that halves the node's events
-            const unsigned mid_ev = base[nd.b0] + (base[nd.b1] - base[nd.b0]) / 2;
-            int m = (int)(std::upper_bound(base.begin() + nd.b0 + 1, base.begin() + nd.b1, mid_ev) - base.begin());
-            m = std::min(std::max(m, nd.b0 + 1), nd.b1 - 1);
-            next.push_back({nd.b0, m});
-            next.push_back({m, nd.b1});
+            const int parts = std::min(F, nd.b1 - nd.b0);
+            int prev_b = nd.b0;
+            for (int q = 1; q <= parts; ++q) {
+                int m = nd.b1;
+                if (q < parts) {
+                    const unsigned long long tgt =
+                        base[nd.b0] + (unsigned long long)(base[nd.b1] - base[nd.b0]) * q / parts;
+                    m = (int)(std::upper_bound(base.begin() + prev_b + 1, base.begin() + nd.b1, (unsigned)tgt) -
+                              base.begin());
+                    m = std::min(std::max(m, prev_b + 1), nd.b1 - (parts - q));
+                }
+                next.push_back({prev_b, m});
+                prev_b = m;
+            }
         }
         nodes.swap(next);
     }
-    // bucket starts over the kept buckets only
-    std::vector<unsigned> kbase(NB + 1);
-    unsigned run = 0, kept_buckets = 0;
-    for (int b = 0; b < NB; ++b) {
-        kbase[b] = run;
-        if (keepv[b]) { run += base[b + 1] - base[b]; ++kept_buckets; }
+    // slope covers of the runs of kept buckets for the pair passes: bucket b
+    // holds keys [bnd[b - 1], bnd[b]), a key being floor(slope 2^32); each
+    // cover is widened by more than the float slope error (2^-22 relative)
+    // and rounded outward; at most PRE_MAX covers (closest runs merged)
+    std::vector<std::pair<double, double>> cov;
+    unsigned kept_buckets = 0;
+    for (int b = 0; b < NB;) {
+        if (!keepv[b]) { ++b; continue; }
+        int e = b + 1;
+        while (e < NB && keepv[e]) ++e;
+        for (int q = b; q < e; ++q) kept_buckets += 1;
+        const double lo = b == 0 ? -INFINITY : (double)bnd[b - 1] * 0x1p-32;
+        const double hi = e >= NB ? INFINITY : (double)bnd[e - 1] * 0x1p-32;
+        cov.push_back({lo - (std::isinf(lo) ? 0.0 : std::fabs(lo) * 0x1p-18 + 0x1p-30),
+                       hi + (std::isinf(hi) ? 0.0 : std::fabs(hi) * 0x1p-18 + 0x1p-30)});
+        b = e;
     }
-    kbase[NB] = run;
+    while (cov.size() > (size_t)PRE_MAX) {
+        size_t best = 1;
+        for (size_t k = 2; k < cov.size(); ++k)
+            if (cov[k].first - cov[k - 1].second < cov[best].first - cov[best - 1].second) best = k;
+        cov[best - 1].second = cov[best].second;
+        cov.erase(cov.begin() + best);
+    }
+    std::vector<float2> prev(cov.size());
+    for (size_t k = 0; k < cov.size(); ++k) {
+        prev[k].x = std::nextafter((float)cov[k].first, -INFINITY);
+        prev[k].y = std::nextafter((float)cov[k].second, INFINITY);
+    }
+    const int npre = (int)cov.size();
+    if (cudaMemcpyAsync(keep, keepv.data(), NB, cudaMemcpyHostToDevice, st) != cudaSuccess) return LMS_ERR_CUDA;
+    if (npre > 0 && cudaMemcpyAsync(pre, prev.data(), sizeof(float2) * npre, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return LMS_ERR_CUDA;
+    // exact events of the kept buckets only: p.base becomes their starts
+    if (launch_sweep_count(p, keep, npre > 0 ? pre : nullptr, npre, st) != cudaSuccess) return LMS_ERR_CUDA;
+    std::vector<unsigned> kbase(NB + 1);
+    int meta6[6];
+    if (cudaMemcpyAsync(kbase.data(), p.base, sizeof(unsigned) * (NB + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return LMS_ERR_CUDA;
+    if (cudaMemcpyAsync(meta6, p.meta, sizeof(meta6), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LMS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
+    const unsigned run = kbase[NB];
     // ranges: pieces of about `target` events inside each run of consecutive
     // kept buckets (a range never spans a dropped bucket: the kinetic order
     // must see every event between its first and last slope); the device
@@ -414,7 +474,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     {
         std::vector<std::pair<unsigned, unsigned>> runs;
         for (int b = 0; b < NB;) {
-            if (!keepv[b] || base[b + 1] == base[b]) { ++b; continue; }
+            if (!keepv[b] || kbase[b + 1] == kbase[b]) { ++b; continue; }
             int e = b + 1;
             while (e < NB && keepv[e]) ++e;
             runs.push_back({kbase[b], kbase[e]});
@@ -439,16 +499,13 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         }
         for (size_t w = used; w < (size_t)p.W; ++w) { rng[2 * w] = run; rng[2 * w + 1] = run; }
     }
-    if (cudaMemcpyAsync(p.base, kbase.data(), sizeof(unsigned) * (NB + 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return LMS_ERR_CUDA;
-    if (cudaMemcpyAsync(keep, keepv.data(), NB, cudaMemcpyHostToDevice, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (cudaMemcpyAsync(p.range, rng.data(), sizeof(unsigned) * 2 * p.W, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return LMS_ERR_CUDA;
-    if (launch_sweep_finish(p, keep, st, false) != cudaSuccess) return LMS_ERR_CUDA;
+    if (launch_sweep_finish(p, keep, st, false, npre > 0 ? pre : nullptr, npre) != cudaSuccess) return LMS_ERR_CUDA;
     if (launch_argmin(p.cands, p.W + p.G, out, LMS_ALGO_BNB, p.meta + 3, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
     if (stats) {
-        stats->events_total = E;
+        stats->events_total = (unsigned)meta6[5];
         stats->events_swept = run;
         stats->buckets_total = NB;
         stats->buckets_swept = kept_buckets;

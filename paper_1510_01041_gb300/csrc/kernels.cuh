@@ -40,6 +40,15 @@ struct KeyI16 {   // packed int16 points: exact key floor(dy 2^32 / dx)
         k = slope_key(dy, dx);
         return true;
     }
+    // float slope dy * (1 / dx), relative error below 2^-22; false when x_i == x_j
+    static __device__ __forceinline__ bool approx(const void *pts, int i, int j, float &sl)
+    {
+        const int *xy = static_cast<const int *>(pts);
+        int dy, dx;
+        if (!pair_slope(__ldg(&xy[i]), __ldg(&xy[j]), dy, dx)) return false;
+        sl = __fmul_rn((float)dy, __frcp_rn((float)dx));
+        return true;
+    }
 };
 struct KeyF32 {   // float2 points: the double slope dy/dx as order-preserving bits
     static __device__ __forceinline__ bool key(const void *pts, int i, int j, long long &k)
@@ -52,6 +61,14 @@ struct KeyF32 {   // float2 points: the double slope dy/dx as order-preserving b
         const double sl = __ddiv_rn(dy, dx);
         const long long bits = sl == 0.0 ? 0LL : __double_as_longlong(sl);
         k = bits < 0 ? (bits ^ 0x7fffffffffffffffLL) : bits;
+        return true;
+    }
+    static __device__ __forceinline__ bool approx(const void *pts, int i, int j, float &sl)
+    {
+        const float2 *P = static_cast<const float2 *>(pts);
+        const double dx = (double)P[j].x - (double)P[i].x, dy = (double)P[j].y - (double)P[i].y;
+        if (dx == 0.0) return false;
+        sl = (float)(dy / dx);
         return true;
     }
 };
@@ -82,7 +99,8 @@ struct SweepPlan {
     long long *skeys;          // [S] sampled slope keys
     long long *skeys2;         // [S] merge ping-pong
     long long *bnd;            // [BND_MAX] bucket boundaries, padded with INT64_MAX
-    int *meta;                 // [16] 0 nbnd, 1 P2, 2 oversize count, 3 error flags, 4 range counter
+    int *meta;                 // [16] 0 nbnd, 1 P2, 2 oversize count, 3 error flags, 4 range counter,
+                               //      5 pairs with distinct x (restricted count)
     unsigned *hist;            // [C][BND_MAX] per-CTA bucket counts, then offsets
     unsigned *base;            // [BND_MAX + 1] bucket starts; base[NB] = E
     int *oversize;             // [BND_MAX] buckets too large for the shared-memory sort
@@ -103,13 +121,26 @@ cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cud
 cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short *y, cudaStream_t st);
 // plan = false: the caller has written the range bounds (any event offsets
 // inside runs of kept buckets); they are moved to group starts on the device
-cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan);
+cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan,
+                                const float2 *pre = nullptr, int npre = 0);
 const long long *sorted_sample(const SweepPlan &p);
 // generic halves of the event pipeline (sample .. bucket starts; scatter .. plan)
 template <class G> cudaError_t launch_events_prepare(const SweepPlan &p, const void *pts, cudaStream_t st);
 template <class G>
 cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsigned char *keep, cudaStream_t st,
-                                 bool plan);
+                                 bool plan, const float2 *pre = nullptr, int npre = 0);
+// Restriction of the pair passes to kept buckets: a pair is examined
+// further only if its float slope lies in one of the npre intervals pre
+// (outward-rounded covers of the kept slope ranges) and its bucket is kept.
+constexpr int PRE_MAX = 8;
+// the sample half of the prepare step (pack, sample, sort, splitters) and
+// the count half (count, prefix, scan) restricted as above; pairs with
+// distinct x are counted into meta[5]
+cudaError_t launch_sweep_sample(const SweepPlan &p, const short *x, const short *y, cudaStream_t st);
+cudaError_t launch_sweep_count(const SweepPlan &p, const unsigned char *keep, const float2 *pre, int npre,
+                               cudaStream_t st);
+// per-bucket counts of the valid sampled pairs into counts[0 .. NB)
+cudaError_t launch_sample_counts(const SweepPlan &p, unsigned *counts, cudaStream_t st);
 // float32 points: event pipeline on the double slope key, double-precision
 // sweep, reduction into `out` (device).  fscratch: sweep_f32_extra_bytes.
 cudaError_t launch_sweep_f32_fit(const SweepPlan &p, const float *x, const float *y, void *fscratch,

@@ -60,34 +60,53 @@ __device__ void set_frame(const short *x, const short *y, long long a, long long
     __syncthreads();
 }
 
-// Forward: one CTA per set.  Writes pred[4] = (phi, b, slope, theta2) in the
-// original frame; with targets, also the loss and dL/d(phi, b).
-__global__ void __launch_bounds__(256) k_setnet_fwd(const __nv_bfloat16 *__restrict__ wb,
-                                                    const short *__restrict__ x, const short *__restrict__ y,
-                                                    const long long *__restrict__ off, int B,
-                                                    const float *__restrict__ targets, float bweight,
-                                                    float *__restrict__ pred, float *__restrict__ state,
-                                                    unsigned long long *__restrict__ pool_out,
-                                                    float *__restrict__ dout)
+// Forward in three launches so that one large set spreads over many SMs.
+// Stage 1, one CTA per set: the set's frame into state[0..2]; clears its pool.
+__global__ void __launch_bounds__(256) k_setnet_frame(const short *__restrict__ x, const short *__restrict__ y,
+                                                      const long long *__restrict__ off, float *__restrict__ state,
+                                                      unsigned long long *__restrict__ pool)
+{
+    const int set = blockIdx.x;
+    float cx, cy, sc;
+    set_frame(x, y, off[set], off[set + 1], cx, cy, sc);
+    if (threadIdx.x == 0) {
+        float *st = state + (size_t)set * STATE;
+        st[0] = cx; st[1] = cy; st[2] = sc;
+    }
+    if (threadIdx.x < H2) pool[(size_t)set * H2 + threadIdx.x] = 0ull;
+}
+
+// Stage 2, grid (set, slice): the per-point layers over one slice of a set's
+// points (slices of whole warps) and the max-pool of the slice, merged into
+// the set's pool by atomic maxima.  A pool entry keeps the largest value
+// and, on ties, the smallest point index; the maximum does not depend on how
+// the points are sliced, so the result is the same for any grid.
+__global__ void __launch_bounds__(256) k_setnet_points(const __nv_bfloat16 *__restrict__ wb,
+                                                       const short *__restrict__ x, const short *__restrict__ y,
+                                                       const long long *__restrict__ off,
+                                                       const float *__restrict__ state,
+                                                       unsigned long long *__restrict__ pool)
 {
     __shared__ float s_w1[H1 * 2], s_b1[H1], s_w2[H2 * H1], s_b2[H2];
     __shared__ unsigned long long s_pool[H2];
-    __shared__ float s_g[H2], s_h3[H3];
     const int set = blockIdx.x;
-    if (set >= B) return;
+    const long long a = off[set], b = off[set + 1];
+    const long long chunk = ((b - a + gridDim.y - 1) / gridDim.y + 31) & ~31LL;
+    const long long c0 = a + chunk * blockIdx.y, c1 = min(b, c0 + chunk);
+    if (c0 >= c1) return;
     for (int k = threadIdx.x; k < H1 * 2; k += blockDim.x) s_w1[k] = ld(wb, OFF_W1 + k);
     for (int k = threadIdx.x; k < H1; k += blockDim.x) s_b1[k] = ld(wb, OFF_B1 + k);
     for (int k = threadIdx.x; k < H2 * H1; k += blockDim.x) s_w2[k] = ld(wb, OFF_W2 + k);
     for (int k = threadIdx.x; k < H2; k += blockDim.x) { s_b2[k] = ld(wb, OFF_B2 + k); s_pool[k] = 0ull; }
-    const long long a = off[set], b = off[set + 1];
-    float cx, cy, sc;
-    set_frame(x, y, a, b, cx, cy, sc);
+    const float *st = state + (size_t)set * STATE;
+    const float cx = st[0], cy = st[1], sc = st[2];
     const float inv = 1.0f / sc;
     const int lane = threadIdx.x & 31;
-    // points: one per lane, warps stride over the set
-    for (long long base = a + (threadIdx.x & ~31); base < b; base += blockDim.x) {
+    __syncthreads();
+    // points: one per lane, warps stride over the slice
+    for (long long base = c0 + (threadIdx.x & ~31); base < c1; base += blockDim.x) {
         const long long p = base + lane;
-        const bool valid = p < b;
+        const bool valid = p < c1;
         const float xn = valid ? ((float)x[p] - cx) * inv : 0.f;
         const float yn = valid ? ((float)y[p] - cy) * inv : 0.f;
         float h1[H1];
@@ -103,24 +122,33 @@ __global__ void __launch_bounds__(256) k_setnet_fwd(const __nv_bfloat16 *__restr
 #pragma unroll
             for (int k = 0; k < H1; ++k) acc = fmaf(s_w2[c * H1 + k], h1[k], acc);
             const float h2 = fmaxf(acc, 0.f);
-            // pool: largest value, then smallest point index
             unsigned long long key = valid ? (((unsigned long long)__float_as_uint(h2) << 32) |
                                               (unsigned long long)(0xffffffffu - (unsigned)(p - a)))
                                            : 0ull;
 #pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                const unsigned long long o = __shfl_xor_sync(FULL, key, s);
+            for (int s2 = 16; s2 >= 1; s2 >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(FULL, key, s2);
                 key = o > key ? o : key;
             }
             if (lane == 0) atomicMax(&s_pool[c], key);
         }
     }
     __syncthreads();
-    if (threadIdx.x < H2) {
-        const unsigned long long k = s_pool[threadIdx.x];
-        s_g[threadIdx.x] = __uint_as_float((unsigned)(k >> 32));
-        if (pool_out) pool_out[(size_t)set * H2 + threadIdx.x] = k;
-    }
+    if (threadIdx.x < H2) atomicMax(&pool[(size_t)set * H2 + threadIdx.x], s_pool[threadIdx.x]);
+}
+
+// Stage 3, one CTA of 64 threads per set: the head on the pooled features.
+// Writes pred[4] = (phi, b, slope, theta2) in the original frame and the
+// state; with targets, also the loss and dL/d(phi, b).
+__global__ void __launch_bounds__(64) k_setnet_head(const __nv_bfloat16 *__restrict__ wb, int B,
+                                                    const float *__restrict__ targets, float bweight,
+                                                    float *__restrict__ pred, float *__restrict__ state,
+                                                    const unsigned long long *__restrict__ pool,
+                                                    float *__restrict__ dout)
+{
+    __shared__ float s_g[H2], s_h3[H3];
+    const int set = blockIdx.x;
+    if (threadIdx.x < H2) s_g[threadIdx.x] = __uint_as_float((unsigned)(pool[(size_t)set * H2 + threadIdx.x] >> 32));
     __syncthreads();
     if (threadIdx.x < H3) {
         float acc = ld(wb, OFF_B3 + threadIdx.x);
@@ -129,6 +157,8 @@ __global__ void __launch_bounds__(256) k_setnet_fwd(const __nv_bfloat16 *__restr
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        float *st = state + (size_t)set * STATE;
+        const float cx = st[0], cy = st[1], sc = st[2];
         float o[NOUT];
         for (int j = 0; j < NOUT; ++j) {
             float acc = ld(wb, OFF_B4 + j);
@@ -140,14 +170,35 @@ __global__ void __launch_bounds__(256) k_setnet_fwd(const __nv_bfloat16 *__restr
         const float theta2 = cy + sc * bn - slope * cx;
         float *pr = pred + (size_t)set * 4;
         pr[0] = phi; pr[1] = bn; pr[2] = slope; pr[3] = theta2;
-        float *st = state + (size_t)set * STATE;
-        st[0] = cx; st[1] = cy; st[2] = sc; st[3] = phi; st[4] = bn; st[5] = slope; st[6] = theta2;
+        st[3] = phi; st[4] = bn; st[5] = slope; st[6] = theta2;
         if (targets) {
             const float e0 = phi - targets[2 * set], e1 = bn - targets[2 * set + 1];
             st[7] = (e0 * e0 + bweight * e1 * e1) / (float)B;
             dout[2 * set] = 2.f * e0 / (float)B;
             dout[2 * set + 1] = 2.f * bweight * e1 / (float)B;
         }
+    }
+}
+
+// The three forward stages on stream st; slices per set so that about two
+// CTAs per SM are busy (at most 64, at least 1).
+void setnet_forward(const __nv_bfloat16 *wb, float *state, unsigned long long *pool, float *dout, const short *x,
+                    const short *y, const long long *off, int B, const float *targets, float bweight, float *pred,
+                    cudaStream_t st)
+{
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int slices = (2 * (sms > 0 ? sms : 1) + B - 1) / B;
+    slices = slices < 1 ? 1 : (slices > 64 ? 64 : slices);
+    { StageTimer _t(STAGE_OTHER, st); k_setnet_frame<<<B, 256, 0, st>>>(x, y, off, state, pool); }
+    {
+        StageTimer _t(STAGE_OTHER, st);
+        k_setnet_points<<<dim3(B, slices), 256, 0, st>>>(wb, x, y, off, state, pool);
+    }
+    {
+        StageTimer _t(STAGE_OTHER, st);
+        k_setnet_head<<<B, 64, 0, st>>>(wb, B, targets, bweight, pred, state, pool, dout);
     }
 }
 
@@ -370,9 +421,8 @@ int lms_setnet_forward(lms_setnet *net, const int16_t *x, const int16_t *y, cons
     if (!net || !x || !y || !offsets || !pred || B < 1) return LMS_ERR_ARG;
     if (grow_sets(net, (int)B)) return LMS_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    StageTimer _t(STAGE_OTHER, st);
-    k_setnet_fwd<<<(int)B, 256, 0, st>>>(net->wb, (const short *)x, (const short *)y, (const long long *)offsets,
-                                         (int)B, nullptr, 0.f, pred, net->state, nullptr, nullptr);
+    setnet_forward(net->wb, net->state, net->pool, net->dout, (const short *)x, (const short *)y,
+                   (const long long *)offsets, (int)B, nullptr, 0.f, pred, st);
     return cudaGetLastError() == cudaSuccess ? LMS_OK : LMS_ERR_CUDA;
 }
 
@@ -384,12 +434,8 @@ int lms_setnet_backward(lms_setnet *net, const int16_t *x, const int16_t *y, con
     if (grow_sets(net, (int)B)) return LMS_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaMemsetAsync(net->g, 0, sizeof(float) * NPARAM, st);
-    {
-        StageTimer _t(STAGE_OTHER, st);
-        k_setnet_fwd<<<(int)B, 256, 0, st>>>(net->wb, (const short *)x, (const short *)y,
-                                             (const long long *)offsets, (int)B, targets, intercept_weight,
-                                             net->pred, net->state, net->pool, net->dout);
-    }
+    setnet_forward(net->wb, net->state, net->pool, net->dout, (const short *)x, (const short *)y,
+                   (const long long *)offsets, (int)B, targets, intercept_weight, net->pred, st);
     {
         StageTimer _t(STAGE_OTHER, st);
         k_setnet_bwd<<<(int)B, 64, 0, st>>>(net->wb, (const short *)x, (const short *)y, (const long long *)offsets,

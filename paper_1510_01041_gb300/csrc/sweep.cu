@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(1024) k_splitters(const long long *__restrict_
     int P2 = 1;
     while (P2 <= nbnd) P2 <<= 1;
     for (int k = nbnd + threadIdx.x; k < P2; k += blockDim.x) bnd[k] = KEY_INF;
-    if (threadIdx.x == 0) { meta[0] = nbnd; meta[1] = P2; meta[2] = 0; meta[3] = 0; }
+    if (threadIdx.x == 0) { meta[0] = nbnd; meta[1] = P2; meta[2] = 0; meta[3] = 0; meta[5] = 0; }
 }
 
 // ---------------------------------------------------------------- count / scatter
@@ -193,13 +193,18 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
                                                               unsigned *__restrict__ hist,
                                                               const unsigned *__restrict__ base,
                                                               unsigned *__restrict__ ev,
-                                                              const unsigned char *__restrict__ keep)
+                                                              const unsigned char *__restrict__ keep,
+                                                              const float2 *__restrict__ pre, int npre,
+                                                              int *__restrict__ meta_mut)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
     unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
+    __shared__ float2 s_pre[PRE_MAX];
     const int nbnd = meta[0], P2 = meta[1], NB = nbnd + 1;
     for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
+    if (threadIdx.x < npre) s_pre[threadIdx.x] = pre[threadIdx.x];
+    unsigned nvalid = 0;
     unsigned *my_hist = hist + (size_t)blockIdx.x * BND_MAX;
     for (int k = threadIdx.x; k < NB; k += blockDim.x)
         s_cnt[k] = SCATTER ? base[k] + my_hist[k] : 0u;
@@ -218,18 +223,48 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
         for (int jj = 0; jj < JPT; ++jj) {
             const int j = bj * TILE + jl0 + jj;
             if (j <= i || j >= n) continue;
+            if (pre) {
+                float sl;
+                if (!G::approx(pts, i, j, sl)) continue;
+                ++nvalid;
+                bool cand = false;
+                for (int r = 0; r < npre; ++r) cand |= (sl >= s_pre[r].x) & (sl <= s_pre[r].y);
+                if (!cand) continue;
+            }
             long long key;
             if (!G::key(pts, i, j, key)) continue;
             const int b = bucket_of(s_bnd, P2, key);
-            if (SCATTER && keep && !keep[b]) continue;
+            if (keep && !keep[b]) continue;
             const unsigned slot = atomicAdd(&s_cnt[b], 1u);
             if (SCATTER) ev[slot] = ev_pack(i, j, false);
         }
     }
     if (!SCATTER) {
+        if (pre) {
+            for (int m = 16; m >= 1; m >>= 1) nvalid += __shfl_xor_sync(FULL, nvalid, m);
+            if ((threadIdx.x & 31) == 0 && nvalid) atomicAdd(reinterpret_cast<unsigned *>(meta_mut + 5), nvalid);
+        }
         __syncthreads();
         for (int k = threadIdx.x; k < NB; k += blockDim.x) my_hist[k] = s_cnt[k];
     }
+}
+
+// Per bucket: the number of valid sampled keys in it (the sample is sorted
+// and the buckets are its quantile ranges, so two binary searches suffice).
+__global__ void k_sample_counts(const long long *__restrict__ sorted, int S, const long long *__restrict__ bnd,
+                                const int *__restrict__ meta, unsigned *__restrict__ counts)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int NB = meta[0] + 1;
+    if (b >= NB) return;
+    auto first_ge = [&](long long v) {
+        int lo = 0, hi = S;
+        while (lo < hi) { const int m = (lo + hi) >> 1; if (sorted[m] < v) lo = m + 1; else hi = m; }
+        return lo;
+    };
+    const int a = b == 0 ? 0 : first_ge(bnd[b - 1]);
+    const int e = b == NB - 1 ? first_ge(KEY_INF) : first_ge(bnd[b]);
+    counts[b] = (unsigned)(e - a);
 }
 
 // Per bucket: exclusive prefix over CTAs (in place) and the bucket total.
@@ -1478,7 +1513,7 @@ const long long *sorted_sample(const SweepPlan &p)
 }
 
 template <class G>
-cudaError_t launch_events_prepare(const SweepPlan &p, const void *pts, cudaStream_t st)
+static cudaError_t events_sample(const SweepPlan &p, const void *pts, cudaStream_t st)
 {
     const int n = p.n;
     { StageTimer _t(STAGE_SAMPLE, st); k_sample<G><<<(p.S + 255) / 256, 256, 0, st>>>(pts, n, p.emax, p.S, p.skeys); }
@@ -1489,22 +1524,60 @@ cudaError_t launch_events_prepare(const SweepPlan &p, const void *pts, cudaStrea
         long long *t = src; src = dst; dst = t;
     }
     { StageTimer _t(STAGE_SPLITTERS, st); k_splitters<<<1, 1024, 0, st>>>(src, p.S, p.B, p.bnd, p.meta); }
+    return cudaGetLastError();
+}
+
+template <class G>
+static cudaError_t events_count(const SweepPlan &p, const void *pts, const unsigned char *keep, const float2 *pre,
+                                int npre, cudaStream_t st)
+{
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
     cudaFuncSetAttribute(k_bucket_pairs<false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    { StageTimer _t(STAGE_COUNT_PAIRS, st); k_bucket_pairs<false, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, nullptr, nullptr, nullptr); }
+    {
+        StageTimer _t(STAGE_COUNT_PAIRS, st);
+        k_bucket_pairs<false, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, p.n, p.bnd, p.meta, p.hist, nullptr, nullptr,
+                                                                    keep, pre, npre, p.meta);
+    }
     { StageTimer _t(STAGE_PREFIX, st); k_bucket_prefix<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.hist, p.C, p.meta, p.base); }
     { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta); }
     return cudaGetLastError();
 }
 
 template <class G>
+cudaError_t launch_events_prepare(const SweepPlan &p, const void *pts, cudaStream_t st)
+{
+    cudaError_t e = events_sample<G>(p, pts, st);
+    if (e != cudaSuccess) return e;
+    return events_count<G>(p, pts, nullptr, nullptr, 0, st);
+}
+
+cudaError_t launch_sweep_sample(const SweepPlan &p, const short *x, const short *y, cudaStream_t st)
+{
+    { StageTimer _t(STAGE_PACK, st); k_pack<<<(p.n + 255) / 256, 256, 0, st>>>(x, y, p.n, p.xy); }
+    return events_sample<KeyI16>(p, p.xy, st);
+}
+
+cudaError_t launch_sweep_count(const SweepPlan &p, const unsigned char *keep, const float2 *pre, int npre,
+                               cudaStream_t st)
+{
+    return events_count<KeyI16>(p, p.xy, keep, pre, npre, st);
+}
+
+cudaError_t launch_sample_counts(const SweepPlan &p, unsigned *counts, cudaStream_t st)
+{
+    StageTimer _t(STAGE_OTHER, st);
+    k_sample_counts<<<(BND_MAX + 255) / 256, 256, 0, st>>>(sorted_sample(p), p.S, p.bnd, p.meta, counts);
+    return cudaGetLastError();
+}
+
+template <class G>
 cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsigned char *keep, cudaStream_t st,
-                                 bool plan)
+                                 bool plan, const float2 *pre, int npre)
 {
     const int n = p.n;
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
     cudaFuncSetAttribute(k_bucket_pairs<true, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    { StageTimer _t(STAGE_SCATTER, st); k_bucket_pairs<true, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep); }
+    { StageTimer _t(STAGE_SCATTER, st); k_bucket_pairs<true, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep, pre, npre, p.meta); }
     const size_t seg_smem = (size_t)SEG_CAP * 12;
     cudaFuncSetAttribute(k_segsort<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
     { StageTimer _t(STAGE_SEGSORT, st); k_segsort<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, p.base, p.bnd, p.meta, p.oversize); }
@@ -1523,7 +1596,7 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
 
 template cudaError_t launch_events_prepare<KeyF32>(const SweepPlan &, const void *, cudaStream_t);
 template cudaError_t launch_events_finish<KeyF32>(const SweepPlan &, const void *, const unsigned char *, cudaStream_t,
-                                                  bool);
+                                                  bool, const float2 *, int);
 
 cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short *y, cudaStream_t st)
 {
@@ -1531,10 +1604,11 @@ cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short
     return launch_events_prepare<KeyI16>(p, p.xy, st);
 }
 
-cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan)
+cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan,
+                                const float2 *pre, int npre)
 {
     const int n = p.n;
-    cudaError_t e = launch_events_finish<KeyI16>(p, p.xy, keep, st, plan);
+    cudaError_t e = launch_events_finish<KeyI16>(p, p.xy, keep, st, plan, pre, npre);
     if (e != cudaSuccess) return e;
     int P = 1;
     while (P < n) P <<= 1;
