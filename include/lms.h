@@ -97,7 +97,9 @@ typedef struct {
 /*
  * lms_fit -- exact LMS of one point set (Algorithm 1, Sec. 3.4).
  *   x, y    device arrays of n coordinates (int16_t or float, per dtype), SoA.
- *   n       2 <= n <= 65536.
+ *   n       2 <= n <= 65536 for int16 points (above 58112 points each
+ *           sweeping warp keeps its position array in global memory);
+ *           float points up to 32768 (larger: LMS_ERR_UNSUPPORTED).
  *   h       order statistic in [1, n]; 0 selects floor(n/2) + 1.
  *   dtype   enum lms_dtype.
  *   opt     NULL for defaults.
@@ -138,7 +140,7 @@ typedef struct {
  *               bound is taken at the sampled slopes nearest it.  NULL: at
  *               evenly spaced sampled slopes instead.
  *   stats       host pointer (may be NULL).
- * Other arguments as lms_fit (int16 points, n <= 32768).  The call waits for
+ * Other arguments as lms_fit (int16 points, n <= 65536).  The call waits for
  * the stream between bisection levels and returns after the fit is done.
  */
 LMS_API int lms_fit_bnb(const void *x, const void *y, int64_t n, int64_t h, const float *seed_slope,

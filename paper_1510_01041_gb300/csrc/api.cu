@@ -110,9 +110,9 @@ int choose(int n, int h, int dtype, const lms_options *opt, int dev, Choice &c)
         c.plain_warps = plain_warps_for(n, sms);
         c.bytes = ((size_t)c.plain_warps * sizeof(Cand) + 255) / 256 * 256;
     } else if (algo == LMS_ALGO_SWEEP || algo == LMS_ALGO_BNB) {
-        if (n > 32768) return LMS_ERR_UNSUPPORTED;
+        if (dtype == LMS_F32 && n > 32768) return LMS_ERR_UNSUPPORTED;
         sweep_plan_configure(c.sweep, n, h, sms, opt ? opt->sweepers : 0, opt ? opt->buckets : 0);
-        c.bytes = sweep_plan_bytes(n, c.sweep.W, c.sweep.C, c.sweep.S);
+        c.bytes = sweep_plan_bytes(c.sweep);
         if (algo == LMS_ALGO_BNB) {
             c.bnb_off = c.bytes;
             c.bytes += bnb_extra_bytes(n, sms);

@@ -356,7 +356,7 @@ int lms_batch_plan_create(const int64_t *offsets_host, int64_t B, const int32_t 
         load[s] += n * n;
         SweepPlan sp;
         sweep_plan_configure(sp, (int)n, p->hval[p->sweep_sets[k]], sms, 0, 0);
-        need[s] = std::max(need[s], sweep_plan_bytes((int)n, sp.W, sp.C, sp.S));
+        need[s] = std::max(need[s], sweep_plan_bytes(sp));
     }
     p->streams.resize(ns);
     p->ev_done.resize(ns);

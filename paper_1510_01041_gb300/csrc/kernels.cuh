@@ -93,6 +93,7 @@ struct SweepPlan {
     int G;             // sweeping warps of the persistent sweep kernel (G < W + spb)
     int spb;           // sweeping warps per sweep CTA
     bool xy_smem;      // sweep CTAs keep all points in shared memory
+    bool pos_smem;     // sweeping warps keep the position array in shared memory (else gpos)
     long long emax;    // n (n - 1) / 2
     // device buffers
     int *xy;                   // [n] packed points
@@ -110,9 +111,10 @@ struct SweepPlan {
     unsigned short *orders;    // [W][n] start orders
     unsigned long long *gsort; // [W][P] global sort scratch when n > SORT_SMEM_N
     Cand *cands;               // [W + G] range-start + sweeping-warp candidates
+    unsigned short *gpos;      // [G][n] positions of the sweeping warps when !pos_smem (else null)
 };
 
-size_t sweep_plan_bytes(int n, int W, int C, int S);
+size_t sweep_plan_bytes(const SweepPlan &p);
 void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int want_b);
 void sweep_plan_carve(SweepPlan &p, void *ws);
 cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cudaStream_t st);

@@ -38,7 +38,10 @@ constexpr long long KEY_INF = 0x7fffffffffffffffLL;
 constexpr int TILE = 64;          // pair tile edge of the count / scatter passes
 constexpr int CNT_THREADS = 512;  // threads of a count / scatter CTA
 constexpr int SORT_CHUNK = 1024;  // sample keys sorted per shared-memory chunk
-constexpr int RANGE_FACTOR = 4;   // slope ranges per sweeping warp (dynamic load balance)
+#ifndef SWEEP_RANGE_FACTOR
+#define SWEEP_RANGE_FACTOR 4
+#endif
+constexpr int RANGE_FACTOR = SWEEP_RANGE_FACTOR;   // slope ranges per sweeping warp (dynamic load balance)
 constexpr long long MIN_RANGE_EVENTS = 512;
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
@@ -627,12 +630,34 @@ __device__ void cta_bitonic_u64(unsigned long long *a, int P)
     }
 }
 
+// Bitonic sort of P words in a with a 16-bit payload moved alongside (one
+// CTA, global or shared memory).
+__device__ void cta_bitonic_kv(unsigned long long *a, unsigned short *pay, int P)
+{
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j >= 1; j >>= 1) {
+            for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                const int i = 2 * t - (t & (j - 1));
+                const int l = i + j;
+                const bool up = (i & k) == 0;
+                const unsigned long long x0 = a[i], x1 = a[l];
+                if ((x0 > x1) == up) {
+                    a[i] = x1; a[l] = x0;
+                    const unsigned short p0 = pay[i];
+                    pay[i] = pay[l]; pay[l] = p0;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // Packed sort word of one point at the start slope: (key + 2^32) in bits
 // 63..31, (x + 2^15) in bits 30..15, point index in bits 14..0.  Ascending
 // words order the points by projection, then x ascending, then index: the
 // order just before the slope (a line of that slope lists its points by
-// increasing x).  For int16 points |key| < 2^32 and n <= 32768, so the
-// fields never overlap.
+// increasing x).  For int16 points |key| < 2^32 and n <= 32768 here, so
+// the fields never overlap.
 __device__ __forceinline__ unsigned long long order_word(long long key, int x, int k)
 {
     return ((unsigned long long)(key + (1LL << 32)) << 31) | ((unsigned long long)(unsigned)(x + 32768) << 15) |
@@ -684,18 +709,36 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
         const int pk = xy[k];
         return order_word(proj(pk, dy, dx), px(pk), k);
     };
-    if (n > SORT_SMEM_N || !cta_fill_sort_any(a, P < (int)blockDim.x ? (int)blockDim.x : P, word)) {
+    // above 32768 points the index needs 16 bits: the word then holds
+    // (key + 2^32, x + 2^15) and the index travels in a payload array (equal
+    // words are identical points, whose order is immaterial)
+    const bool wide = n > 32768;
+    unsigned short *pay = wide ? reinterpret_cast<unsigned short *>(gsort + (size_t)W * P) + (size_t)w * P : nullptr;
+    if (wide) {
+        for (int k = threadIdx.x; k < P; k += blockDim.x) {
+            if (k < n) {
+                const int pk = xy[k];
+                a[k] = ((unsigned long long)(proj(pk, dy, dx) + (1LL << 32)) << 16) | (unsigned)(px(pk) + 32768);
+            } else {
+                a[k] = ~0ull;
+            }
+            pay[k] = (unsigned short)k;
+        }
+        __syncthreads();
+        cta_bitonic_kv(a, pay, P);
+    } else if (n > SORT_SMEM_N || !cta_fill_sort_any(a, P < (int)blockDim.x ? (int)blockDim.x : P, word)) {
         for (int k = threadIdx.x; k < P; k += blockDim.x) a[k] = word(k);
         __syncthreads();
         cta_bitonic_u64(a, P);
     }
+    auto akey = [&](int q) { return wide ? (long long)(a[q] >> 16) - (1LL << 32) : word_key(a[q]); };
     for (int k = threadIdx.x; k < n; k += blockDim.x)
-        orders[(size_t)w * n + k] = (unsigned short)word_index(a[k]);
+        orders[(size_t)w * n + k] = wide ? pay[k] : (unsigned short)word_index(a[k]);
     // every window at the first slope
     long long bw = KEY_INF;
     int ba = 0x7fffffff;
     for (int q = threadIdx.x; q + h - 1 < n; q += blockDim.x) {
-        const long long wd = word_key(a[q + h - 1]) - word_key(a[q]);
+        const long long wd = akey(q + h - 1) - akey(q);
         if (wd < bw) { bw = wd; ba = q; }
     }
     // the first event of a group carries its smallest index pair
@@ -727,7 +770,7 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
         if (lane == 0) {
             Cand c;
             c.w = bw;
-            c.t = word_key(a[ba]) + word_key(a[ba + h - 1]);
+            c.t = akey(ba) + akey(ba + h - 1);
             c.dy = dy;
             c.dx = dx;
             c.i = vertical ? -1 : (int)(mp >> 16);
@@ -1093,7 +1136,8 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
                                                const unsigned *__restrict__ ev,
                                                const unsigned *__restrict__ range, int W,
                                                const unsigned short *__restrict__ orders,
-                                               Cand *__restrict__ cands, int *__restrict__ meta)
+                                               Cand *__restrict__ cands, int *__restrict__ meta,
+                                               unsigned short *__restrict__ gpos)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -1102,8 +1146,12 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
     int *s_xy = reinterpret_cast<int *>(smem);
     const size_t off0 = XY_SMEM ? align16((size_t)n * 4) : 0;
     const size_t half = align16((size_t)n * 2);
-    unsigned short *order = reinterpret_cast<unsigned short *>(smem + off0 + warp * 2 * half);
-    unsigned short *pos = reinterpret_cast<unsigned short *>(smem + off0 + warp * 2 * half + half);
+    // order (and, when it fits, pos) of this warp in shared memory; for
+    // large n the positions live in the warp's own slice of gpos
+    const size_t per = gpos ? half : 2 * half;
+    unsigned short *order = reinterpret_cast<unsigned short *>(smem + off0 + warp * per);
+    unsigned short *pos = gpos ? gpos + (size_t)(blockIdx.x * nwarp + warp) * n
+                               : reinterpret_cast<unsigned short *>(smem + off0 + warp * per + half);
     if (XY_SMEM) {
         for (int k = threadIdx.x; k < n; k += blockDim.x) s_xy[k] = g_xy[k];
         __syncthreads();
@@ -1405,9 +1453,9 @@ static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Shared memory of one sweep CTA: the points (when kept on chip) plus the
 // order and position arrays of each of its sweeping warps.
-static size_t sweep_smem_bytes(int n, bool xy_smem, int spb)
+static size_t sweep_smem_bytes(int n, bool xy_smem, bool pos_smem, int spb)
 {
-    const size_t per = 2 * (((size_t)n * 2 + 15) / 16 * 16);
+    const size_t per = (pos_smem ? 2 : 1) * (((size_t)n * 2 + 15) / 16 * 16);
     const size_t xyb = xy_smem ? ((size_t)n * 4 + 15) / 16 * 16 : 0;
     return xyb + per * spb;
 }
@@ -1418,15 +1466,18 @@ void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int w
     p.h = h;
     p.emax = (long long)n * (n - 1) / 2;
     p.xy_smem = n <= 16384;
-    // sweeping warps per CTA limited by shared memory (order + pos each)
-    const size_t per = 2 * (((size_t)n * 2 + 15) / 16 * 16);
+    // sweeping warps per CTA limited by shared memory (order + pos each;
+    // order alone when both do not fit, the positions then in global memory)
+    const size_t half = ((size_t)n * 2 + 15) / 16 * 16;
     const size_t xyb = p.xy_smem ? ((size_t)n * 4 + 15) / 16 * 16 : 0;
     const size_t cap = 227 * 1024;
+    p.pos_smem = xyb + 2 * half <= cap;
+    const size_t per = (p.pos_smem ? 2 : 1) * half;
     int spb = (int)((cap - xyb) / per);
     spb = spb < 1 ? 1 : (spb > 8 ? 8 : spb);
     p.spb = spb;
     // resident sweep CTAs per SM (the sweep kernel is persistent)
-    const size_t sw_smem = sweep_smem_bytes(n, p.xy_smem, spb);
+    const size_t sw_smem = sweep_smem_bytes(n, p.xy_smem, p.pos_smem, spb);
     int per_sm = 0;
     if (p.xy_smem) {
         cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
@@ -1461,8 +1512,9 @@ void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int w
     p.C = sms;
 }
 
-size_t sweep_plan_bytes(int n, int W, int C, int S)
+size_t sweep_plan_bytes(const SweepPlan &p)
 {
+    const int n = p.n, W = p.W, C = p.C, S = p.S;
     const long long emax = (long long)n * (n - 1) / 2;
     int P = 1;
     while (P < n) P <<= 1;
@@ -1478,8 +1530,9 @@ size_t sweep_plan_bytes(int n, int W, int C, int S)
     b += emax > SEG_CAP ? a256((size_t)emax * 4) : 0;
     b += a256((size_t)2 * W * 4);
     b += a256((size_t)W * n * 2);
-    b += (n > SORT_SMEM_N) ? a256((size_t)W * P * 8) : 0;
+    b += (n > SORT_SMEM_N) ? a256((size_t)W * P * (n > 32768 ? 10 : 8)) : 0;
     b += a256((size_t)(2 * W + 8) * sizeof(Cand));
+    b += p.pos_smem ? 0 : a256((size_t)p.G * n * 2);
     return b;
 }
 
@@ -1501,8 +1554,9 @@ void sweep_plan_carve(SweepPlan &p, void *ws)
     p.ev2 = p.emax > SEG_CAP ? (unsigned *)take((size_t)p.emax * 4) : nullptr;
     p.range = (unsigned *)take((size_t)2 * p.W * 4);
     p.orders = (unsigned short *)take((size_t)p.W * p.n * 2);
-    p.gsort = (p.n > SORT_SMEM_N) ? (unsigned long long *)take((size_t)p.W * P * 8) : nullptr;
+    p.gsort = (p.n > SORT_SMEM_N) ? (unsigned long long *)take((size_t)p.W * P * (p.n > 32768 ? 10 : 8)) : nullptr;
     p.cands = (Cand *)take((size_t)(2 * p.W + 8) * sizeof(Cand));
+    p.gpos = p.pos_smem ? nullptr : (unsigned short *)take((size_t)p.G * p.n * 2);
 }
 
 const long long *sorted_sample(const SweepPlan &p)
@@ -1619,16 +1673,16 @@ cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, c
         k_sweep_init<<<p.W, 1024, init_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.meta, p.base, p.orders,
                                                   p.gsort, p.cands);
     }
-    const size_t sw_smem = sweep_smem_bytes(n, p.xy_smem, p.spb);
+    const size_t sw_smem = sweep_smem_bytes(n, p.xy_smem, p.pos_smem, p.spb);
     const int blocks = p.G / p.spb;
     if (p.xy_smem) {
         cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
         StageTimer _t(STAGE_SWEEP, st);
-        k_sweep<true><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta);
+        k_sweep<true><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta, p.gpos);
     } else {
         cudaFuncSetAttribute(k_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
         StageTimer _t(STAGE_SWEEP, st);
-        k_sweep<false><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta);
+        k_sweep<false><<<blocks, 32 * p.spb, sw_smem, st>>>(p.xy, n, p.h, p.ev, p.range, p.W, p.orders, p.cands, p.meta, p.gpos);
     }
     return cudaGetLastError();
 }
