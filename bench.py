@@ -243,6 +243,66 @@ def _hough(args):
     }), flush=True)
 
 
+# The paper's Table 1 (one exact solve on random point sets; its GPU is
+# named "GTX 720", a Kepler-class part), ms per solve: context only.
+PAPER_TABLE1_MS = {128: 0.98, 256: 4.22, 512: 35.3}
+
+
+def _table1(args):
+    """The sizes of the paper's Table 1 (n = 128, 256, 512): one exact solve
+    with the paper's own kernel layout (8x8-thread vertex blocks, one thread
+    block and a shared-memory bitonic sort per vertex, reduction), with the
+    per-slope warp kernel and with the kinetic sweep.  Device time per solve
+    (CUDA events on the launching stream), inputs resident in HBM, L2 flushed
+    (256 MB write) before every timed solve outside the events."""
+    import numpy as np
+    import torch
+
+    from paper_1510_01041_gb300 import build, datagen, lms
+    build.build()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rows = {}
+    for n in sorted(PAPER_TABLE1_MS):
+        x, y = datagen.line_with_outliers(n, 7)
+        xt = torch.from_numpy(x).to(dev)
+        yt = torch.from_numpy(y).to(dev)
+        rows[n] = {"paper_table1_ms": PAPER_TABLE1_MS[n]}
+        ref = None
+        for algo in ("paper", "plain", "sweep"):
+            out = torch.empty(lms.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+            for _ in range(args.warmup):
+                lms.fit(xt, yt, 0, algo, out=out)
+            torch.cuda.synchronize()
+            tot = 0.0
+            for _ in range(args.steps):
+                flush.fill_(1)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lms.fit(xt, yt, 0, algo, out=out)
+                b.record(stream)
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            r = lms.decode(out)[0]
+            got = tuple(r[k] for k in ("status", "w_num", "w_den", "s_num", "s_den", "t_num", "i", "j"))
+            ref = ref or got
+            if got != ref:
+                raise SystemExit(f"n={n}: {algo} disagrees: {got} vs {ref}")
+            rows[n][algo + "_ms"] = tot / args.steps
+    v = 1000.0 / rows[512]["paper_ms"]
+    print(json.dumps({
+        "metric": "exact LMS solves/sec at n=512 with the paper's kernel layout (Table 1 sizes)",
+        "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": rows[512]["paper_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": v / (1000.0 / PAPER_TABLE1_MS[512]), "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "one exact fit of line_with_outliers at n = 128, 256, 512 (paper Table 1 sizes)",
+                   "l2": "flushed before every timed solve (256 MB write, outside the events)",
+                   "baseline": "paper Table 1, GTX-class GPU of 2015 (context)"},
+        "rows_ms": {str(k): v2 for k, v2 in rows.items()},
+    }), flush=True)
+
+
 def _timed(fit, steps, warmup, flush, stream, barrier):
     """Per-step CUDA-event device time of `fit(k)` for steps warmup..warmup+steps-1."""
     import torch
@@ -266,9 +326,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="per-stage times to stderr")
-    ap.add_argument("--workload", choices=["single", "batched", "hough"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "hough", "table1"], default="single",
                     help="single: n=8192 fit (default); batched: 4096 uneven sets in one graph; "
-                         "hough: 64 edge images, Hough peaks refined by exact LMS")
+                         "hough: 64 edge images, Hough peaks refined by exact LMS; table1: the paper's "
+                         "kernel layout, the warp kernel and the sweep at n = 128, 256, 512")
     args = ap.parse_args()
     if args.impl == "reference":
         _reference_arm(args)
@@ -278,6 +339,9 @@ def main():
         return
     if args.workload == "hough":
         _hough(args)
+        return
+    if args.workload == "table1":
+        _table1(args)
         return
 
     import numpy as np

@@ -69,7 +69,10 @@ enum lms_algo {
     LMS_ALGO_AUTO = 0,        /* library choice */
     LMS_ALGO_PLAIN = 1,       /* sort the projections at every pairwise slope (n <= 1024) */
     LMS_ALGO_SWEEP = 2,       /* exact kinetic sweep over slope-sorted events */
-    LMS_ALGO_BNB = 3          /* seeded branch-and-bound over slope intervals + sweep of survivors */
+    LMS_ALGO_BNB = 3,         /* seeded branch-and-bound over slope intervals + sweep of survivors */
+    LMS_ALGO_PAPER = 4        /* the paper's own kernel layout (Sec. 3.6): 8x8-thread vertex blocks,
+                                 one thread block and a shared-memory bitonic sort per vertex,
+                                 then the reduction; int16, n <= 1024; an ablation of Table 1 */
 };
 
 typedef struct {

@@ -182,7 +182,10 @@ __global__ void k_min_ub(const long long *__restrict__ w, int nk, long long *__r
     if (threadIdx.x == 0) *ub = m;
 }
 
-constexpr unsigned long long BNB_MIN_RANGE = 512;   // events per swept range, at least
+#ifndef LMS_BNB_MIN_RANGE
+#define LMS_BNB_MIN_RANGE 512
+#endif
+constexpr unsigned long long BNB_MIN_RANGE = LMS_BNB_MIN_RANGE;   // events per swept range, at least
 constexpr double PRED_WINDOW = 0.35;   // radians around a predicted slope angle
 
 // Seed slopes.  With a predicted slope: half of them evenly spaced quantiles

@@ -78,6 +78,12 @@ int plain_elems(int n);
 cudaError_t launch_plain(const short *x, const short *y, int n, int h, Cand *cands, int nwarps_total,
                          cudaStream_t st);
 
+// ---------------------------------------------------------------- the paper's kernel layout
+size_t paper_bytes(int n);
+// vertices, then one block per vertex; *cands / *count: the records for the argmin
+cudaError_t launch_paper(const short *x, const short *y, int n, int h, void *ws, Cand **cands, long long *count,
+                         cudaStream_t st);
+
 // ---------------------------------------------------------------- sweep path
 constexpr int SEG_CAP = 16384;   // events a bucket may hold to be sorted in shared memory
 constexpr int BND_MAX = 16384;   // slope-bucket boundaries (power of two, shared memory)

@@ -16,7 +16,7 @@ from . import build as _build
 LMS_OK, LMS_ERR_ARG, LMS_ERR_RANGE, LMS_ERR_VERTICAL = 0, 1, 2, 3
 LMS_ERR_TIMEOUT, LMS_ERR_CUDA, LMS_ERR_WORKSPACE, LMS_ERR_UNSUPPORTED, LMS_ERR_INTERNAL = 4, 5, 6, 7, 8
 LMS_I16, LMS_F32 = 0, 1
-ALGOS = {"auto": 0, "plain": 1, "sweep": 2, "bnb": 3}
+ALGOS = {"auto": 0, "plain": 1, "sweep": 2, "bnb": 3, "paper": 4}
 
 # lms_result: 6 x int64, 3 x double, 4 x int32 = 88 bytes
 RESULT_DTYPE = np.dtype([("w_num", "<i8"), ("w_den", "<i8"), ("s_num", "<i8"), ("s_den", "<i8"),

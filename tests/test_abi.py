@@ -59,6 +59,11 @@ def test_argument_errors_before_any_device_work(L):
         rc = lib.lms_fit(vp(xp), vp(yp), n, h, dt, None, vp(res.ctypes.data), None)
         assert rc == L.LMS_ERR_ARG
     bad = L.options("plain")
+    bad.algorithm = 5                             # beyond the last algorithm
+    rc = lib.lms_fit(vp(x.ctypes.data), vp(x.ctypes.data), 8, 0, 0, ctypes.byref(bad),
+                     vp(res.ctypes.data), None)
+    assert rc == L.LMS_ERR_ARG
+    bad = L.options("plain")
     bad.reserved[1] = 1
     rc = lib.lms_fit(vp(x.ctypes.data), vp(x.ctypes.data), 8, 0, 0, ctypes.byref(bad),
                      vp(res.ctypes.data), None)

@@ -69,9 +69,9 @@ def _degenerate(rng, n):
     return x.astype(np.int16), y.astype(np.int16)
 
 
-@pytest.mark.parametrize("algorithm", ["plain", "sweep"])
+@pytest.mark.parametrize("algorithm", ["plain", "sweep", "paper"])
 def test_small_random_and_degenerate(L, orc, algorithm):
-    rng = np.random.default_rng(77 if algorithm == "plain" else 78)
+    rng = np.random.default_rng({"plain": 77, "sweep": 78, "paper": 79}[algorithm])
     for trial in range(60):
         n = int(rng.integers(2, 70))
         if trial % 2:
@@ -104,6 +104,20 @@ def test_plain_config_n512(L, orc, seed):
     o = orc.lms_i16(x, y, 0, "brute")
     assert same(gpu_fit(L, x, y, 0, "plain"), o)
     assert same(gpu_fit(L, x, y, 0, "sweep"), o)
+    assert same(gpu_fit(L, x, y, 0, "paper"), o)
+
+
+@pytest.mark.parametrize("n", [128, 256, 300, 1024])
+def test_paper_layout_table1_sizes(L, orc, n):
+    """The paper's own kernel layout (8 x 8 vertex blocks, a thread block and a
+    bitonic sort per vertex) at the sizes of its Table 1, a size that is not a
+    power of two (padding) and its largest supported size."""
+    x, y = datagen.line_with_outliers(n, 40 + n)
+    o = orc.lms_i16(x, y, 0, "brute")
+    assert same(gpu_fit(L, x, y, 0, "paper"), o)
+    xs, ys, _ = datagen.sloped(n, 50 + n, 0.3)
+    o = orc.lms_i16(xs, ys, 0, "brute")
+    assert same(gpu_fit(L, xs, ys, 0, "paper"), o)
 
 
 @pytest.mark.parametrize("n", [300, 777, 1024, 2048])
