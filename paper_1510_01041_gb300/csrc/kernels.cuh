@@ -107,12 +107,13 @@ struct SweepPlan {
     long long *skeys2;         // [S] merge ping-pong
     long long *bnd;            // [BND_MAX] bucket boundaries, padded with INT64_MAX
     int *meta;                 // [16] 0 nbnd, 1 P2, 2 oversize count, 3 error flags, 4 range counter,
-                               //      5 pairs with distinct x (restricted count)
+                               //      5 pairs with distinct x, 6 listed kept pairs (restricted count)
     unsigned *hist;            // [C][BND_MAX] per-CTA bucket counts, then offsets
     unsigned *base;            // [BND_MAX + 1] bucket starts; base[NB] = E
     int *oversize;             // [BND_MAX] buckets too large for the shared-memory sort
     unsigned *ev;              // [emax] events
-    unsigned *ev2;             // [emax] merge copy for buckets above SEG_CAP (null if emax <= SEG_CAP)
+    unsigned *ev2;             // [emax] merge copy for buckets above SEG_CAP (null if emax <= SEG_CAP);
+                               //        before the bucket sorts, the list of kept pairs of a restricted count
     unsigned *range;           // [2W] range event bounds
     unsigned short *orders;    // [W][n] start orders
     unsigned long long *gsort; // [W][P] global sort scratch when n > SORT_SMEM_N

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(1024) k_splitters(const long long *__restrict_
     int P2 = 1;
     while (P2 <= nbnd) P2 <<= 1;
     for (int k = nbnd + threadIdx.x; k < P2; k += blockDim.x) bnd[k] = KEY_INF;
-    if (threadIdx.x == 0) { meta[0] = nbnd; meta[1] = P2; meta[2] = 0; meta[3] = 0; meta[5] = 0; }
+    if (threadIdx.x == 0) { meta[0] = nbnd; meta[1] = P2; meta[2] = 0; meta[3] = 0; meta[5] = 0; meta[6] = 0; }
 }
 
 // ---------------------------------------------------------------- count / scatter
@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
                                                               unsigned *__restrict__ ev,
                                                               const unsigned char *__restrict__ keep,
                                                               const float2 *__restrict__ pre, int npre,
-                                                              int *__restrict__ meta_mut)
+                                                              int *__restrict__ meta_mut,
+                                                              unsigned *__restrict__ list)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
@@ -240,6 +241,15 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
             if (keep && !keep[b]) continue;
             const unsigned slot = atomicAdd(&s_cnt[b], 1u);
             if (SCATTER) ev[slot] = ev_pack(i, j, false);
+            if (!SCATTER && list) {
+                // the kept pair to the compact list (one atomic per warp)
+                const unsigned am = __activemask();
+                const int lead = __ffs(am) - 1, me = threadIdx.x & 31;
+                unsigned at = 0;
+                if (me == lead) at = atomicAdd(reinterpret_cast<unsigned *>(meta_mut + 6), (unsigned)__popc(am));
+                at = __shfl_sync(am, at, lead) + __popc(am & ((1u << me) - 1u));
+                list[at] = ((unsigned)i << 16) | (unsigned)j;
+            }
         }
     }
     if (!SCATTER) {
@@ -250,6 +260,57 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
         __syncthreads();
         for (int k = threadIdx.x; k < NB; k += blockDim.x) my_hist[k] = s_cnt[k];
     }
+}
+
+// The listed pairs to their buckets (the order inside a bucket is left to
+// the bucket sort); cursor[b] starts at the bucket's first slot.  Each CTA
+// takes a contiguous part of the list, counts it per bucket in shared
+// memory, reserves one range per bucket with a single global atomic, then
+// places its pairs (bucket indices recomputed from the exact keys).
+template <class G>
+__global__ void __launch_bounds__(CNT_THREADS) k_scatter_list(const void *__restrict__ pts,
+                                                              const long long *__restrict__ bnd,
+                                                              const int *__restrict__ meta,
+                                                              const unsigned *__restrict__ list,
+                                                              unsigned *__restrict__ cursor,
+                                                              unsigned *__restrict__ ev)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long *s_bnd = reinterpret_cast<long long *>(smem);
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
+    const int P2 = meta[1], NB = meta[0] + 1;
+    for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
+    for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0u;
+    __syncthreads();
+    const unsigned m = (unsigned)meta[6];
+    const unsigned per = (m + gridDim.x - 1) / gridDim.x;
+    const unsigned q0 = min(m, blockIdx.x * per), q1 = min(m, q0 + per);
+    auto bucket = [&](unsigned pr, int &b) {
+        long long key;
+        if (!G::key(pts, (int)(pr >> 16), (int)(pr & 0xffffu), key)) return false;
+        b = bucket_of(s_bnd, P2, key);
+        return true;
+    };
+    for (unsigned q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        int b;
+        if (bucket(list[q], b)) atomicAdd(&s_cnt[b], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NB; k += blockDim.x)
+        if (s_cnt[k]) s_cnt[k] = atomicAdd(&cursor[k], s_cnt[k]);
+    __syncthreads();
+    for (unsigned q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        const unsigned pr = list[q];
+        int b;
+        if (bucket(pr, b)) ev[atomicAdd(&s_cnt[b], 1u)] = ev_pack((int)(pr >> 16), (int)(pr & 0xffffu), false);
+    }
+}
+
+__global__ void k_copy_starts(const unsigned *__restrict__ base, const int *__restrict__ meta,
+                              unsigned *__restrict__ cursor)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b <= meta[0]) cursor[b] = base[b];
 }
 
 // Per bucket: the number of valid sampled keys in it (the sample is sorted
@@ -1590,7 +1651,8 @@ static cudaError_t events_count(const SweepPlan &p, const void *pts, const unsig
     {
         StageTimer _t(STAGE_COUNT_PAIRS, st);
         k_bucket_pairs<false, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, p.n, p.bnd, p.meta, p.hist, nullptr, nullptr,
-                                                                    keep, pre, npre, p.meta);
+                                                                    keep, pre, npre, p.meta,
+                                                                    (pre && p.ev2) ? p.ev2 : nullptr);
     }
     { StageTimer _t(STAGE_PREFIX, st); k_bucket_prefix<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.hist, p.C, p.meta, p.base); }
     { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta); }
@@ -1631,7 +1693,19 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
     const int n = p.n;
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
     cudaFuncSetAttribute(k_bucket_pairs<true, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    { StageTimer _t(STAGE_SCATTER, st); k_bucket_pairs<true, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep, pre, npre, p.meta); }
+    if (pre && p.ev2) {
+        // the restricted count listed the kept pairs: place only those
+        unsigned *cursor = p.hist;
+        { StageTimer _t(STAGE_SCATTER, st); k_copy_starts<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.base, p.meta, cursor); }
+        const size_t bsm = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
+        cudaFuncSetAttribute(k_scatter_list<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+        StageTimer _t(STAGE_SCATTER, st);
+        k_scatter_list<G><<<p.C, CNT_THREADS, bsm, st>>>(pts, p.bnd, p.meta, p.ev2, cursor, p.ev);
+    } else {
+        StageTimer _t(STAGE_SCATTER, st);
+        k_bucket_pairs<true, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep,
+                                                                   pre, npre, p.meta, nullptr);
+    }
     const size_t seg_smem = (size_t)SEG_CAP * 12;
     cudaFuncSetAttribute(k_segsort<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
     { StageTimer _t(STAGE_SEGSORT, st); k_segsort<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, p.base, p.bnd, p.meta, p.oversize); }
