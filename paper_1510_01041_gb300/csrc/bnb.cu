@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(1024) k_score_dyadic(const int *__restrict__ x
         long long *a = in_smem ? reinterpret_cast<long long *>(smem) : gscratch + (size_t)blockIdx.x * 2 * P;
         const int xc = *xcp;
         auto z = [&](int k) { return k < n ? zscaled(xy[k], xc, K) : I64_MAX; };
-        if (!in_smem || !cta_fill_sort_any(a, P < (int)blockDim.x ? (int)blockDim.x : P, z)) {
+        const int Ps = P < (int)blockDim.x ? (int)blockDim.x : P;
+        if (!in_smem || !cta_fill_merge_sort_any(a, a + Ps, Ps, z)) {
             for (int k = threadIdx.x; k < P; k += blockDim.x) a[k] = z(k);
             __syncthreads();
             cta_bitonic_i64(a, P);
@@ -155,7 +156,8 @@ __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, in
         auto zhi = [&](int k) {
             return k < n ? max(zscaled(xy[k], xc, Klo), zscaled(xy[k], xc, Khi)) : I64_MAX;
         };
-        if (!in_smem || !cta_fill_sort_any(lo, Ps, zlo) || !cta_fill_sort_any(hi, Ps, zhi)) {
+        if (!in_smem || !cta_fill_merge_sort_any(lo, hi + Ps, Ps, zlo) ||
+            !cta_fill_merge_sort_any(hi, hi + Ps, Ps, zhi)) {
             for (int k = threadIdx.x; k < P; k += blockDim.x) {
                 lo[k] = zlo(k);
                 hi[k] = zhi(k);
@@ -318,8 +320,9 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         k_pick_seeds<<<1, 128, 0, st>>>(sorted_sample(p), p.S, pred_dev, seed_mode, BNB_SEEDS, seed_keys);
     }
     const int Ps = P < 1024 ? 1024 : P;   // the shared-memory sorts fill whole 1024-thread CTAs
-    const size_t one_sort = (n <= SORT_SMEM_N) ? (size_t)Ps * 8 : 0;
-    const size_t two_sorts = (n <= SORT_SMEM_N) ? (size_t)2 * Ps * 8 : 0;
+    // one sorted array plus merge scratch; two sorted arrays plus scratch
+    const size_t one_sort = (n <= SORT_SMEM_N) ? (size_t)2 * Ps * 8 : 0;
+    const size_t two_sorts = (n <= SORT_SMEM_N) ? (size_t)3 * Ps * 8 : 0;
     cudaFuncSetAttribute(k_score_dyadic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one_sort);
     cudaFuncSetAttribute(k_node_lb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_sorts);
     {

@@ -204,6 +204,92 @@ __device__ __forceinline__ void cta_sort_blocked(T (&v)[IPT], T *s, int P)
     }
 }
 
+// Ascending merge sort of P = IPT * blockDim.x words held IPT per thread in
+// v (thread t holds positions t IPT ..), result in s; s2 is scratch of P
+// words.  Each thread sorts its IPT words in registers (bitonic network),
+// then runs of width w = IPT, 2 IPT, .. are merged pairwise: thread t
+// produces the IPT outputs starting at t IPT of its merged run, finding its
+// start on the merge path by a binary search (the diagonal split with
+// A[i - 1] <= B[d - i], ties taken from the left run) and merging
+// sequentially.  Every thread of the CTA calls it.
+template <int IPT, class T>
+__device__ __forceinline__ void cta_merge_sort(T (&v)[IPT], T *s, T *s2, int P)
+{
+#pragma unroll
+    for (int k = 2; k <= IPT; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j >= 1; j >>= 1) {
+#pragma unroll
+            for (int r = 0; r < IPT; ++r) {
+                const int q = r ^ j;
+                if (q > r) {
+                    const bool up = (r & k) == 0;
+                    const T a = v[r], b = v[q];
+                    if ((a > b) == up) { v[r] = b; v[q] = a; }
+                }
+            }
+        }
+    }
+    const int t = threadIdx.x;
+    const int o = t * IPT;
+    // the number of merge levels decides where the first write goes so that
+    // the last one lands in s
+    int levels = 0;
+    for (int w = IPT; w < P; w <<= 1) ++levels;
+    T *src = (levels & 1) ? s2 : s, *dst = (levels & 1) ? s : s2;
+#pragma unroll
+    for (int r = 0; r < IPT; ++r) src[o + r] = v[r];
+    __syncthreads();
+    for (int w = IPT; w < P; w <<= 1) {
+        const int base = o & ~(2 * w - 1);       // start of this thread's merged run
+        const int d = o - base;                   // output offset inside it
+        const T *A = src + base, *B = src + base + w;
+        int lo = d > w ? d - w : 0, hi = d < w ? d : w;
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (A[m] <= B[d - 1 - m]) lo = m + 1; else hi = m;
+        }
+        int ia = lo, ib = d - lo;
+#pragma unroll
+        for (int r = 0; r < IPT; ++r) {
+            const bool take_a = ib >= w || (ia < w && A[ia] <= B[ib]);
+            v[r] = take_a ? A[ia] : B[ib];
+            if (take_a) ++ia; else ++ib;
+        }
+#pragma unroll
+        for (int r = 0; r < IPT; ++r) dst[o + r] = v[r];
+        __syncthreads();
+        T *tmp = src; src = dst; dst = tmp;
+    }
+}
+
+// Fills P = IPT * blockDim.x words with fill(position) and merge-sorts them
+// into s (s2: scratch of P words).
+template <int IPT, class T, class F>
+__device__ __forceinline__ void cta_fill_merge_sort(T *s, T *s2, int P, F fill)
+{
+    T v[IPT];
+    const int base = threadIdx.x * IPT;
+#pragma unroll
+    for (int r = 0; r < IPT; ++r) v[r] = fill(base + r);
+    cta_merge_sort<IPT>(v, s, s2, P);
+}
+
+// The same for P / blockDim.x in {1, 2, 4, 8, 16}; false (nothing done)
+// for other sizes.
+template <class T, class F>
+__device__ bool cta_fill_merge_sort_any(T *s, T *s2, int P, F fill)
+{
+    switch (P / (int)blockDim.x) {
+        case 1: cta_fill_merge_sort<1>(s, s2, P, fill); return true;
+        case 2: cta_fill_merge_sort<2>(s, s2, P, fill); return true;
+        case 4: cta_fill_merge_sort<4>(s, s2, P, fill); return true;
+        case 8: cta_fill_merge_sort<8>(s, s2, P, fill); return true;
+        case 16: cta_fill_merge_sort<16>(s, s2, P, fill); return true;
+        default: return false;
+    }
+}
+
 // Fills P = IPT * blockDim.x words with fill(position), sorts them and
 // leaves the ascending result in s.
 template <int IPT, class T, class F>

@@ -462,7 +462,8 @@ __global__ void __launch_bounds__(1024) k_segsort(const void *__restrict__ xy, u
                 return ((unsigned long long)(event_key<G>(xy, e) - klo) << 32) | pair_of(e);
             };
             __syncthreads();
-            if (cta_fill_sort_any(w, P < (int)blockDim.x ? (int)blockDim.x : P, word)) {
+            const int Pw = P < (int)blockDim.x ? (int)blockDim.x : P;
+            if (cta_fill_sort_any(w, Pw, word)) {
                 for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
                     const unsigned long long v = w[k];
                     const bool cont = k > 0 && (w[k - 1] >> 32) == (v >> 32);
@@ -787,7 +788,9 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
         }
         __syncthreads();
         cta_bitonic_kv(a, pay, P);
-    } else if (n > SORT_SMEM_N || !cta_fill_sort_any(a, P < (int)blockDim.x ? (int)blockDim.x : P, word)) {
+    } else if (n > SORT_SMEM_N ||
+               !cta_fill_merge_sort_any(a, a + (P < (int)blockDim.x ? (int)blockDim.x : P),
+                                        P < (int)blockDim.x ? (int)blockDim.x : P, word)) {
         for (int k = threadIdx.x; k < P; k += blockDim.x) a[k] = word(k);
         __syncthreads();
         cta_bitonic_u64(a, P);
@@ -971,6 +974,14 @@ __device__ unsigned group_end(const int *s_xy, const int *__restrict__ g_xy, con
         event_slope<XY_SMEM>(s_xy, g_xy, ev[q], dy, dx);
         return (long long)dy * dx0 == (long long)dy0 * dx;
     };
+    // most groups end within the next 32 events: one coalesced look first
+    {
+        const unsigned q = known + lane;
+        const unsigned out = __ballot_sync(FULL, q < end && !ev_cont(ev[q]));
+        if (out) return known + __ffs(out) - 1;
+        if (known + 32 >= end) return end;
+        known += 32;
+    }
     // lo: last index known inside the group; hi: first index known outside
     unsigned lo = known - 1, hi = end;
     {
@@ -1371,34 +1382,54 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
             // depend on the order inside a run.)
             const unsigned actm = __ballot_sync(FULL, act);
             const unsigned runm = __ballot_sync(FULL, act && !simple);
+            const int top = lo + h - 1, bot = hi - h + 1;
             bool conflict = false;
-            if (runm == 0 && fold_ok) {
-                // All active lanes are simple swaps [p, p + 1].  With H = h - 1,
-                // earlier e and later l conflict only if e - l lies in [-2, 2]
-                // (neighbours), [H - 1, H] (l's window top) or [-H, 1 - H] (l's
-                // window bottom): in every case e - l = -2..2 modulo H.  So the
-                // residues f = p mod H of conflicting lanes are within 2 of each
-                // other, cyclically, and then share a cell of width 4 in one of
-                // three grids: f / 4, (f + 2) / 4, ((f + 2) mod H) / 4 (the last
-                // catches pairs across the wrap).  Lanes sharing a cell are
-                // treated as conflicting: a superset, so the cut stays safe.
+            if (fold_ok) {
+                // Pairs of simple swaps [p, p + 1]: with H = h - 1, earlier e
+                // and later l conflict only if e - l lies in [-2, 2]
+                // (neighbours), [H - 1, H] (l's window top) or [-H, 1 - H]
+                // (l's window bottom): in every case e - l = -2..2 modulo H.
+                // So the residues f = p mod H of conflicting lanes are within 2
+                // of each other, cyclically, and then share a cell of width 4
+                // in one of three grids: f / 4, (f + 2) / 4, ((f + 2) mod H) / 4
+                // (the last catches pairs across the wrap).  Lanes sharing a
+                // cell are treated as conflicting: a superset, so the cut stays
+                // safe.
+                const bool sim = act && simple;
                 int f = pa;
                 if (f >= H) f -= H;
                 if (f >= H) f -= H;
                 int f2 = f + 2;
                 const unsigned none = 0x40000000u | (unsigned)lane;
-                const unsigned cA = act ? (unsigned)(f >> 2) : none;
-                const unsigned cB = act ? (unsigned)(f2 >> 2) : none;
+                const unsigned cA = sim ? (unsigned)(f >> 2) : none;
+                const unsigned cB = sim ? (unsigned)(f2 >> 2) : none;
                 if (f2 >= H) f2 -= H;
-                const unsigned cC = act ? (unsigned)(f2 >> 2) : none;
+                const unsigned cC = sim ? (unsigned)(f2 >> 2) : none;
                 const unsigned grp = __match_any_sync(FULL, (unsigned)(gfirst + 1));
                 const unsigned nearm = __match_any_sync(FULL, cA) | __match_any_sync(FULL, cB) |
                                        __match_any_sync(FULL, cC);
-                conflict = act && (nearm & actm & ~grp & lanemask_lt) != 0u;
+                conflict = sim && (nearm & actm & ~runm & ~grp & lanemask_lt) != 0u;
+                // Pairs with a run leader (a longer rewritten block), checked
+                // exactly in both directions, one leader at a time.
+                for (unsigned rm = runm; rm; rm &= rm - 1) {
+                    const int t = __ffs(rm) - 1;
+                    const int tlo = __shfl_sync(FULL, lo, t), thi = __shfl_sync(FULL, hi, t);
+                    const int tg = __shfl_sync(FULL, gfirst, t);
+                    const int ttop = tlo + h - 1, tbot = thi - h + 1;
+                    const bool other = act && gfirst != tg;
+                    // a later lane reads what the leader rewrites
+                    if (other && lane > t &&
+                        ((tlo <= hi + 1 && thi >= lo - 1) || (top >= tlo && top <= thi) || (bot >= tlo && bot <= thi)))
+                        conflict = true;
+                    // the leader reads what an earlier lane rewrites
+                    const bool hit = other && lane < t &&
+                                     ((lo <= thi + 1 && hi >= tlo - 1) || (ttop >= lo && ttop <= hi) ||
+                                      (tbot >= lo && tbot <= hi));
+                    if (__any_sync(FULL, hit) && lane == t) conflict = true;
+                }
             } else {
                 const unsigned me = act ? (((unsigned)lo << 16) | ((unsigned)(hi - lo) << 6) | (unsigned)(gfirst + 1))
                                         : 0xffffffffu;
-                const int top = lo + h - 1, bot = hi - h + 1;
                 for (int t = 0; t < 31; ++t) {
                     const unsigned o = __shfl_sync(FULL, me, t);
                     if (!act || t >= lane || o == 0xffffffffu || (o & 0x3fu) == (unsigned)(gfirst + 1)) continue;
@@ -1417,7 +1448,6 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
             if (cut > 0) {
                 // ---- parallel events: window reads, then the rewrites
                 const bool go = act && lane < cut;
-                const int top = lo + h - 1, bot = hi - h + 1;
                 __syncwarp();
                 if (go) {
                     if (simple) {
@@ -1740,7 +1770,7 @@ cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, c
     if (e != cudaSuccess) return e;
     int P = 1;
     while (P < n) P <<= 1;
-    const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)(P < 1024 ? 1024 : P) * 8 : 0;
+    const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)(P < 1024 ? 1024 : P) * 16 : 0;   // words + merge scratch
     cudaFuncSetAttribute(k_sweep_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)init_smem);
     {
         StageTimer _t(STAGE_INIT, st);
