@@ -430,7 +430,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     }
     // slope covers of the runs of kept buckets for the pair passes: bucket b
     // holds keys [bnd[b - 1], bnd[b]), a key being floor(slope 2^32); each
-    // cover is widened by more than the float slope error (2^-22 relative)
+    // cover is widened by more than the float slope error (2^-21 relative)
     // and rounded outward; at most PRE_MAX covers (closest runs merged)
     std::vector<std::pair<double, double>> cov;
     unsigned kept_buckets = 0;

@@ -27,6 +27,8 @@
 //             window there
 //   sweep     per sweeper (one warp): apply the events in slope order,
 //             re-score the touched windows, keep the best
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -223,13 +225,25 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
         tile_decode(q, bi, bj);
         const int i = bi * TILE + il;
         if (i >= n) continue;
+        // int16 points: this thread's fixed point, loaded once per tile
+        int Pi = 0;
+        if constexpr (std::is_same<G, KeyI16>::value) Pi = __ldg(static_cast<const int *>(pts) + i);
 #pragma unroll 4
         for (int jj = 0; jj < JPT; ++jj) {
             const int j = bj * TILE + jl0 + jj;
             if (j <= i || j >= n) continue;
             if (pre) {
                 float sl;
-                if (!G::approx(pts, i, j, sl)) continue;
+                if constexpr (std::is_same<G, KeyI16>::value) {
+                    // dy / dx by the fast division (relative error below 2^-21;
+                    // exact small-integer operands)
+                    const int Pj = __ldg(static_cast<const int *>(pts) + j);
+                    const int dx = px(Pj) - px(Pi);
+                    if (dx == 0) continue;
+                    sl = __fdividef((float)(py(Pj) - py(Pi)), (float)dx);
+                } else {
+                    if (!G::approx(pts, i, j, sl)) continue;
+                }
                 ++nvalid;
                 bool cand = false;
                 for (int r = 0; r < npre; ++r) cand |= (sl >= s_pre[r].x) & (sl <= s_pre[r].y);
