@@ -225,22 +225,38 @@ LMS_API int lms_fit_batched(lms_batch_plan *plan, const void *x, const void *y, 
  * +-nms_rho of a taken peak; the points within band_px of each peak's line
  * (rho at the bin centre) are fitted by exact LMS, with x and y swapped for
  * near-vertical peaks (|sin| < |cos|).
+ *   max_points   0: fit every band point.  Otherwise a band holding more
+ *             than max_points points is randomly subsampled before the fit
+ *             (Sec. 5: the supporting points may be sampled to save time):
+ *             point u of set k (k = image * top_k + peak, u its raster rank
+ *             in the band) is kept iff the upper 32 bits of SplitMix64's
+ *             output function applied to sample_seed ^ ((k << 32 | u) *
+ *             0x9E3779B97F4A7C15) are below floor(2^32 max_points / count):
+ *             about max_points points, reproducible from the seed.  The fit
+ *             is the exact LMS of the kept points.
  *   cos_sin   optional device table of n_theta (cos, sin) float pairs; NULL:
  *             computed on the host as cos/sin in double rounded to float.
  *   acc_out   optional device int32 [B][n_theta][n_rho] receiving the votes.
  *   out       host array of B * top_k lms_line (peaks in greedy order).
+ * Besides the LMS fit, each line carries the ordinary least-squares line of
+ * the same fitted points (exact integer sums, one double division), for
+ * comparisons such as the paper's Sec. 5 experiments.
  * Synchronous; allocates its scratch.
  */
 typedef struct {
     int32_t theta_index, rho_index, votes;   /* the peak; theta_index = -1 if the image had fewer peaks */
     int32_t transposed;                      /* 1: x and y swapped before the fit */
     int32_t npoints;                         /* points within the band */
-    int32_t pad[3];
+    int32_t nfit;                            /* points fitted (npoints unless subsampled) */
+    int32_t pad[2];
     lms_result fit;                          /* status LMS_ERR_ARG if fewer than 2 points */
+    double ols_theta1, ols_theta2;           /* least squares y = theta1 x + theta2 of the fitted points
+                                                (fit frame); NaN when undefined (all x equal, < 2 points) */
 } lms_line;
 LMS_API int lms_hough_refine(const uint8_t *edges, int64_t B, int32_t H, int32_t W, int32_t n_theta,
                              int32_t n_rho, int32_t top_k, float band_px, int32_t nms_theta, int32_t nms_rho,
-                             const float *cos_sin, int32_t *acc_out, lms_line *out, lms_stream_t stream);
+                             int32_t max_points, uint64_t sample_seed, const float *cos_sin, int32_t *acc_out,
+                             lms_line *out, lms_stream_t stream);
 
 /*
  * lms_workspace_size -- device bytes one lms_fit of this size needs.

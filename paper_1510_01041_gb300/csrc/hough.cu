@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <numeric>
 #include <vector>
 
 #include "common.cuh"
@@ -327,12 +328,93 @@ __global__ void k_compact_sets(const short *__restrict__ sx, const short *__rest
     }
 }
 
+// SplitMix64's output function (Steele, Lea and Flood, 2014) on a counter:
+// the upper 32 bits decide whether point u of set k is kept.
+__device__ __forceinline__ unsigned keep_hash(unsigned long long seed, unsigned long long k, unsigned long long u)
+{
+    unsigned long long z = seed ^ (((k << 32) | u) * 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (unsigned)(z >> 32);
+}
+
+// Random subsampling of the fitted sets, one CTA per set: COUNT = true
+// writes the kept count of each set, COUNT = false writes the kept points at
+// dst (raster order kept: a block-wide rank by ballots).  thr[u] = 0 keeps
+// every point.
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_subsample(const short *__restrict__ sx, const short *__restrict__ sy,
+                                                   const long long *__restrict__ src,
+                                                   const long long *__restrict__ cnt,
+                                                   const unsigned *__restrict__ thr,
+                                                   const int *__restrict__ set_id, unsigned long long seed,
+                                                   const long long *__restrict__ dst, int *__restrict__ kept,
+                                                   short *__restrict__ tx, short *__restrict__ ty)
+{
+    __shared__ int s_warp[8];
+    const int u = blockIdx.x;
+    const long long a = src[u], m = cnt[u];
+    const unsigned th = thr[u];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long run = 0;
+    for (long long c0 = 0; c0 < m; c0 += blockDim.x) {
+        const long long q = c0 + threadIdx.x;
+        const bool keep = q < m && (th == 0u || keep_hash(seed, (unsigned long long)set_id[u], (unsigned long long)q) < th);
+        const unsigned bal = __ballot_sync(FULL, keep);
+        if (lane == 0) s_warp[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) before += s_warp[w];
+            total += s_warp[w];
+        }
+        if (!COUNT && keep) {
+            const long long o = dst[u] + run + before + __popc(bal & ((1u << lane) - 1u));
+            tx[o] = sx[a + q];
+            ty[o] = sy[a + q];
+        }
+        run += total;
+        __syncthreads();
+    }
+    if (COUNT && threadIdx.x == 0) kept[u] = (int)run;
+}
+
+// Exact sums n, sum x, sum y, sum x^2, sum x y of each fitted set (int16
+// points, at most 32768 of them: every sum fits in int64).
+__global__ void __launch_bounds__(256) k_ols_sums(const short *__restrict__ tx, const short *__restrict__ ty,
+                                                  const long long *__restrict__ dst, long long *__restrict__ sums)
+{
+    __shared__ long long s_part[8][5];
+    const int u = blockIdx.x;
+    const long long a = dst[u], m = dst[u + 1] - a;
+    long long v[5] = {0, 0, 0, 0, 0};
+    for (long long q = threadIdx.x; q < m; q += blockDim.x) {
+        const long long x = tx[a + q], y = ty[a + q];
+        v[0] += 1; v[1] += x; v[2] += y; v[3] += x * x; v[4] += x * y;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
+        if (lane == 0) s_part[warp][k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w][threadIdx.x];
+        sums[5 * (size_t)u + threadIdx.x] = t;
+    }
+}
+
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 }  // namespace
 }  // namespace lms
 
 using namespace lms;
+
+static_assert(sizeof(lms_line) == 136, "lms_line layout");
 
 extern "C" {
 
@@ -348,12 +430,13 @@ static void make_tables(int n_theta, std::vector<float> &cs)
 }
 
 int lms_hough_refine(const uint8_t *edges, int64_t B, int32_t H, int32_t W, int32_t n_theta, int32_t n_rho,
-                     int32_t top_k, float band_px, int32_t nms_theta, int32_t nms_rho, const float *cos_sin,
-                     int32_t *acc_out, lms_line *out, lms_stream_t stream)
+                     int32_t top_k, float band_px, int32_t nms_theta, int32_t nms_rho, int32_t max_points,
+                     uint64_t sample_seed, const float *cos_sin, int32_t *acc_out, lms_line *out,
+                     lms_stream_t stream)
 {
     if (!edges || !out || B < 1 || H < 2 || W < 2 || H > 32768 || W > 32768) return LMS_ERR_ARG;
     if (n_theta < 1 || n_theta > 65535 || n_rho < 2 || n_rho > 65535 || top_k < 1 || top_k > 64) return LMS_ERR_ARG;
-    if (nms_theta < 0 || nms_rho < 0 || !(band_px >= 0.f)) return LMS_ERR_ARG;
+    if (nms_theta < 0 || nms_rho < 0 || !(band_px >= 0.f) || max_points < 0) return LMS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const long long HW = (long long)H * W;
     const int nchunk = (int)((HW + CH - 1) / CH);
@@ -463,44 +546,93 @@ int lms_hough_refine(const uint8_t *edges, int64_t B, int32_t H, int32_t W, int3
         k_set_finish<<<(unsigned)(B * top_k), 1024, 32768 * 4, st>>>(pts, img_off, cs, peaks, top_k, soff, keys, sx,
                                                                     sy, err);
     }
-    // exact LMS of every set of a real peak with at least two points
+    // exact LMS of every set of a real peak with at least two points (after
+    // the optional subsampling), and the least-squares sums of the same points
     std::vector<int> fit_set;
-    std::vector<long long> src, dst(1, 0);
+    std::vector<long long> src, cntv;
+    std::vector<unsigned> thr;
     for (long long k = 0; k < B * top_k; ++k) {
         if (hpk[3 * k] < 0 || hcnt[k] < 2) continue;
         fit_set.push_back((int)k);
         src.push_back(hsoff[k]);
-        dst.push_back(dst.back() + hcnt[k]);
+        cntv.push_back(hcnt[k]);
+        const bool sub = max_points > 0 && hcnt[k] > max_points;
+        unsigned t = 0;
+        if (sub) {
+            t = (unsigned)(((unsigned long long)max_points << 32) / (unsigned long long)hcnt[k]);
+            if (t == 0) t = 1;
+        }
+        thr.push_back(t);
     }
     std::vector<lms_result> res(fit_set.size());
+    std::vector<long long> sums(5 * fit_set.size(), 0);
+    std::vector<long long> dst(fit_set.size() + 1, 0);
     if (!fit_set.empty()) {
         const size_t F = fit_set.size();
         lms_batch_plan *plan = nullptr;
-        long long *d_src = nullptr, *d_dst = nullptr;
+        long long *d_src = nullptr, *d_dst = nullptr, *d_cnt = nullptr, *d_sums = nullptr;
+        unsigned *d_thr = nullptr;
+        int *d_id = nullptr, *d_kept = nullptr;
         lms_result *d_res = nullptr;
         short *tx = nullptr, *ty = nullptr;
+        const long long all = std::accumulate(cntv.begin(), cntv.end(), 0LL);
         if (cudaMalloc(&d_src, sizeof(long long) * F) != cudaSuccess ||
+            cudaMalloc(&d_cnt, sizeof(long long) * F) != cudaSuccess ||
             cudaMalloc(&d_dst, sizeof(long long) * (F + 1)) != cudaSuccess ||
+            cudaMalloc(&d_thr, sizeof(unsigned) * F) != cudaSuccess ||
+            cudaMalloc(&d_id, sizeof(int) * F) != cudaSuccess ||
+            cudaMalloc(&d_kept, sizeof(int) * F) != cudaSuccess ||
+            cudaMalloc(&d_sums, sizeof(long long) * 5 * F) != cudaSuccess ||
             cudaMalloc(&d_res, sizeof(lms_result) * F) != cudaSuccess ||
-            cudaMalloc(&tx, sizeof(short) * dst.back()) != cudaSuccess ||
-            cudaMalloc(&ty, sizeof(short) * dst.back()) != cudaSuccess) {
+            cudaMalloc(&tx, sizeof(short) * std::max(1LL, all)) != cudaSuccess ||
+            cudaMalloc(&ty, sizeof(short) * std::max(1LL, all)) != cudaSuccess) {
             cudaGetLastError();
             rc = LMS_ERR_CUDA;
         }
         if (rc == LMS_OK) {
             cudaMemcpyAsync(d_src, src.data(), sizeof(long long) * F, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(d_cnt, cntv.data(), sizeof(long long) * F, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(d_thr, thr.data(), sizeof(unsigned) * F, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(d_id, fit_set.data(), sizeof(int) * F, cudaMemcpyHostToDevice, st);
+            std::vector<int> kept(F);
+            if (max_points > 0) {
+                {
+                    StageTimer _t(STAGE_OTHER, st);
+                    k_subsample<true><<<(unsigned)F, 256, 0, st>>>(sx, sy, d_src, d_cnt, d_thr, d_id, sample_seed,
+                                                                   nullptr, d_kept, nullptr, nullptr);
+                }
+                cudaMemcpyAsync(kept.data(), d_kept, sizeof(int) * F, cudaMemcpyDeviceToHost, st);
+                if (cudaStreamSynchronize(st) != cudaSuccess) rc = LMS_ERR_CUDA;
+                // a sample of fewer than two points cannot be fitted: keep that set whole
+                bool redo = false;
+                for (size_t u = 0; u < F; ++u)
+                    if (kept[u] < 2) { thr[u] = 0; kept[u] = (int)cntv[u]; redo = true; }
+                if (redo) cudaMemcpyAsync(d_thr, thr.data(), sizeof(unsigned) * F, cudaMemcpyHostToDevice, st);
+            } else {
+                for (size_t u = 0; u < F; ++u) kept[u] = (int)cntv[u];
+            }
+            for (size_t u = 0; u < F; ++u) dst[u + 1] = dst[u] + kept[u];
+        }
+        if (rc == LMS_OK) {
             cudaMemcpyAsync(d_dst, dst.data(), sizeof(long long) * (F + 1), cudaMemcpyHostToDevice, st);
             StageTimer _t(STAGE_OTHER, st);
-            k_compact_sets<<<(unsigned)F, 256, 0, st>>>(sx, sy, d_src, d_dst, tx, ty);
+            k_subsample<false><<<(unsigned)F, 256, 0, st>>>(sx, sy, d_src, d_cnt, d_thr, d_id, sample_seed, d_dst,
+                                                            nullptr, tx, ty);
+        }
+        if (rc == LMS_OK) {
+            StageTimer _t(STAGE_OTHER, st);
+            k_ols_sums<<<(unsigned)F, 256, 0, st>>>(tx, ty, d_dst, d_sums);
         }
         if (rc == LMS_OK) rc = lms_batch_plan_create((const int64_t *)dst.data(), (int64_t)F, nullptr, 0, 16, &plan);
         if (rc == LMS_OK) rc = lms_fit_batched(plan, tx, ty, (const int64_t *)d_dst, d_res, stream);
         if (rc == LMS_OK) {
             cudaMemcpyAsync(res.data(), d_res, sizeof(lms_result) * F, cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(sums.data(), d_sums, sizeof(long long) * 5 * F, cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) rc = LMS_ERR_CUDA;
         }
         lms_batch_plan_destroy(plan);
-        cudaFree(d_src); cudaFree(d_dst); cudaFree(d_res); cudaFree(tx); cudaFree(ty);
+        cudaFree(d_src); cudaFree(d_dst); cudaFree(d_cnt); cudaFree(d_thr); cudaFree(d_id); cudaFree(d_kept);
+        cudaFree(d_sums); cudaFree(d_res); cudaFree(tx); cudaFree(ty);
     }
     std::vector<float> tab(2 * (size_t)n_theta);
     cudaMemcpyAsync(tab.data(), cs, sizeof(float) * 2 * n_theta, cudaMemcpyDeviceToHost, st);
@@ -517,8 +649,18 @@ int lms_hough_refine(const uint8_t *edges, int64_t B, int32_t H, int32_t W, int3
         L.npoints = hcnt[k];
         if (L.theta_index >= 0)
             L.transposed = fabsf(tab[2 * L.theta_index + 1]) < fabsf(tab[2 * L.theta_index]) ? 1 : 0;
+        L.ols_theta1 = L.ols_theta2 = NAN;
         if (u < fit_set.size() && fit_set[u] == (int)k) {
             L.fit = res[u];
+            L.nfit = (int)(dst[u + 1] - dst[u]);
+            const long long *S = &sums[5 * u];
+            // least squares: theta1 = (n Sxy - Sx Sy) / (n Sxx - Sx^2), exact
+            // integers, one double division; theta2 = (Sy - theta1 Sx) / n
+            const long long num = S[0] * S[4] - S[1] * S[2], den = S[0] * S[3] - S[1] * S[1];
+            if (den != 0 && S[0] > 0) {
+                L.ols_theta1 = (double)num / (double)den;
+                L.ols_theta2 = ((double)S[2] - L.ols_theta1 * (double)S[1]) / (double)S[0];
+            }
             ++u;
         } else {
             L.fit.status = LMS_ERR_ARG;

@@ -20,6 +20,9 @@ stand in for them):
   outliers.
 * ``batch``               -- many ``sloped`` instances with log-uniform sizes.
 * ``edge_images``         -- binary images with random line segments and salt.
+* ``single_line_images``  -- binary images with one line segment whose pixels
+  are kept with probability 0.5, plus salt (the synthetic images of the
+  paper's line-detection experiments, Sec. 5.1); returns the true lines.
 """
 from __future__ import annotations
 
@@ -182,3 +185,43 @@ def edge_images(num: int, seed: int, height: int = 2048, width: int = 2048,
         thresh = np.uint64(int(salt * 2.0 ** 64))
         img[b].reshape(-1)[u < thresh] = 1
     return img
+
+
+def single_line_images(num: int, seed: int, size: int = 1024, noise: float = 0.001, keep: float = 0.5,
+                       len_min: int = 400, len_max: int = 900):
+    """Binary images (uint8 0/1, [num, size, size]) each with one straight
+    segment: the digital line through a random point of the central half of
+    the image at a random angle with |tan| in [0.25, 4], of length
+    U[len_min, len_max] px along its major axis, each pixel kept with
+    probability ``keep``; plus salt pixels set with probability ``noise``.
+    Returns (images, truth) with truth[b] = (slope, intercept) of the
+    generating line in image-centre coordinates (x - size/2, y - size/2):
+    y = slope x + intercept."""
+    img = np.zeros((num, size, size), dtype=np.uint8)
+    truth = np.zeros((num, 2), dtype=np.float64)
+    h = size // 2
+    for b in range(num):
+        st = Stream(seed * 104729 + b + 1)
+        a = math.atan(0.25) + st.uniform(1)[0] * (math.atan(4.0) - math.atan(0.25))
+        if st.uniform(1)[0] < 0.5:
+            a = -a
+        s = math.tan(a)
+        cx = (st.uniform(1)[0] - 0.5) * h
+        cy = (st.uniform(1)[0] - 0.5) * h
+        c = cy - s * cx
+        L = int(st.integers(len_min, len_max + 1, 1)[0])
+        t = np.arange(L + 1, dtype=np.float64) - L / 2.0
+        if abs(s) <= 1.0:
+            x = np.rint(cx + t).astype(np.int64)
+            y = np.rint(s * x + c).astype(np.int64)
+        else:
+            y = np.rint(cy + t).astype(np.int64)
+            x = np.rint((y - c) / s).astype(np.int64)
+        on = st.uniform(L + 1) < keep
+        col, row = x + h, y + h
+        ok = on & (col >= 0) & (col < size) & (row >= 0) & (row < size)
+        img[b, row[ok], col[ok]] = 1
+        u = st.u64(size * size)
+        img[b].reshape(-1)[u < np.uint64(int(noise * 2.0 ** 64))] = 1
+        truth[b] = (s, c)
+    return img, truth

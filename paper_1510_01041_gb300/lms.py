@@ -458,25 +458,28 @@ class _LmsResultC(ctypes.Structure):
 
 class LmsLine(ctypes.Structure):
     _fields_ = [("theta_index", ctypes.c_int32), ("rho_index", ctypes.c_int32), ("votes", ctypes.c_int32),
-                ("transposed", ctypes.c_int32), ("npoints", ctypes.c_int32), ("pad", ctypes.c_int32 * 3),
-                ("fit", _LmsResultC)]
+                ("transposed", ctypes.c_int32), ("npoints", ctypes.c_int32), ("nfit", ctypes.c_int32),
+                ("pad", ctypes.c_int32 * 2), ("fit", _LmsResultC), ("ols_theta1", ctypes.c_double),
+                ("ols_theta2", ctypes.c_double)]
 
 
 def hough_refine(edges, n_theta=1024, n_rho=2896, top_k=32, band_px=4.0, nms_theta=5, nms_rho=5,
-                 cos_sin=None, acc_out=None, stream=None):
+                 cos_sin=None, acc_out=None, stream=None, max_points=0, sample_seed=0):
     """lms_hough_refine on a CUDA uint8 tensor [B, H, W]; returns a list of
-    B * top_k dicts (peak, band size, transposed flag, exact LMS fit)."""
+    B * top_k dicts (peak, band size, points fitted, transposed flag, exact
+    LMS fit, least-squares line of the same points)."""
     L = lib()
     if not getattr(L, "_hough_ready", False):
         vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
-        L.lms_hough_refine.argtypes = [vp, i64, i32, i32, i32, i32, i32, ctypes.c_float, i32, i32, vp, vp, vp, vp]
+        L.lms_hough_refine.argtypes = [vp, i64, i32, i32, i32, i32, i32, ctypes.c_float, i32, i32, i32,
+                                       ctypes.c_uint64, vp, vp, vp, vp]
         L.lms_hough_refine.restype = ctypes.c_int
         L._hough_ready = True
     B, H, W = edges.shape
     edges = edges.contiguous()
     out = (LmsLine * (B * top_k))()
     rc = L.lms_hough_refine(ctypes.c_void_p(edges.data_ptr()), B, H, W, n_theta, n_rho, top_k, float(band_px),
-                            nms_theta, nms_rho,
+                            nms_theta, nms_rho, int(max_points), int(sample_seed) & 0xFFFFFFFFFFFFFFFF,
                             ctypes.c_void_p(cos_sin.data_ptr()) if cos_sin is not None else None,
                             ctypes.c_void_p(acc_out.data_ptr()) if acc_out is not None else None,
                             ctypes.byref(out), _stream_handle(stream))
@@ -484,7 +487,8 @@ def hough_refine(edges, n_theta=1024, n_rho=2896, top_k=32, band_px=4.0, nms_the
         raise LmsError(rc, "lms_hough_refine")
     res = []
     for ln in out:
-        d = {f: getattr(ln, f) for f in ("theta_index", "rho_index", "votes", "transposed", "npoints")}
+        d = {f: getattr(ln, f) for f in ("theta_index", "rho_index", "votes", "transposed", "npoints", "nfit",
+                                         "ols_theta1", "ols_theta2")}
         d["fit"] = {f: getattr(ln.fit, f) for f, _ in _LmsResultC._fields_}
         res.append(d)
     return res

@@ -22,15 +22,50 @@ def L():
     return lms
 
 
-def run(L, imgs, n_theta, n_rho, top_k, band, nms):
+def run(L, imgs, n_theta, n_rho, top_k, band, nms, max_points=0, seed=0):
     cs = ohough.tables(n_theta)
     acc = torch.zeros((imgs.shape[0], n_theta, n_rho), dtype=torch.int32, device="cuda")
     lines = L.hough_refine(torch.from_numpy(imgs).cuda(), n_theta, n_rho, top_k, band, nms, nms,
-                           cos_sin=torch.from_numpy(cs).cuda(), acc_out=acc)
+                           cos_sin=torch.from_numpy(cs).cuda(), acc_out=acc, max_points=max_points,
+                           sample_seed=seed)
     return cs, acc.cpu().numpy(), lines
 
 
-def compare(orc, L, imgs, cs, acc, lines, n_theta, n_rho, top_k, band, nms, check_sets=None):
+M64 = (1 << 64) - 1
+
+
+def splitmix_out(z):
+    """SplitMix64's output function (Steele, Lea and Flood, OOPSLA 2014)."""
+    z &= M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def subsample_mask(seed, k, count, max_points):
+    """Which band points the documented sampling rule keeps (raster ranks)."""
+    if max_points == 0 or count <= max_points:
+        return np.ones(count, bool)
+    thr = ((max_points << 32) // count) or 1
+    m = np.array([(splitmix_out(seed ^ ((((k << 32) | u) * 0x9E3779B97F4A7C15) & M64)) >> 32) < thr
+                  for u in range(count)])
+    return m if m.sum() >= 2 else np.ones(count, bool)
+
+
+def ols(x, y):
+    """Least squares from exact integer sums (one division for the slope)."""
+    x = [int(v) for v in x]
+    y = [int(v) for v in y]
+    n, sx, sy = len(x), sum(x), sum(y)
+    sxx, sxy = sum(v * v for v in x), sum(a * b for a, b in zip(x, y))
+    den = n * sxx - sx * sx
+    if den == 0:
+        return None, None
+    t1 = (n * sxy - sx * sy) / den
+    return t1, (sy - t1 * sx) / n
+
+
+def compare(orc, L, imgs, cs, acc, lines, n_theta, n_rho, top_k, band, nms, check_sets=None, max_points=0, seed=0):
     for b in range(imgs.shape[0]):
         oacc = ohough.vote(imgs[b], n_theta, n_rho, cs)
         assert np.array_equal(acc[b], oacc), b
@@ -44,6 +79,15 @@ def compare(orc, L, imgs, cs, acc, lines, n_theta, n_rho, top_k, band, nms, chec
             ln = lines[b * top_k + k]
             assert ln["npoints"] == x.size and ln["transposed"] == int(tr)
             if x.size >= 2:
+                keep = subsample_mask(seed, b * top_k + k, x.size, max_points)
+                x, y = x[keep], y[keep]
+                assert ln["nfit"] == x.size, (b, k)
+                t1, t2 = ols(x, y)
+                if t1 is None:
+                    assert np.isnan(ln["ols_theta1"])
+                else:
+                    assert ln["ols_theta1"] == t1, (b, k)
+                    assert abs(ln["ols_theta2"] - t2) <= 1e-12 * max(1.0, abs(t2)), (b, k)
                 o = orc.lms_i16(x, y, 0, "sweep")
                 f = ln["fit"]
                 assert (f["status"], f["w_num"], f["s_num"], f["s_den"], f["t_num"], f["i"], f["j"], f["med_sq"]) == \
@@ -63,3 +107,14 @@ def test_hough_full_size_image(L, orc):
     imgs = datagen.edge_images(1, 4, height=2048, width=2048)
     cs, acc, lines = run(L, imgs, 1024, 2896, 32, 4.0, 5)
     compare(orc, L, imgs, cs, acc, lines, 1024, 2896, 32, 4.0, 5, check_sets={0, 1, 7, 31})
+
+
+def test_hough_subsampled_sets(L, orc):
+    """Bands subsampled to about 40 points: the kept points follow the
+    documented rule (reproduced here from SplitMix64's definition) and their
+    exact LMS and least-squares lines match the oracle's."""
+    imgs = datagen.edge_images(2, 33, height=384, width=512, segments=5, len_min=150, len_max=300, salt=0.01)
+    n_theta, n_rho, top_k, band, nms = 180, 2 * int(np.ceil(np.hypot(192, 256))) + 2, 6, 4.0, 5
+    cs, acc, lines = run(L, imgs, n_theta, n_rho, top_k, band, nms, max_points=40, seed=12345)
+    assert any(ln["npoints"] > 40 for ln in lines)
+    compare(orc, L, imgs, cs, acc, lines, n_theta, n_rho, top_k, band, nms, max_points=40, seed=12345)
