@@ -355,7 +355,7 @@ int lms_batch_plan_create(const int64_t *offsets_host, int64_t B, const int32_t 
         p->stream_of[k] = s;
         load[s] += n * n;
         SweepPlan sp;
-        sweep_plan_configure(sp, (int)n, p->hval[p->sweep_sets[k]], sms, 0, 0);
+        sweep_plan_configure(sp, (int)n, p->hval[p->sweep_sets[k]], sms, 0, 0, true);
         need[s] = std::max(need[s], sweep_plan_bytes(sp));
     }
     p->streams.resize(ns);
@@ -439,7 +439,7 @@ int lms_fit_batched(lms_batch_plan *p, const void *xv, const void *yv, const int
         const long long a = p->off_host[i];
         const int n = (int)(p->off_host[i + 1] - a);
         SweepPlan sp;
-        sweep_plan_configure(sp, n, p->hval[i], sms, 0, 0);
+        sweep_plan_configure(sp, n, p->hval[i], sms, 0, 0, true);
         sweep_plan_carve(sp, p->ws[s]);
         if (launch_sweep(sp, x + a, y + a, p->streams[s]) != cudaSuccess) return LMS_ERR_CUDA;
         if (launch_argmin(sp.cands, sp.W + sp.G, out + i, LMS_ALGO_SWEEP, sp.meta + 3, p->streams[s]) != cudaSuccess)

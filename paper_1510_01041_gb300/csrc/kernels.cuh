@@ -122,7 +122,8 @@ struct SweepPlan {
 };
 
 size_t sweep_plan_bytes(const SweepPlan &p);
-void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int want_b);
+// concurrent: the fit shares the GPU with other fits (batch plans)
+void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int want_b, bool concurrent = false);
 void sweep_plan_carve(SweepPlan &p, void *ws);
 cudaError_t launch_sweep(const SweepPlan &p, const short *x, const short *y, cudaStream_t st);
 // the two halves of launch_sweep: bucket counts and starts (prepare), then

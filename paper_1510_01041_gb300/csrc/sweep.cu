@@ -27,6 +27,7 @@
 //             window there
 //   sweep     per sweeper (one warp): apply the events in slope order,
 //             re-score the touched windows, keep the best
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -1565,7 +1566,7 @@ static size_t sweep_smem_bytes(int n, bool xy_smem, bool pos_smem, int spb)
     return xyb + per * spb;
 }
 
-void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int want_b)
+void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int want_b, bool concurrent)
 {
     p.n = n;
     p.h = h;
@@ -1594,11 +1595,17 @@ void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int w
     cudaGetLastError();
     if (per_sm < 1) per_sm = 1;
     const long long g_full = (long long)sms * per_sm * spb;
-    // slope ranges: RANGE_FACTOR per sweeping warp, handed out dynamically, at
-    // least MIN_RANGE_EVENTS events each so that a range's start sort pays off
+    // slope ranges: RANGE_FACTOR per sweeping warp, handed out dynamically.
+    // A range's start sort costs n log n, so ranges hold at least n events
+    // where that still keeps every sweeping warp busy (and always when other
+    // fits share the GPU), and at least MIN_RANGE_EVENTS events in any case.
     long long w = want_w > 0 ? want_w : RANGE_FACTOR * g_full;
-    const long long by_events = p.emax / MIN_RANGE_EVENTS + 1;
-    if (want_w <= 0 && w > by_events) w = by_events;
+    if (want_w <= 0) {
+        const long long by_n = p.emax / (n > MIN_RANGE_EVENTS ? (long long)n : MIN_RANGE_EVENTS) + 1;
+        const long long by_min = p.emax / MIN_RANGE_EVENTS + 1;
+        const long long cap = concurrent ? by_n : std::max(by_n, std::min(g_full, by_min));
+        if (w > cap) w = cap;
+    }
     if (w < 1) w = 1;
     p.W = (int)w;
     long long blocks = (w + spb - 1) / spb;
