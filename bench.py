@@ -40,6 +40,11 @@ UNIT = "solves/s"
 # 2 window widths and centres, 2 exact candidate comparisons, decode.
 SWEEP_INT_OPS_PER_EVENT = 50
 INT_LANES_PER_SM = 128
+# DRAM bytes (read + written) of one timed plain-path k_sweep launch of this
+# benchmark, from an ncu capture of the current kernel (192.06 MB read,
+# 3.58 MB written); against 194 MB of algorithmic traffic (events and range
+# start orders).  Must be re-measured whenever the kernel changes.
+SWEEP_DRAM_BYTES = 195_635_456
 
 
 def _dist():
@@ -576,7 +581,8 @@ def main():
         ev_per_launch = sum(events) / len(events)
         achieved = SWEEP_INT_OPS_PER_EVENT * ev_per_launch / per_launch_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": int_peak, "unit": "Tops/s (int32)",
-                "frac": achieved / int_peak, "traffic": None, "kernel": "k_sweep (plain path)",
+                "frac": achieved / int_peak, "traffic": SWEEP_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu)",
+                "kernel": "k_sweep (plain path)",
                 "kernel_ms": per_launch_s * 1e3, "events_per_launch": ev_per_launch,
                 "ops_per_event": SWEEP_INT_OPS_PER_EVENT,
                 "peak_basis": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int32 lanes x "

@@ -268,10 +268,11 @@ __device__ __forceinline__ void cta_merge_sort(T (&v)[IPT], T *s, T *s2, int P)
 template <int IPT, class T, class F>
 __device__ __forceinline__ void cta_fill_merge_sort(T *s, T *s2, int P, F fill)
 {
+    // which thread starts with which value does not matter to a sort: read
+    // the inputs with consecutive threads on consecutive positions
     T v[IPT];
-    const int base = threadIdx.x * IPT;
 #pragma unroll
-    for (int r = 0; r < IPT; ++r) v[r] = fill(base + r);
+    for (int r = 0; r < IPT; ++r) v[r] = fill(r * (int)blockDim.x + (int)threadIdx.x);
     cta_merge_sort<IPT>(v, s, s2, P);
 }
 
@@ -295,10 +296,12 @@ __device__ bool cta_fill_merge_sort_any(T *s, T *s2, int P, F fill)
 template <int IPT, class T, class F>
 __device__ __forceinline__ void cta_fill_sort(T *s, int P, F fill)
 {
+    // inputs read by consecutive threads at consecutive positions (the
+    // starting arrangement of a sort is arbitrary)
     T v[IPT];
     const int base = threadIdx.x * IPT;
 #pragma unroll
-    for (int r = 0; r < IPT; ++r) v[r] = fill(base + r);
+    for (int r = 0; r < IPT; ++r) v[r] = fill(r * (int)blockDim.x + (int)threadIdx.x);
     cta_sort_blocked<IPT>(v, s, P);
 #pragma unroll
     for (int r = 0; r < IPT; ++r) s[base + r] = v[r];
