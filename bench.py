@@ -47,6 +47,29 @@ INT_LANES_PER_SM = 128
 SWEEP_DRAM_BYTES = 195_635_456
 
 
+def rank_seeds(rank: int, count: int):
+    """Instance seeds of one rank: every rank fits its own instances (weak
+    scaling, no collective on the data path)."""
+    return [rank * 100003 + 1 + s for s in range(count)]
+
+
+def max_over_ranks(v: float, device=None) -> float:
+    """The largest of every rank's value (the slowest rank's time), or v on
+    one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the solves of all ranks over the slowest rank's time."""
+    return world * steps_per_rank / (max_ms / 1000.0)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -484,7 +507,7 @@ def main():
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(dev)
     total = args.warmup + args.steps
-    seeds = [rank * 100003 + 1 + s for s in range(total)]
+    seeds = rank_seeds(rank, total)
     host = [datagen.line_with_outliers(N_POINTS, s) for s in seeds]
     xs = [torch.from_numpy(h[0]).to(dev) for h in host]
     ys = [torch.from_numpy(h[1]).to(dev) for h in host]
@@ -501,14 +524,6 @@ def main():
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize(dev)
-
-    def max_over_ranks(v):
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([v], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return v
 
     learned_stats = []
 
@@ -536,8 +551,8 @@ def main():
         plain_ms = _timed(fit_plain, args.steps, args.warmup, flush, stream, barrier)
         stages_p = lms.profile_read()
     lms.profile_enable(False)
-    learned_ms = max_over_ranks(learned_ms)
-    plain_ms = max_over_ranks(plain_ms)
+    learned_ms = max_over_ranks(learned_ms, dev)
+    plain_ms = max_over_ranks(plain_ms, dev)
     res_l = lms.decode(out_l)[args.warmup:]
     res_p = lms.decode(out_p)[args.warmup:]
     keys = ("status", "w_num", "w_den", "s_num", "s_den", "t_num", "t_den", "i", "j", "theta1", "theta2", "med_sq")
@@ -562,12 +577,12 @@ def main():
         hres.copy_(dres, non_blocking=True)
         torch.cuda.synchronize(dev)
         assert lms.decode(hres)[0]["status"] == lms.LMS_OK
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
 
     slopes = N_POINTS * (N_POINTS - 1) // 2
     solves = ws * args.steps
-    value = solves / (learned_ms / 1000.0)
-    plain_value = solves / (plain_ms / 1000.0)
+    value = job_rate(args.steps, ws, learned_ms)
+    plain_value = job_rate(args.steps, ws, plain_ms)
     csum = clk.summary()
     mhz = csum.get("sm_mhz") or 1462.0
     int_peak = props.multi_processor_count * INT_LANES_PER_SM * mhz * 1e6 / 1e12
