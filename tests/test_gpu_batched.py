@@ -89,3 +89,35 @@ def test_batched_graph_replay(L, orc):
     g.replay()
     torch.cuda.synchronize()
     check(L, orc, x, y2, off, L.decode(out))
+
+
+def test_batched_full_4096_sets_in_one_graph(L, orc):
+    """The full batch workload: 4096 sets, n log-uniform in [64, 4096],
+    outlier fraction U(0, 0.45), slope angle U(-1.5, 1.5), in the plan shape
+    the benchmark tunes to (plain kernel up to 128 points, 48 streams),
+    captured into one CUDA graph and replayed.  The smallest and largest sets
+    and 30 random ones are checked against the oracle one by one; every set
+    of the replay equals the eager run."""
+    x, y, off = datagen.batch(4096, 5000)
+    xt, yt, ot = (torch.from_numpy(a).cuda() for a in (x, y, off))
+    plan = L.BatchPlan(off, plain_max_n=128, streams=48)
+    out = plan.fit(xt, yt, ot)
+    torch.cuda.synchronize()
+    res = L.decode(out)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    out2 = torch.zeros_like(out)
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.fit(xt, yt, ot, out=out2, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), out2.cpu().numpy())
+    sizes = np.diff(off)
+    rng = np.random.default_rng(3)
+    pick = sorted(set([int(np.argmin(sizes)), int(np.argmax(sizes))] + rng.choice(4096, 30, replace=False).tolist()))
+    for b in pick:
+        xs, ys = x[off[b]:off[b + 1]], y[off[b]:off[b + 1]]
+        o = orc.lms_i16(xs, ys, 0, "brute" if xs.size <= 160 else "sweep")
+        r = res[b]
+        assert tuple(r[k] for k in KEYS) == tuple(getattr(o, k) for k in KEYS), (b, xs.size, r, o)
