@@ -452,12 +452,17 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         cov[best - 1].second = cov[best].second;
         cov.erase(cov.begin() + best);
     }
-    std::vector<float2> prev(cov.size());
+    // rounded outward to floats; covers that now touch or overlap are merged
+    // so that they stay sorted and disjoint (the device searches them)
+    std::vector<float2> prev;
     for (size_t k = 0; k < cov.size(); ++k) {
-        prev[k].x = std::nextafter((float)cov[k].first, -INFINITY);
-        prev[k].y = std::nextafter((float)cov[k].second, INFINITY);
+        float2 f;
+        f.x = std::nextafter((float)cov[k].first, -INFINITY);
+        f.y = std::nextafter((float)cov[k].second, INFINITY);
+        if (!prev.empty() && f.x <= prev.back().y) prev.back().y = std::max(prev.back().y, f.y);
+        else prev.push_back(f);
     }
-    const int npre = (int)cov.size();
+    const int npre = (int)prev.size();
     if (cudaMemcpyAsync(keep, keepv.data(), NB, cudaMemcpyHostToDevice, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (npre > 0 && cudaMemcpyAsync(pre, prev.data(), sizeof(float2) * npre, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return LMS_ERR_CUDA;

@@ -207,10 +207,11 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
     unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
-    __shared__ float2 s_pre[PRE_MAX];
+    __shared__ float2 s_pre[2 * PRE_MAX];   // covers sorted and disjoint, padded with lower bound +inf
     const int nbnd = meta[0], P2 = meta[1], NB = nbnd + 1;
     for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
-    if (threadIdx.x < npre) s_pre[threadIdx.x] = pre[threadIdx.x];
+    if (threadIdx.x < 2 * PRE_MAX)
+        s_pre[threadIdx.x] = threadIdx.x < npre ? pre[threadIdx.x] : make_float2(INFINITY, INFINITY);
     unsigned nvalid = 0;
     unsigned *my_hist = hist + (size_t)blockIdx.x * BND_MAX;
     for (int k = threadIdx.x; k < NB; k += blockDim.x)
@@ -246,9 +247,12 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
                     if (!G::approx(pts, i, j, sl)) continue;
                 }
                 ++nvalid;
-                bool cand = false;
-                for (int r = 0; r < npre; ++r) cand |= (sl >= s_pre[r].x) & (sl <= s_pre[r].y);
-                if (!cand) continue;
+                // the last cover starting at or below sl must reach it
+                int c = 0;
+#pragma unroll
+                for (int step = PRE_MAX; step >= 1; step >>= 1)
+                    if (s_pre[c + step - 1].x <= sl) c += step;
+                if (c == 0 || sl > s_pre[c - 1].y) continue;
             }
             long long key;
             if (!G::key(pts, i, j, key)) continue;
