@@ -190,8 +190,35 @@ __global__ void __launch_bounds__(1024) k_splitters(const long long *__restrict_
 }
 
 // ---------------------------------------------------------------- count / scatter
+// Float pre-test of a restricted pass: 0 when x_i == x_j (no slope), 1 when
+// the slope lies outside every cover, 2 for a candidate.  The restricted
+// count and the restricted scatter both call it, so they keep the same pairs.
+// Pi: the packed point i (int16 points only).
+template <class G>
+__device__ __forceinline__ int pre_test(const void *pts, int Pi, int i, int j, const float2 *s_pre)
+{
+    float sl;
+    if constexpr (std::is_same<G, KeyI16>::value) {
+        // dy / dx by the fast division (relative error below 2^-21; exact
+        // small-integer operands)
+        const int Pj = __ldg(static_cast<const int *>(pts) + j);
+        const int dx = px(Pj) - px(Pi);
+        if (dx == 0) return 0;
+        sl = __fdividef((float)(py(Pj) - py(Pi)), (float)dx);
+    } else {
+        if (!G::approx(pts, i, j, sl)) return 0;
+    }
+    // the last cover starting at or below sl must reach it
+    int c = 0;
+#pragma unroll
+    for (int step = PRE_MAX; step >= 1; step >>= 1)
+        if (s_pre[c + step - 1].x <= sl) c += step;
+    return (c > 0 && sl <= s_pre[c - 1].y) ? 2 : 1;
+}
+
 // Both passes walk the same upper-triangle tiles in the same static order,
-// so the scatter's per-CTA bucket cursors match the counts exactly.
+// so the scatter's per-CTA bucket cursors match the counts exactly (the
+// restricted count, k_count_restricted, walks them in the same order too).
 template <bool SCATTER, class G>
 __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__restrict__ pts, int n,
                                                               const long long *__restrict__ bnd,
@@ -200,9 +227,7 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
                                                               const unsigned *__restrict__ base,
                                                               unsigned *__restrict__ ev,
                                                               const unsigned char *__restrict__ keep,
-                                                              const float2 *__restrict__ pre, int npre,
-                                                              int *__restrict__ meta_mut,
-                                                              unsigned *__restrict__ list)
+                                                              const float2 *__restrict__ pre, int npre)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
@@ -212,7 +237,6 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
     for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
     if (threadIdx.x < 2 * PRE_MAX)
         s_pre[threadIdx.x] = threadIdx.x < npre ? pre[threadIdx.x] : make_float2(INFINITY, INFINITY);
-    unsigned nvalid = 0;
     unsigned *my_hist = hist + (size_t)blockIdx.x * BND_MAX;
     for (int k = threadIdx.x; k < NB; k += blockDim.x)
         s_cnt[k] = SCATTER ? base[k] + my_hist[k] : 0u;
@@ -234,51 +258,129 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
         for (int jj = 0; jj < JPT; ++jj) {
             const int j = bj * TILE + jl0 + jj;
             if (j <= i || j >= n) continue;
-            if (pre) {
-                float sl;
-                if constexpr (std::is_same<G, KeyI16>::value) {
-                    // dy / dx by the fast division (relative error below 2^-21;
-                    // exact small-integer operands)
-                    const int Pj = __ldg(static_cast<const int *>(pts) + j);
-                    const int dx = px(Pj) - px(Pi);
-                    if (dx == 0) continue;
-                    sl = __fdividef((float)(py(Pj) - py(Pi)), (float)dx);
-                } else {
-                    if (!G::approx(pts, i, j, sl)) continue;
-                }
-                ++nvalid;
-                // the last cover starting at or below sl must reach it
-                int c = 0;
-#pragma unroll
-                for (int step = PRE_MAX; step >= 1; step >>= 1)
-                    if (s_pre[c + step - 1].x <= sl) c += step;
-                if (c == 0 || sl > s_pre[c - 1].y) continue;
-            }
+            if (pre && pre_test<G>(pts, Pi, i, j, s_pre) != 2) continue;
             long long key;
             if (!G::key(pts, i, j, key)) continue;
             const int b = bucket_of(s_bnd, P2, key);
             if (keep && !keep[b]) continue;
             const unsigned slot = atomicAdd(&s_cnt[b], 1u);
             if (SCATTER) ev[slot] = ev_pack(i, j, false);
-            if (!SCATTER && list) {
-                // the kept pair to the compact list (one atomic per warp)
-                const unsigned am = __activemask();
-                const int lead = __ffs(am) - 1, me = threadIdx.x & 31;
-                unsigned at = 0;
-                if (me == lead) at = atomicAdd(reinterpret_cast<unsigned *>(meta_mut + 6), (unsigned)__popc(am));
-                at = __shfl_sync(am, at, lead) + __popc(am & ((1u << me) - 1u));
-                list[at] = ((unsigned)i << 16) | (unsigned)j;
-            }
         }
     }
     if (!SCATTER) {
-        if (pre) {
-            for (int m = 16; m >= 1; m >>= 1) nvalid += __shfl_xor_sync(FULL, nvalid, m);
-            if ((threadIdx.x & 31) == 0 && nvalid) atomicAdd(reinterpret_cast<unsigned *>(meta_mut + 5), nvalid);
-        }
         __syncthreads();
         for (int k = threadIdx.x; k < NB; k += blockDim.x) my_hist[k] = s_cnt[k];
     }
+}
+
+// ---------------------------------------------------------------- restricted count
+// The count pass of a restricted fit (covers given, kept pairs listed).  The
+// float pre-test passes about one pair in a hundred, so resolving a pair
+// where it is tested would run the costly steps (exact key, bucket search,
+// keep test, count, list) with one or two lanes of a warp live.  Instead
+// every warp pushes the pairs that pass onto a stack in shared memory and
+// resolves them 32 at a time, all lanes busy; the rest of the stack is
+// resolved after the last tile.  Counts, list and meta[5] / meta[6] are the
+// same as the combined pass would give (the list order may differ).
+constexpr int CNT_WARPS = CNT_THREADS / 32;
+constexpr int CNT_STACK = 64;   // per warp: at most 31 left + 32 pushed
+
+template <class G>
+__device__ __forceinline__ void resolve_pairs(const void *pts, const long long *s_bnd, int P2, unsigned *s_cnt,
+                                              const unsigned char *keep, unsigned pr, bool have, int *meta_mut,
+                                              unsigned *list)
+{
+    bool kept = false;
+    if (have) {
+        long long key;
+        if (G::key(pts, (int)(pr >> 16), (int)(pr & 0xffffu), key)) {
+            const int b = bucket_of(s_bnd, P2, key);
+            if (!keep || keep[b]) {
+                atomicAdd(&s_cnt[b], 1u);
+                kept = true;
+            }
+        }
+    }
+    if (list) {
+        const unsigned m = __ballot_sync(FULL, kept);
+        if (m) {
+            const int lane = threadIdx.x & 31;
+            unsigned at = 0;
+            if (lane == 0) at = atomicAdd(reinterpret_cast<unsigned *>(meta_mut + 6), (unsigned)__popc(m));
+            at = __shfl_sync(FULL, at, 0) + __popc(m & ((1u << lane) - 1u));
+            if (kept) list[at] = pr;
+        }
+    }
+}
+
+template <class G>
+__global__ void __launch_bounds__(CNT_THREADS) k_count_restricted(const void *__restrict__ pts, int n,
+                                                                  const long long *__restrict__ bnd,
+                                                                  unsigned *__restrict__ hist,
+                                                                  const unsigned char *__restrict__ keep,
+                                                                  const float2 *__restrict__ pre, int npre,
+                                                                  int *__restrict__ meta,
+                                                                  unsigned *__restrict__ list)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long *s_bnd = reinterpret_cast<long long *>(smem);
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
+    __shared__ float2 s_pre[2 * PRE_MAX];   // covers sorted and disjoint, padded with lower bound +inf
+    __shared__ unsigned s_stack[CNT_WARPS][CNT_STACK];
+    const int P2 = meta[1], NB = meta[0] + 1;
+    for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
+    if (threadIdx.x < 2 * PRE_MAX)
+        s_pre[threadIdx.x] = threadIdx.x < npre ? pre[threadIdx.x] : make_float2(INFINITY, INFINITY);
+    for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    unsigned *stk = s_stack[threadIdx.x >> 5];
+    const unsigned below = (1u << lane) - 1u;
+    int top = 0;   // warp-uniform stack height
+    unsigned nvalid = 0;
+    const int T = (n + TILE - 1) / TILE;
+    const int ntiles = T * (T + 1) / 2;
+    const int il = threadIdx.x & (TILE - 1);
+    constexpr int JPT = TILE * TILE / CNT_THREADS;
+    const int jl0 = (threadIdx.x / TILE) * JPT;
+    for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
+        int bi, bj;
+        tile_decode(q, bi, bj);
+        const int i = bi * TILE + il;
+        const bool row = i < n;
+        int Pi = 0;
+        if constexpr (std::is_same<G, KeyI16>::value)
+            if (row) Pi = __ldg(static_cast<const int *>(pts) + i);
+#pragma unroll 4
+        for (int jj = 0; jj < JPT; ++jj) {
+            const int j = bj * TILE + jl0 + jj;
+            bool cand = false;
+            if (row && j > i && j < n) {
+                const int r = pre_test<G>(pts, Pi, i, j, s_pre);
+                nvalid += r != 0;
+                cand = r == 2;
+            }
+            const unsigned m = __ballot_sync(FULL, cand);
+            if (m) {
+                if (cand) stk[top + __popc(m & below)] = ((unsigned)i << 16) | (unsigned)j;
+                top += __popc(m);
+                if (top >= 32) {
+                    __syncwarp();
+                    top -= 32;
+                    const unsigned pr = stk[top + lane];
+                    __syncwarp();
+                    resolve_pairs<G>(pts, s_bnd, P2, s_cnt, keep, pr, true, meta, list);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (top > 0) resolve_pairs<G>(pts, s_bnd, P2, s_cnt, keep, lane < top ? stk[lane] : 0u, lane < top, meta, list);
+    for (int m = 16; m >= 1; m >>= 1) nvalid += __shfl_xor_sync(FULL, nvalid, m);
+    if (lane == 0 && nvalid) atomicAdd(reinterpret_cast<unsigned *>(meta + 5), nvalid);
+    __syncthreads();
+    unsigned *my_hist = hist + (size_t)blockIdx.x * BND_MAX;
+    for (int k = threadIdx.x; k < NB; k += blockDim.x) my_hist[k] = s_cnt[k];
 }
 
 // The listed pairs to their buckets (the order inside a bucket is left to
@@ -1702,12 +1804,16 @@ static cudaError_t events_count(const SweepPlan &p, const void *pts, const unsig
                                 int npre, cudaStream_t st)
 {
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
-    cudaFuncSetAttribute(k_bucket_pairs<false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    {
+    if (pre) {
+        cudaFuncSetAttribute(k_count_restricted<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
+        StageTimer _t(STAGE_COUNT_PAIRS, st);
+        k_count_restricted<G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, p.n, p.bnd, p.hist, keep, pre, npre, p.meta,
+                                                                  p.ev2);
+    } else {
+        cudaFuncSetAttribute(k_bucket_pairs<false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
         StageTimer _t(STAGE_COUNT_PAIRS, st);
         k_bucket_pairs<false, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, p.n, p.bnd, p.meta, p.hist, nullptr, nullptr,
-                                                                    keep, pre, npre, p.meta,
-                                                                    (pre && p.ev2) ? p.ev2 : nullptr);
+                                                                    keep, nullptr, 0);
     }
     { StageTimer _t(STAGE_PREFIX, st); k_bucket_prefix<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.hist, p.C, p.meta, p.base); }
     { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta); }
@@ -1759,7 +1865,7 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
     } else {
         StageTimer _t(STAGE_SCATTER, st);
         k_bucket_pairs<true, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep,
-                                                                   pre, npre, p.meta, nullptr);
+                                                                   pre, npre);
     }
     const size_t seg_smem = (size_t)SEG_CAP * 12;
     cudaFuncSetAttribute(k_segsort<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
