@@ -7,6 +7,7 @@ import pytest
 
 from oracle import hough as ohough
 from paper_1510_01041_gb300 import datagen
+from subsample_rule import subsample_mask
 
 pytestmark = pytest.mark.gpu
 
@@ -29,27 +30,6 @@ def run(L, imgs, n_theta, n_rho, top_k, band, nms, max_points=0, seed=0):
                            cos_sin=torch.from_numpy(cs).cuda(), acc_out=acc, max_points=max_points,
                            sample_seed=seed)
     return cs, acc.cpu().numpy(), lines
-
-
-M64 = (1 << 64) - 1
-
-
-def splitmix_out(z):
-    """SplitMix64's output function (Steele, Lea and Flood, OOPSLA 2014)."""
-    z &= M64
-    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
-    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
-    return z ^ (z >> 31)
-
-
-def subsample_mask(seed, k, count, max_points):
-    """Which band points the documented sampling rule keeps (raster ranks)."""
-    if max_points == 0 or count <= max_points:
-        return np.ones(count, bool)
-    thr = ((max_points << 32) // count) or 1
-    m = np.array([(splitmix_out(seed ^ ((((k << 32) | u) * 0x9E3779B97F4A7C15) & M64)) >> 32) < thr
-                  for u in range(count)])
-    return m if m.sum() >= 2 else np.ones(count, bool)
 
 
 def ols(x, y):
