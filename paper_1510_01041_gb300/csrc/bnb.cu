@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -261,7 +262,31 @@ __global__ void k_pick_seeds(const long long *__restrict__ sorted, int S, const 
     }
 }
 
+constexpr size_t a256_const(size_t v) { return (v + 255) & ~(size_t)255; }
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Page-locked host staging for the device-to-host reads of a fit, so that
+// they are queued asynchronously and waited for once.  One buffer per host
+// thread, allocated on first use and kept for the life of the process (a fit
+// waits for its reads before it returns, so nothing is in flight between
+// fits).  Layout: meta (8 ints), upper bound, bucket counts, boundaries,
+// kept-bucket starts, prune flags.
+constexpr size_t HS_META = 0, HS_UB = 32, HS_CNT = 64;
+constexpr size_t HS_BND = HS_CNT + (size_t)BND_MAX * 4;
+constexpr size_t HS_KBASE = HS_BND + (size_t)BND_MAX * 8;
+constexpr size_t HS_PRUNE = HS_KBASE + a256_const((size_t)(BND_MAX + 1) * 4);
+constexpr size_t HS_BYTES = HS_PRUNE + (size_t)BND_MAX;
+
+unsigned char *host_stage()
+{
+    thread_local unsigned char *buf = nullptr;
+    if (!buf) {
+        void *q = nullptr;
+        if (cudaHostAlloc(&q, HS_BYTES, cudaHostAllocPortable) != cudaSuccess) return nullptr;
+        buf = static_cast<unsigned char *>(q);
+    }
+    return buf;
+}
 
 }  // namespace
 
@@ -292,8 +317,8 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
             lms_bnb_stats *stats, void *extra, int sms, cudaStream_t st)
 {
     const int n = p.n, h = p.h;
-    unsigned char *q = static_cast<unsigned char *>(extra);
-    auto take = [&](size_t bytes) { void *r = q; q += a256(bytes); return r; };
+    unsigned char *cur = static_cast<unsigned char *>(extra);
+    auto take = [&](size_t bytes) { void *r = cur; cur += a256(bytes); return r; };
     int *xc = (int *)take(64);
     long long *ub = (long long *)(xc + 4);
     long long *seed_keys = (long long *)take((size_t)BNB_SEEDS * 8 * 2);
@@ -309,8 +334,34 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     long long *gscr = (n > SORT_SMEM_N) ? (long long *)take((size_t)2 * sms * 2 * P * 8) : nullptr;
     const int grid = 2 * sms;
 
+    unsigned char *hs = host_stage();
+    if (!hs) return LMS_ERR_CUDA;
+    int *h_meta = reinterpret_cast<int *>(hs + HS_META);
+    long long *h_ub = reinterpret_cast<long long *>(hs + HS_UB);
+    const unsigned *cnt = reinterpret_cast<const unsigned *>(hs + HS_CNT);
+    const long long *bnd = reinterpret_cast<const long long *>(hs + HS_BND);
+    const unsigned *kbase = reinterpret_cast<const unsigned *>(hs + HS_KBASE);
+    unsigned char *h_prune = hs + HS_PRUNE;
+
     if (launch_sweep_sample(p, x, y, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (launch_sample_counts(p, scount, st) != cudaSuccess) return LMS_ERR_CUDA;
+    // bucket structure to the host; the tree weighs buckets by sampled pairs
+    // (the buckets are quantile ranges of the sample), so no pass over all
+    // pairs is needed before the bounds have pruned.  The reads are waited
+    // for after the seed stage is queued, so the host builds the first level
+    // while the GPU scores the seeds.
+    cudaEvent_t sampled;
+    if (cudaEventCreateWithFlags(&sampled, cudaEventDisableTiming) != cudaSuccess) return LMS_ERR_CUDA;
+    const bool queued = cudaMemcpyAsync(h_meta, p.meta, sizeof(int) * 4, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                        cudaMemcpyAsync(hs + HS_CNT, scount, sizeof(unsigned) * BND_MAX, cudaMemcpyDeviceToHost,
+                                        st) == cudaSuccess &&
+                        cudaMemcpyAsync(hs + HS_BND, p.bnd, sizeof(long long) * BND_MAX, cudaMemcpyDeviceToHost,
+                                        st) == cudaSuccess &&
+                        cudaEventRecord(sampled, st) == cudaSuccess;
+    if (!queued) {
+        cudaEventDestroy(sampled);
+        return LMS_ERR_CUDA;
+    }
     {
         StageTimer _t(STAGE_OTHER, st);
         k_x_center<<<1, 1024, 0, st>>>(p.xy, n, xc);
@@ -334,22 +385,11 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         StageTimer _t(STAGE_OTHER, st);
         k_min_ub<<<1, 32, 0, st>>>(seed_w, BNB_SEEDS, ub);
     }
-    // bucket structure to the host; the tree weighs buckets by sampled pairs
-    // (the buckets are quantile ranges of the sample), so no pass over all
-    // pairs is needed before the bounds have pruned
-    int meta[4];
-    long long ub_host = 0;
-    if (cudaMemcpyAsync(meta, p.meta, sizeof(meta), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LMS_ERR_CUDA;
-    if (cudaMemcpyAsync(&ub_host, ub, sizeof(ub_host), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LMS_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
-    const int NB = meta[0] + 1;
-    std::vector<unsigned> cnt(NB);
+    const cudaError_t waited = cudaEventSynchronize(sampled);
+    cudaEventDestroy(sampled);
+    if (waited != cudaSuccess) return LMS_ERR_CUDA;
+    const int NB = h_meta[0] + 1;
     std::vector<unsigned> base(NB + 1);
-    std::vector<long long> bnd(NB > 1 ? NB - 1 : 1);
-    if (cudaMemcpy(cnt.data(), scount, sizeof(unsigned) * NB, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return LMS_ERR_CUDA;
-    if (NB > 1 && cudaMemcpy(bnd.data(), p.bnd, sizeof(long long) * (NB - 1), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return LMS_ERR_CUDA;
     base[0] = 0;
     for (int b = 0; b < NB; ++b) base[b + 1] = base[b] + cnt[b];
     const unsigned E = base[NB];
@@ -384,19 +424,20 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
             hk[2 * k + 1] = nodes[k].b1 >= NB ? I64_MAX : bnd[nodes[k].b1 - 1];
         }
         for (int off = 0; off < nn; off += BND_MAX) {
-            const int cnt = std::min(BND_MAX, nn - off);
-            if (cudaMemcpyAsync(node_keys, hk.data() + 2 * off, sizeof(long long) * 2 * cnt, cudaMemcpyHostToDevice,
+            const int chunk = std::min(BND_MAX, nn - off);
+            if (cudaMemcpyAsync(node_keys, hk.data() + 2 * off, sizeof(long long) * 2 * chunk, cudaMemcpyHostToDevice,
                                 st) != cudaSuccess)
                 return LMS_ERR_CUDA;
             {
                 StageTimer _t(STAGE_OTHER, st);
-                k_node_lb<<<std::min(cnt, grid), 1024, two_sorts, st>>>(p.xy, n, h, xc, node_keys, cnt, ub, prune,
+                k_node_lb<<<std::min(chunk, grid), 1024, two_sorts, st>>>(p.xy, n, h, xc, node_keys, chunk, ub, prune,
                                                                         lbv, gscr);
             }
             hp.resize(nn);
-            if (cudaMemcpyAsync(hp.data() + off, prune, cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            if (cudaMemcpyAsync(h_prune, prune, chunk, cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 return LMS_ERR_CUDA;
             if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
+            std::memcpy(hp.data() + off, h_prune, chunk);
         }
         evaluated += nn;
         // survivors split into F children of about equal sampled events, F
@@ -438,7 +479,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         if (!keepv[b]) { ++b; continue; }
         int e = b + 1;
         while (e < NB && keepv[e]) ++e;
-        for (int q = b; q < e; ++q) kept_buckets += 1;
+        kept_buckets += (unsigned)(e - b);
         const double lo = b == 0 ? -INFINITY : (double)bnd[b - 1] * 0x1p-32;
         const double hi = e >= NB ? INFINITY : (double)bnd[e - 1] * 0x1p-32;
         cov.push_back({lo - (std::isinf(lo) ? 0.0 : std::fabs(lo) * 0x1p-18 + 0x1p-30),
@@ -468,12 +509,14 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         return LMS_ERR_CUDA;
     // exact events of the kept buckets only: p.base becomes their starts
     if (launch_sweep_count(p, keep, npre > 0 ? pre : nullptr, npre, st) != cudaSuccess) return LMS_ERR_CUDA;
-    std::vector<unsigned> kbase(NB + 1);
-    int meta6[6];
-    if (cudaMemcpyAsync(kbase.data(), p.base, sizeof(unsigned) * (NB + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    if (cudaMemcpyAsync(hs + HS_KBASE, p.base, sizeof(unsigned) * (NB + 1), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(h_meta, p.meta, sizeof(int) * 6, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(h_ub, ub, sizeof(long long), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return LMS_ERR_CUDA;
-    if (cudaMemcpyAsync(meta6, p.meta, sizeof(meta6), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
+    const unsigned events_total = (unsigned)h_meta[5];
+    const long long ub_host = *h_ub;
     const unsigned run = kbase[NB];
     // ranges: pieces of about `target` events inside each run of consecutive
     // kept buckets (a range never spans a dropped bucket: the kinetic order
@@ -516,7 +559,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     if (launch_argmin(p.cands, p.W + p.G, out, LMS_ALGO_BNB, p.meta + 3, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
     if (stats) {
-        stats->events_total = (unsigned)meta6[5];
+        stats->events_total = events_total;
         stats->events_swept = run;
         stats->buckets_total = NB;
         stats->buckets_swept = kept_buckets;
