@@ -21,7 +21,12 @@
  *     memory of the current device; "host" pointers are ordinary host memory.
  *   - The caller owns all input and output buffers.  The library owns an
  *     internal per-device workspace (grown with cudaMalloc on demand) unless
- *     the caller installs one with lms_set_workspace.
+ *     the caller installs one with lms_set_workspace.  lms_fit,
+ *     lms_fit_host, lms_fit_bnb and lms_fit_learned on one device all use
+ *     that one workspace: fits whose GPU work may overlap (different streams
+ *     or host threads) race and must be ordered by the caller; many fits at
+ *     once go through one lms_fit_batched call instead.  The workspace
+ *     bookkeeping itself is locked, so the calls may come from any thread.
  *   - Device-pointer calls are asynchronous on `stream` (NULL = the legacy
  *     default stream); host-pointer calls synchronise before returning.
  *   - The return value reports argument and launch errors detected on the
