@@ -150,6 +150,8 @@ typedef struct {
  *   stats       host pointer (may be NULL).
  * Other arguments as lms_fit (int16 points, n <= 65536).  The call waits for
  * the stream between bisection levels and returns after the fit is done.
+ * The first call on a host thread allocates about 272 KB of page-locked host
+ * memory for its reads (kept for that thread until the process exits).
  */
 LMS_API int lms_fit_bnb(const void *x, const void *y, int64_t n, int64_t h, const float *seed_slope,
                         const lms_options *opt, lms_result *out, lms_bnb_stats *stats, lms_stream_t stream);
