@@ -618,7 +618,8 @@ def main():
                    "l2": "flushed before every step (256 MB write, outside the timed events)",
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": solves / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 2 * N_POINTS,
-                "d2h_bytes_per_step": lms.RESULT_DTYPE.itemsize},
+                "d2h_bytes_per_step": lms.RESULT_DTYPE.itemsize,
+                "l2": "not flushed: back-to-back calls, wall clock around copies, fit and result read"},
         "gpu_launches": launches,
         "clocks": {k: csum.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "roofline": roof,
