@@ -204,17 +204,35 @@ __device__ __forceinline__ void cta_sort_blocked(T (&v)[IPT], T *s, int P)
     }
 }
 
+// Shared-memory slot of word p of an intermediate merge level: inside every
+// aligned 128-byte row (R words) the word index is XORed with the row index
+// mod R.  A thread stores IPT consecutive words, so plain slots put the
+// threads of a warp that are R / IPT apart on one bank (16-way for 8-byte
+// words and IPT = 8); with the XOR every bank takes the minimum two (8-byte)
+// or one (4-byte) accesses of a warp store for IPT = 1 .. 16, and the merge
+// reads of neighbouring threads spread the same way.  A permutation inside
+// each row, so the arrays keep their size (P must be a multiple of R).
+template <class T>
+__device__ __forceinline__ int merge_slot(int p)
+{
+    constexpr int R = 128 / (int)sizeof(T);
+    return p ^ ((p / R) & (R - 1));
+}
+
 // Ascending merge sort of P = IPT * blockDim.x words held IPT per thread in
-// v (thread t holds positions t IPT ..), result in s; s2 is scratch of P
-// words.  Each thread sorts its IPT words in registers (bitonic network),
-// then runs of width w = IPT, 2 IPT, .. are merged pairwise: thread t
-// produces the IPT outputs starting at t IPT of its merged run, finding its
-// start on the merge path by a binary search (the diagonal split with
-// A[i - 1] <= B[d - i], ties taken from the left run) and merging
-// sequentially.  Every thread of the CTA calls it.
+// v (thread t holds positions t IPT ..), result in s (plain order); s2 is
+// scratch of P words.  Each thread sorts its IPT words in registers
+// (bitonic network), then runs of width w = IPT, 2 IPT, .. are merged
+// pairwise: thread t produces the IPT outputs starting at t IPT of its
+// merged run, finding its start on the merge path by a binary search (the
+// diagonal split with A[i - 1] <= B[d - i], ties taken from the left run)
+// and merging sequentially with the heads of both runs in registers.
+// Intermediate levels use the slots of merge_slot; the last level writes
+// plain positions.  Every thread of the CTA calls it.
 template <int IPT, class T>
 __device__ __forceinline__ void cta_merge_sort(T (&v)[IPT], T *s, T *s2, int P)
 {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "merge_slot assumes 4- or 8-byte words");
 #pragma unroll
     for (int k = 2; k <= IPT; k <<= 1) {
 #pragma unroll
@@ -236,28 +254,37 @@ __device__ __forceinline__ void cta_merge_sort(T (&v)[IPT], T *s, T *s2, int P)
     // the last one lands in s
     int levels = 0;
     for (int w = IPT; w < P; w <<= 1) ++levels;
+    const bool swz = P % (128 / (int)sizeof(T)) == 0;   // whole rows: the slots are a permutation
+    auto slot = [&](int p) { return swz ? merge_slot<T>(p) : p; };
     T *src = (levels & 1) ? s2 : s, *dst = (levels & 1) ? s : s2;
 #pragma unroll
-    for (int r = 0; r < IPT; ++r) src[o + r] = v[r];
+    for (int r = 0; r < IPT; ++r) src[levels ? slot(o + r) : o + r] = v[r];
     __syncthreads();
     for (int w = IPT; w < P; w <<= 1) {
+        const bool last = 2 * w >= P;
         const int base = o & ~(2 * w - 1);       // start of this thread's merged run
         const int d = o - base;                   // output offset inside it
-        const T *A = src + base, *B = src + base + w;
+        const int ba = base, bb = base + w;       // the two runs
         int lo = d > w ? d - w : 0, hi = d < w ? d : w;
         while (lo < hi) {
             const int m = (lo + hi) >> 1;
-            if (A[m] <= B[d - 1 - m]) lo = m + 1; else hi = m;
+            if (src[slot(ba + m)] <= src[slot(bb + d - 1 - m)]) lo = m + 1; else hi = m;
         }
         int ia = lo, ib = d - lo;
+        T a = src[slot(ba + (ia < w ? ia : w - 1))];
+        T b = src[slot(bb + (ib < w ? ib : w - 1))];
 #pragma unroll
         for (int r = 0; r < IPT; ++r) {
-            const bool take_a = ib >= w || (ia < w && A[ia] <= B[ib]);
-            v[r] = take_a ? A[ia] : B[ib];
-            if (take_a) ++ia; else ++ib;
+            const bool take_a = ib >= w || (ia < w && a <= b);
+            v[r] = take_a ? a : b;
+            if (take_a) {
+                if (++ia < w) a = src[slot(ba + ia)];
+            } else {
+                if (++ib < w) b = src[slot(bb + ib)];
+            }
         }
 #pragma unroll
-        for (int r = 0; r < IPT; ++r) dst[o + r] = v[r];
+        for (int r = 0; r < IPT; ++r) dst[last ? o + r : slot(o + r)] = v[r];
         __syncthreads();
         T *tmp = src; src = dst; dst = tmp;
     }
