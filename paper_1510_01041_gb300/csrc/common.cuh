@@ -275,13 +275,17 @@ __device__ __forceinline__ void cta_merge_sort(T (&v)[IPT], T *s, T *s2, int P)
         T b = src[slot(bb + (ib < w ? ib : w - 1))];
 #pragma unroll
         for (int r = 0; r < IPT; ++r) {
+            // branch-free: the taken head is replaced by the next word of its
+            // run (one load, skipped past the run's end)
             const bool take_a = ib >= w || (ia < w && a <= b);
-            v[r] = take_a ? a : b;
-            if (take_a) {
-                if (++ia < w) a = src[slot(ba + ia)];
-            } else {
-                if (++ib < w) b = src[slot(bb + ib)];
-            }
+            const T x = take_a ? a : b;
+            v[r] = x;
+            ia += take_a;
+            ib += !take_a;
+            const int nx = take_a ? ba + ia : bb + ib;
+            const T y = (take_a ? ia : ib) < w ? src[slot(nx)] : x;
+            a = take_a ? y : a;
+            b = take_a ? b : y;
         }
 #pragma unroll
         for (int r = 0; r < IPT; ++r) dst[last ? o + r : slot(o + r)] = v[r];
