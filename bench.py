@@ -35,6 +35,7 @@ N_POINTS = 8192
 OUTLIER_FRAC = 0.4
 METRIC = "exact LMS solves/sec at n=8192, learned-seeded branch-and-bound (plain sweep alongside)"
 UNIT = "solves/s"
+WORKLOAD = "single exact LMS fit, n=8192 int16, 40% outliers (line_with_outliers)"
 # Algorithmic work of the sweep kernel per event (one pair of points meeting):
 # 2 position reads, 4 order/position writes, 3 projections (2 IMAD each),
 # 2 window widths and centres, 2 exact candidate comparisons, decode.
@@ -156,7 +157,7 @@ def _reference_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128",
         "data": "synthetic", "candidate_slopes_per_sec": v * slopes,
-        "config": {"workload": "single exact LMS fit, n=8192 int16, 40% outliers", "n": N_POINTS,
+        "config": {"workload": WORKLOAD, "n": N_POINTS, "h": N_POINTS // 2 + 1,
                    "algorithm": "CPU oracle O2 (exact rational sweep)"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} full solves at n={N_POINTS}"},
@@ -612,8 +613,7 @@ def main():
                   "candidate_slopes_per_sec": plain_value * slopes, "algorithm": "kinetic sweep, every slope"},
         "learned": {"events_swept_mean": mean("events_swept"), "events_total_mean": mean("events_total"),
                     "nodes_evaluated_mean": mean("nodes_evaluated"), "upper_bound_mean": mean("upper_bound")},
-        "config": {"workload": "single exact LMS fit, n=8192 int16, 40% outliers (line_with_outliers)",
-                   "n": N_POINTS, "h": N_POINTS // 2 + 1,
+        "config": {"workload": WORKLOAD, "n": N_POINTS, "h": N_POINTS // 2 + 1,
                    "algorithm": "learned-seeded branch-and-bound + sweep of surviving slopes",
                    "l2": "flushed before every step (256 MB write, outside the timed events)",
                    "parallelism": f"replicas x{ws}"},
