@@ -29,6 +29,19 @@ def test_bound_sound_and_tight():
             s = a + (b - a) * t
             assert lb <= bound.width_at(xs, ys, h, s)
         assert bound.lower_bound(xs, ys, h, a, a) == bound.width_at(xs, ys, h, a)
+        assert lb >= 0
+
+
+def test_bound_clamps_at_zero():
+    # over a very wide slope interval the hulls of the projections overlap:
+    # the difference of order statistics is negative and the bound is 0
+    rng = np.random.default_rng(5)
+    for _ in range(10):
+        n = int(rng.integers(4, 12))
+        xs = rng.integers(1, 50, n).tolist()          # x > 0: every hull is wide
+        ys = rng.integers(-50, 50, n).tolist()
+        h = n // 2 + 1
+        assert bound.lower_bound(xs, ys, h, Fraction(-10**6), Fraction(10**6)) == 0
 
 
 def test_width_matches_subset_definition():
