@@ -1,5 +1,8 @@
 """The set-network oracle's backward pass equals finite differences of its
-loss (float64), and bf16 rounding matches the IEEE round-to-nearest-even rule."""
+loss (float64); bf16 rounding matches the IEEE round-to-nearest-even rule;
+a sparse network's forward pass and the set frame match values worked out
+by hand (ReLUs, max-pooling, biases, the bounding-box frame and the target
+definition)."""
 import numpy as np
 
 from oracle import setnet
@@ -34,3 +37,49 @@ def test_backward_matches_finite_differences():
         e[k] = eps
         num = (setnet.loss_only(flat + e, sets, targets, lam) - setnet.loss_only(flat - e, sets, targets, lam)) / (2 * eps)
         assert abs(num - g[k]) <= 1e-6 + 1e-4 * abs(num), (k, num, g[k])
+
+
+def _pack(P):
+    return np.concatenate([P[name].ravel() for name, _ in setnet.SHAPES])
+
+
+def test_forward_by_hand():
+    # a sparse network whose outputs follow by hand: frame of
+    # x = {0, 10, 4}, y = {0, 4, 2} is centre (5, 2), scale 5, so the
+    # normalised points are xn = (-1, 1, -0.2), yn = (-0.4, 0.4, 0)
+    P = {name: np.zeros(shp) for name, shp in setnet.SHAPES}
+    P["W1"][0, 0] = 1.0     # h1_0 = relu(xn)   -> pooled max 1
+    P["W1"][1, 0] = -1.0    # h1_1 = relu(-xn)  -> pooled max 1
+    P["W1"][2, 1] = 1.0     # h1_2 = relu(yn)   -> pooled max 0.4
+    P["b1"][3] = -2.0       # h1_3 = relu(-2) = 0 everywhere
+    for c in range(4):
+        P["W2"][c, c] = 1.0
+    P["W2"][4, 3] = 1.0
+    P["b2"][4] = 0.5        # h2_4 = relu(h1_3 + 0.5) = 0.5
+    P["W3"][0, 0] = 1.0     # h3_0 = 1
+    P["W3"][1, 1] = -1.0    # h3_1 = relu(-1) = 0
+    P["W3"][2, 2] = 1.0     # h3_2 = 0.4
+    P["W3"][3, 4] = 2.0     # h3_3 = 1
+    P["W4"][0, 0] = 2.0
+    P["W4"][0, 1] = 5.0     # multiplies the clipped unit: contributes 0
+    P["W4"][0, 3] = 0.25
+    P["W4"][1, 2] = 1.0
+    P["b4"][:] = (0.5, -1.0)
+    x, y = [0, 10, 4], [0, 4, 2]
+    assert setnet.frame(x, y) == (5.0, 2.0, 5.0)
+    phi, b, _ = setnet.forward(_pack(P), x, y)
+    assert abs(phi - (2.0 * 1.0 + 0.25 * 1.0 + 0.5)) < 1e-12
+    assert abs(b - (0.4 - 1.0)) < 1e-12
+    # the loss of the same parameters (no rounding needed: all exact in bf16)
+    L = setnet.loss_only(_pack(P), [(x, y)], [(2.0, 0.0)], 0.5)
+    assert abs(L - ((phi - 2.0) ** 2 + 0.5 * b * b)) < 1e-12
+
+
+def test_frame_scale_floor_and_target_definition():
+    # scale is half the larger side, at least 1; a single point has scale 1
+    assert setnet.frame([3, 3], [7, 8]) == (3.0, 7.5, 1.0)
+    assert setnet.frame([0, 40], [0, 10]) == (20.0, 5.0, 20.0)
+    # target of the line y = x through a frame centred at (20, 5), scale 20:
+    # angle pi/4, normalised intercept (0 - 5 + 1 * 20) / 20
+    phi, bn = setnet.targets_from_fit([0, 40], [0, 10], 1.0, 0.0)
+    assert abs(phi - np.pi / 4) < 1e-15 and abs(bn - 0.75) < 1e-15
