@@ -1,15 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark of the exact 2D LMS line estimator on the GB300.
 
-Workload (one "step"): one exact LMS fit of n = 8192 int16 points, 40%
-outliers (y = round(0.7 x + 100) + U{-3..3} inliers, uniform outliers), over
-all n(n-1)/2 = 33,550,336 candidate slopes, through the C ABI.  The headline
-path is the learned-seeded exact branch-and-bound (lms_fit_learned: the set
-network predicts the slope, bounds drop slope intervals, the rest is swept);
-the plain kinetic sweep over every candidate slope (lms_fit) is timed the
-same way beside it.  Both are bit-identical to the oracle.  Every step uses a
-fresh seeded instance already resident in HBM; L2 is flushed (256 MB write)
-before each step, outside the timed events.
+Workload (one "step"): one exact LMS fit of n = 8192 int16 points on a line
+of random slope angle U(-1.4, 1.4) and integer intercept, inlier noise
+U{-3..3}, 45% uniform outliers (the learned-proposal workload), over all
+n(n-1)/2 = 33,550,336 candidate slopes, through the C ABI.  Three arms on the
+same instances, bit-identical to each other (and, in the tests, to the
+oracle):
+
+* ``learned``       (headline ``value``) lms_fit_learned: the set network
+                    predicts the slope, branch-and-bound takes its upper bound
+                    there, drops slope intervals whose lower bound exceeds it,
+                    and sweeps the rest exactly;
+* ``quantile_bnb``  lms_fit_bnb without a network: the same branch-and-bound
+                    seeded at quantiles of sampled pair slopes;
+* ``plain``         lms_fit with the kinetic sweep over every candidate slope.
+
+The previous fixed-slope workload (slope 0.7, 40% outliers) is timed beside
+them (``line_40pct``).  Every step uses a fresh seeded instance already
+resident in HBM; L2 is flushed (256 MB write) before each step, outside the
+timed events.  ``e2e`` runs the learned fit through the host-buffer entry
+point lms_fit_learned_host, copies included.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,20 +43,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_POINTS = 8192
-OUTLIER_FRAC = 0.4
-METRIC = "exact LMS solves/sec at n=8192, learned-seeded branch-and-bound (plain sweep alongside)"
+OUTLIER_FRAC = 0.45
+PHI_MAX = 1.4
+METRIC = "exact LMS solves/sec at n=8192, learned-seeded branch-and-bound (quantile-seeded and plain sweep alongside)"
 UNIT = "solves/s"
-WORKLOAD = "single exact LMS fit, n=8192 int16, 40% outliers (line_with_outliers)"
+WORKLOAD = "single exact LMS fit, n=8192 int16, random slope angle U(-1.4,1.4), 45% outliers (sloped)"
 # Algorithmic work of the sweep kernel per event (one pair of points meeting):
 # 2 position reads, 4 order/position writes, 3 projections (2 IMAD each),
 # 2 window widths and centres, 2 exact candidate comparisons, decode.
 SWEEP_INT_OPS_PER_EVENT = 50
-INT_LANES_PER_SM = 128
-# DRAM bytes (read + written) of one timed plain-path k_sweep launch of this
-# benchmark, from an ncu capture of the current kernel (192.06 MB read,
-# 3.58 MB written); against 194 MB of algorithmic traffic (events and range
-# start orders).  Must be re-measured whenever the kernel changes.
-SWEEP_DRAM_BYTES = 195_635_456
 
 
 def rank_seeds(rank: int, count: int):
@@ -143,7 +149,7 @@ def _reference_arm(args):
     from paper_1510_01041_gb300 import datagen
     oracle.build()
     cores = oracle.max_threads()
-    inst = [datagen.line_with_outliers(N_POINTS, 1000 + s) for s in range(args.warmup + args.steps)]
+    inst = _instances([1000 + s for s in range(args.warmup + args.steps)])
     for s in range(args.warmup):
         oracle.lms_i16(*inst[s], 0, "sweep")
     t0 = time.perf_counter()
@@ -459,6 +465,50 @@ def _timed(fit, steps, warmup, flush, stream, barrier):
     return sum(a.elapsed_time(b) for a, b in ev)
 
 
+def node_bound_ops(n: int) -> int:
+    """Algorithmic int32 instruction-equivalents of one slope interval's lower
+    bound: projections of all points at both interval ends (4n, 4 ops each:
+    a 32x32->64 multiply-add, shift, subtract, min/max), two comparison sorts
+    of n 64-bit words (n ceil(log2 n) comparisons each, 4 ops per 64-bit
+    compare-and-select) and one scan of the n - h + 1 windows (3 ops each)."""
+    lg = max(1, math.ceil(math.log2(n)))
+    return 4 * n * 4 + 2 * n * lg * 4 + 3 * n
+
+
+# Algorithmic work per unit, int32 instruction-equivalents:
+#   sweep        per event swept (SWEEP_INT_OPS_PER_EVENT)
+#   node_bounds  per slope interval bounded (node_bound_ops)
+#   count        per candidate pair tested by the restricted pair pass: two
+#                int16 unpacks and differences, a float reciprocal and
+#                product, a 4-step search of the slope covers, index update
+RESTRICTED_COUNT_OPS_PER_PAIR = 12
+
+
+def _roof(stage, stages, units_per_fit, ops_per_unit, fits, peak_tops, mhz_basis, traffic=None):
+    ms, launches = stages.get(stage, (0.0, 0))
+    if not launches or units_per_fit <= 0:
+        return None
+    per_launch_s = ms / launches / 1000.0
+    units = units_per_fit * fits / launches
+    achieved = units * ops_per_unit / per_launch_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s (int32)",
+            "frac": achieved / peak_tops, "traffic": traffic, "traffic_unit": "bytes per launch (ncu)",
+            "stage": stage, "kernel_ms": per_launch_s * 1e3, "launches_per_fit": launches / fits,
+            "units_per_launch": units, "ops_per_unit": ops_per_unit, "peak_basis": mhz_basis}
+
+
+# Kernels of the timed paths: the stage name the library's profiler uses,
+# the kernel, and its DRAM traffic per launch from the ncu captures under
+# profiles/ (None when the kernel changed after its capture).
+KERNEL_OF_STAGE = {"sweep": "k_sweep", "node_bounds": "k_node_lb", "count": "k_count_restricted"}
+DRAM_BYTES = {}
+
+
+def _instances(seeds):
+    from paper_1510_01041_gb300 import datagen
+    return [datagen.sloped(N_POINTS, s, OUTLIER_FRAC, phi_max=PHI_MAX)[:2] for s in seeds]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -509,15 +559,23 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     total = args.warmup + args.steps
     seeds = rank_seeds(rank, total)
-    host = [datagen.line_with_outliers(N_POINTS, s) for s in seeds]
+    host = _instances(seeds)
+    # the previous workload (fixed slope 0.7, 40% outliers) beside it
+    host2 = [datagen.line_with_outliers(N_POINTS, s, 0.4) for s in seeds]
     xs = [torch.from_numpy(h[0]).to(dev) for h in host]
     ys = [torch.from_numpy(h[1]).to(dev) for h in host]
-    out_l = torch.empty((total, lms.RESULT_DTYPE.itemsize), dtype=torch.uint8, device=dev)
-    out_p = torch.empty((total, lms.RESULT_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    xs2 = [torch.from_numpy(h[0]).to(dev) for h in host2]
+    ys2 = [torch.from_numpy(h[1]).to(dev) for h in host2]
+    R = lms.RESULT_DTYPE.itemsize
+    outs = {k: torch.empty((total, R), dtype=torch.uint8, device=dev)
+            for k in ("learned", "quantile", "plain", "learned2", "plain2")}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     lms.reserve(N_POINTS, algorithm="bnb")
     net = lms.pretrained()
+    # measured int32 peaks of this GPU (outside every timed region)
+    peak_addxor = lms.measure_int_peak(0, 20000) / 1e12
+    peak_imad = lms.measure_int_peak(1, 20000) / 1e12
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -526,116 +584,144 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    learned_stats = []
-
-    def fit_learned(s):
-        learned_stats.append(net.fit(xs[s], ys[s], 0, out=out_l[s])[1])
-
-    def fit_plain(s):
-        lms.fit(xs[s], ys[s], 0, "sweep", out=out_p[s])
-
+    stats = {"learned": [], "quantile": []}
+    arms = {
+        "learned": lambda s: stats["learned"].append(net.fit(xs[s], ys[s], 0, out=outs["learned"][s])[1]),
+        "quantile": lambda s: stats["quantile"].append(
+            lms.fit_bnb(xs[s], ys[s], 0, None, out=outs["quantile"][s], seed_mode="quantiles")[1]),
+        "plain": lambda s: lms.fit(xs[s], ys[s], 0, "sweep", out=outs["plain"][s]),
+        "learned2": lambda s: net.fit(xs2[s], ys2[s], 0, out=outs["learned2"][s]),
+        "plain2": lambda s: lms.fit(xs2[s], ys2[s], 0, "sweep", out=outs["plain2"][s]),
+    }
     for s in range(args.warmup):
         flush.fill_(s & 0xff)
-        fit_learned(s)
-        fit_plain(s)
+        for f in arms.values():
+            f(s)
     barrier()
-    learned_stats.clear()
-    launches0 = lms.launch_count()
+    for v in stats.values():
+        v.clear()
+    ms, stages = {}, {}
     lms.profile_read()
     lms.profile_enable(True)
     with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
-        learned_ms = _timed(fit_learned, args.steps, args.warmup, flush, stream, barrier)
-        wall = time.perf_counter() - wall0
+        launches0 = lms.launch_count()
+        ms["learned"] = _timed(arms["learned"], args.steps, args.warmup, flush, stream, barrier)
         launches = lms.launch_count() - launches0
-        stages_l = lms.profile_read()
-        plain_ms = _timed(fit_plain, args.steps, args.warmup, flush, stream, barrier)
-        stages_p = lms.profile_read()
+        wall = time.perf_counter() - wall0
+        stages["learned"] = lms.profile_read()
+        for k in ("quantile", "plain", "learned2", "plain2"):
+            ms[k] = _timed(arms[k], args.steps, args.warmup, flush, stream, barrier)
+            stages[k] = lms.profile_read()
     lms.profile_enable(False)
-    learned_ms = max_over_ranks(learned_ms, dev)
-    plain_ms = max_over_ranks(plain_ms, dev)
-    res_l = lms.decode(out_l)[args.warmup:]
-    res_p = lms.decode(out_p)[args.warmup:]
+    ms = {k: max_over_ranks(v, dev) for k, v in ms.items()}
+    res = {k: lms.decode(v)[args.warmup:] for k, v in outs.items()}
     keys = ("status", "w_num", "w_den", "s_num", "s_den", "t_num", "t_den", "i", "j", "theta1", "theta2", "med_sq")
-    for a, b in zip(res_l, res_p):
-        if a["status"] != lms.LMS_OK or tuple(a[k] for k in keys) != tuple(b[k] for k in keys):
-            raise SystemExit(f"learned and plain fits disagree: {a} {b}")
+    for a, b, c in zip(res["learned"], res["quantile"], res["plain"]):
+        if a["status"] != lms.LMS_OK or not (tuple(a[k] for k in keys) == tuple(b[k] for k in keys)
+                                             == tuple(c[k] for k in keys)):
+            raise SystemExit(f"learned, quantile-seeded and plain fits disagree: {a} {b} {c}")
+    for a, c in zip(res["learned2"], res["plain2"]):
+        if a["status"] != lms.LMS_OK or tuple(a[k] for k in keys) != tuple(c[k] for k in keys):
+            raise SystemExit(f"learned and plain fits disagree (line_with_outliers): {a} {c}")
 
-    # end to end through the public API with host buffers (pinned), copies inside
+    # end to end through the public C ABI with host buffers: lms_fit_learned_host
+    # copies the points in, fits and copies the 88-byte result out every step
     pin_x = [torch.from_numpy(h[0]).pin_memory() for h in host]
     pin_y = [torch.from_numpy(h[1]).pin_memory() for h in host]
-    dres = torch.empty(lms.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-    hres = torch.empty(lms.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
-    dx = torch.empty(N_POINTS, dtype=torch.int16, device=dev)
-    dy = torch.empty(N_POINTS, dtype=torch.int16, device=dev)
+    hres = torch.zeros(R, dtype=torch.uint8).pin_memory()
     barrier()
     t0 = time.perf_counter()
     for k in range(args.steps):
         s = args.warmup + k
-        dx.copy_(pin_x[s], non_blocking=True)
-        dy.copy_(pin_y[s], non_blocking=True)
-        net.fit(dx, dy, 0, out=dres)
-        hres.copy_(dres, non_blocking=True)
-        torch.cuda.synchronize(dev)
-        assert lms.decode(hres)[0]["status"] == lms.LMS_OK
+        net.fit_host(pin_x[s], pin_y[s], 0, out=hres)
+        r = lms.decode(hres)[0]
+        if tuple(r[q] for q in keys) != tuple(res["learned"][k][q] for q in keys):
+            raise SystemExit("host-buffer learned fit disagrees with the device-buffer fit")
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
 
     slopes = N_POINTS * (N_POINTS - 1) // 2
-    solves = ws * args.steps
-    value = job_rate(args.steps, ws, learned_ms)
-    plain_value = job_rate(args.steps, ws, plain_ms)
+    rate = {k: job_rate(args.steps, ws, v) for k, v in ms.items()}
     csum = clk.summary()
-    mhz = csum.get("sm_mhz") or 1462.0
-    int_peak = props.multi_processor_count * INT_LANES_PER_SM * mhz * 1e6 / 1e12
-    # roofline of the plain path's dominant kernel, the sweep: exact events per
-    # launch = pairs with distinct x, counted per instance on the host
+    mhz = csum.get("sm_mhz") or 0.0
+    basis = (f"measured: lms_measure_int_peak kind 0 (int32 add/xor chains, full occupancy), "
+             f"{peak_addxor:.2f} Tops/s; kind 1 (multiply-add) {peak_imad:.2f} Tops/s")
+    peak = max(peak_addxor, peak_imad)
+    mean = lambda arm, k: float(np.mean([st[k] for st in stats[arm]])) if stats[arm] else 0.0
+    roofs = {}
+    for arm, st in (("learned", stages["learned"]),):
+        roofs["sweep"] = _roof("sweep", st, mean(arm, "events_swept"), SWEEP_INT_OPS_PER_EVENT, args.steps, peak,
+                               basis, DRAM_BYTES.get("k_sweep"))
+        roofs["node_bounds"] = _roof("node_bounds", st, mean(arm, "nodes_evaluated"), node_bound_ops(N_POINTS),
+                                     args.steps, peak, basis, DRAM_BYTES.get("k_node_lb"))
+        roofs["count"] = _roof("count", st, slopes, RESTRICTED_COUNT_OPS_PER_PAIR, args.steps, peak, basis,
+                               DRAM_BYTES.get("k_count_restricted"))
+    # the plain path's sweep kernel: every pair with distinct x is an event
     events = [int(np.sum(np.triu(np.not_equal.outer(h[0], h[0]), 1))) for h in host[args.warmup:]]
-    sweep_ms, sweep_launches = stages_p.get("sweep", (0.0, 0))
+    plain_sweep_roof = _roof("sweep", stages["plain"], float(np.mean(events)), SWEEP_INT_OPS_PER_EVENT, args.steps,
+                             peak, basis, DRAM_BYTES.get("k_sweep_plain"))
+    modeled = {k: v for k, v in roofs.items() if v}
+    dom = max(modeled, key=lambda k: stages["learned"][k][0]) if modeled else None
     roof = None
-    if sweep_launches:
-        per_launch_s = sweep_ms / sweep_launches / 1000.0
-        ev_per_launch = sum(events) / len(events)
-        achieved = SWEEP_INT_OPS_PER_EVENT * ev_per_launch / per_launch_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": int_peak, "unit": "Tops/s (int32)",
-                "frac": achieved / int_peak, "traffic": SWEEP_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu)",
-                "kernel": "k_sweep (plain path)",
-                "kernel_ms": per_launch_s * 1e3, "events_per_launch": ev_per_launch,
-                "ops_per_event": SWEEP_INT_OPS_PER_EVENT,
-                "peak_basis": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int32 lanes x "
-                              f"median SM clock {mhz:.0f} MHz under load (derived, not measured)"}
-    mean = lambda k: float(np.mean([st[k] for st in learned_stats])) if learned_stats else None
+    if dom:
+        roof = dict(modeled[dom])
+        roof["kernel"] = KERNEL_OF_STAGE[dom] + " (learned-seeded path, dominant modeled kernel)"
+    if plain_sweep_roof:
+        plain_sweep_roof["kernel"] = "k_sweep (plain path, every event)"
+
+    def arm_line(k, extra=None):
+        d = {"value": rate[k], "unit": UNIT, "ms_per_step": ms[k] / args.steps,
+             "candidate_slopes_per_sec": rate[k] * slopes}
+        d.update(extra or {})
+        return d
+
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": learned_ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": rate["learned"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms["learned"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "candidate_slopes_per_sec": value * slopes,
-        "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms / args.steps,
-                  "candidate_slopes_per_sec": plain_value * slopes, "algorithm": "kinetic sweep, every slope"},
-        "learned": {"events_swept_mean": mean("events_swept"), "events_total_mean": mean("events_total"),
-                    "nodes_evaluated_mean": mean("nodes_evaluated"), "upper_bound_mean": mean("upper_bound")},
+        "candidate_slopes_per_sec": rate["learned"] * slopes,
+        "learned": arm_line("learned", {"events_swept_mean": mean("learned", "events_swept"),
+                                        "nodes_evaluated_mean": mean("learned", "nodes_evaluated"),
+                                        "upper_bound_mean": mean("learned", "upper_bound"),
+                                        "algorithm": "set-network seed + branch-and-bound"}),
+        "quantile_bnb": arm_line("quantile", {"events_swept_mean": mean("quantile", "events_swept"),
+                                              "nodes_evaluated_mean": mean("quantile", "nodes_evaluated"),
+                                              "upper_bound_mean": mean("quantile", "upper_bound"),
+                                              "algorithm": "branch-and-bound seeded at sample quantiles "
+                                                           "(the method without the network)"}),
+        "plain": arm_line("plain", {"algorithm": "kinetic sweep, every slope"}),
+        "events_total_mean": mean("learned", "events_total"),
+        "line_40pct": {"workload": "line_with_outliers: slope 0.7, 40% outliers, n=8192",
+                       "learned": arm_line("learned2"), "plain": arm_line("plain2")},
         "config": {"workload": WORKLOAD, "n": N_POINTS, "h": N_POINTS // 2 + 1,
                    "algorithm": "learned-seeded branch-and-bound + sweep of surviving slopes",
                    "l2": "flushed before every step (256 MB write, outside the timed events)",
                    "parallelism": f"replicas x{ws}"},
-        "e2e": {"value": solves / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 2 * N_POINTS,
-                "d2h_bytes_per_step": lms.RESULT_DTYPE.itemsize,
+        "e2e": {"value": args.steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 2 * N_POINTS,
+                "d2h_bytes_per_step": R,
+                "api": "lms_fit_learned_host (C ABI, pinned host buffers, copies in the timed region)",
                 "l2": "not flushed: back-to-back calls, wall clock around copies, fit and result read"},
         "gpu_launches": launches,
         "clocks": {k: csum.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "roofline": roof,
-        "stage_ms_per_step": {k: v[0] / args.steps for k, v in sorted(stages_l.items(), key=lambda kv: -kv[1][0])},
-        "plain_stage_ms_per_step": {k: v[0] / args.steps for k, v in sorted(stages_p.items(), key=lambda kv: -kv[1][0])},
+        "roofline_kernels": {"learned_path": modeled, "plain_path_sweep": plain_sweep_roof},
+        "int_peak_tops": {"add_xor": peak_addxor, "imad": peak_imad, "sm_mhz_during_run": mhz,
+                          "sms": props.multi_processor_count},
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in
+                              sorted(stages["learned"].items(), key=lambda kv: -kv[1][0])},
+        "plain_stage_ms_per_step": {k: v[0] / args.steps for k, v in
+                                    sorted(stages["plain"].items(), key=lambda kv: -kv[1][0])},
         "wall_s": wall,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, o = _cpu_baseline(*host[args.warmup])
-        r = res_l[0]
+        r = res["learned"][0]
         cb["agrees_with_gpu"] = (r["w_num"], r["w_den"], r["s_num"], r["s_den"], r["t_num"], r["i"], r["j"]) == (
             o.w_num, o.w_den, o.s_num, o.s_den, o.t_num, o.i, o.j)
         line["cpu_baseline"] = cb
     if args.breakdown and rank == 0:
-        for name, st in (("learned", stages_l), ("plain", stages_p)):
-            for k, v in sorted(st.items(), key=lambda kv: -kv[1][0]):
+        for name in ("learned", "quantile", "plain"):
+            for k, v in sorted(stages[name].items(), key=lambda kv: -kv[1][0]):
                 print(f"  {name:8s} {k:14s} {v[0] / args.steps:9.3f} ms/step  launches {v[1]}", file=sys.stderr)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -194,6 +194,14 @@ LMS_API int lms_setnet_load(lms_setnet *net, const char *path);
 LMS_API int lms_fit_learned(lms_setnet *net, const void *x, const void *y, int64_t n, int64_t h,
                             const lms_options *opt, lms_result *out, lms_bnb_stats *stats,
                             lms_stream_t stream);
+/* lms_fit_learned with host arrays x, y (int16, n <= 65536; page-locked
+ * memory makes the copies asynchronous) and a host result: copies the points
+ * into device staging owned by `net` (allocated on the first such call, kept
+ * until lms_setnet_destroy), fits, copies the result back and waits for
+ * `stream`.  One net must not run two host-buffer fits at once. */
+LMS_API int lms_fit_learned_host(lms_setnet *net, const void *x, const void *y, int64_t n, int64_t h,
+                                 const lms_options *opt, lms_result *out, lms_bnb_stats *stats,
+                                 lms_stream_t stream);
 
 /*
  * Batched fits of many point sets of uneven size (not in the paper: its
@@ -292,15 +300,29 @@ LMS_API const char *lms_stage_name(int stage);
 LMS_API int64_t lms_launch_count(void);
 
 /*
+ * lms_measure_int_peak -- measured int32 instruction throughput of the
+ * current GPU (instructions per second over all SMs), the denominator of the
+ * integer roofline reported for the LMS kernels.  A full-occupancy grid runs
+ * eight independent dependency chains per thread for `iters` x 8 steps:
+ *   kind 0  alternating add and xor (one add-class and one logic-class
+ *           instruction per step),
+ *   kind 1  32-bit multiply-add (one instruction per step).
+ * Timed with CUDA events on `stream` (one warm-up launch first); synchronous.
+ * Allocates and frees 64 bytes of device memory.  LMS_ERR_ARG for a bad kind,
+ * iters outside [1, 2^24] or a null pointer.
+ */
+LMS_API int lms_measure_int_peak(int32_t kind, int64_t iters, double *ops_per_s, lms_stream_t stream);
+
+/*
  * lms_fit_noalloc -- the plain fit (every pairwise slope, sort, window scan)
  * for callers that cannot have the library allocate device memory.  The
  * paper has no counterpart; it is an interface convenience.
  *
- * Who needs it: code that enqueues work while a stream is being captured
- * into a CUDA graph (an allocation there invalidates the capture), real-time
- * or embedded loops that forbid allocation once running, and frameworks
- * that hand out all device memory from their own pools.  lms_fit may grow an
- * internal workspace with cudaMalloc; this call never allocates or frees.
+ * Who needs it: real-time or embedded loops that forbid allocation once
+ * running (cudaMalloc and cudaFree can block and synchronise the device),
+ * and frameworks that hand out all device memory from their own pools and
+ * budgets.  lms_fit may grow an internal workspace with cudaMalloc; this
+ * call never allocates or frees.
  *
  *   x, y    device arrays of n int16 coordinates.
  *   n       2 <= n <= LMS_NOALLOC_MAX_N; larger n returns LMS_ERR_TOO_LARGE.

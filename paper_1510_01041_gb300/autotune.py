@@ -1,8 +1,8 @@
 """Autotuner for batched fits: picks the size threshold between the plain
 kernel classes and the sweep, and the number of sweep streams, by timing
 CUDA-graph replays of a batch plan on the caller's own sets.  Results are
-cached per (device name, size histogram) in autotune_cache.json next to
-this file.
+cached per (device name, size mix) in autotune_cache.json next to this
+file, or in the file $LMS_AUTOTUNE_CACHE names.
 
     from paper_1510_01041_gb300 import autotune
     plan, cfg = autotune.tuned_plan(offsets, x, y, offsets_dev)
@@ -18,16 +18,24 @@ import numpy as np
 
 from . import lms
 
-CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
+# The cache file: $LMS_AUTOTUNE_CACHE if set, else next to this module; a
+# cache that cannot be written is reported by a warning and tuning still works.
+CACHE = os.environ.get("LMS_AUTOTUNE_CACHE") or os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                             "autotune_cache.json")
 PLAIN_MAX = (64, 128, 256)
 STREAMS = (8, 16, 32, 48)
 
 
 def _key(offsets, device_name):
+    """Device, set count, total points, total candidate pairs and a histogram
+    of set sizes at eighth-octave resolution: batches that differ in how
+    their work is spread over sizes get different keys; the order of the
+    sets does not matter."""
     sizes = np.diff(np.asarray(offsets, dtype=np.int64))
-    hist = np.histogram(np.log2(np.maximum(sizes, 2)), bins=16, range=(1, 17))[0]
+    hist = np.histogram(np.log2(np.maximum(sizes, 2)), bins=128, range=(1, 17))[0]
+    pairs = int(np.sum(sizes * (sizes - 1) // 2))
     h = hashlib.sha1(hist.tobytes() + device_name.encode()).hexdigest()[:16]
-    return f"{device_name}:{sizes.size}:{h}"
+    return f"{device_name}:{sizes.size}:{int(sizes.sum())}:{pairs}:{h}"
 
 
 def _time_plan(plan, x, y, od, reps=2):
@@ -79,7 +87,9 @@ def tuned_plan(offsets, x, y, offsets_dev, use_cache=True):
         cfg, _ = tune(offsets, x, y, offsets_dev)
         cache[key] = cfg
         try:
-            json.dump(cache, open(CACHE, "w"), indent=1)
-        except OSError:
-            pass
+            with open(CACHE, "w") as f:
+                json.dump(cache, f, indent=1)
+        except OSError as e:
+            import warnings
+            warnings.warn(f"autotune cache {CACHE} not written ({e}); set LMS_AUTOTUNE_CACHE to a writable path")
     return lms.BatchPlan(offsets, plain_max_n=cfg["plain_max_n"], streams=cfg["streams"]), cfg

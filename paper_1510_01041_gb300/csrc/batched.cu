@@ -433,7 +433,8 @@ int lms_fit_batched(lms_batch_plan *p, const void *xv, const void *yv, const int
     // sweep sets on their streams
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (size_t k = 0; k < p->sweep_sets.size(); ++k) {
+    bool failed = false;
+    for (size_t k = 0; k < p->sweep_sets.size() && !failed; ++k) {
         const int i = p->sweep_sets[k];
         const int s = p->stream_of[k];
         const long long a = p->off_host[i];
@@ -441,15 +442,17 @@ int lms_fit_batched(lms_batch_plan *p, const void *xv, const void *yv, const int
         SweepPlan sp;
         sweep_plan_configure(sp, n, p->hval[i], sms, 0, 0, true);
         sweep_plan_carve(sp, p->ws[s]);
-        if (launch_sweep(sp, x + a, y + a, p->streams[s]) != cudaSuccess) return LMS_ERR_CUDA;
-        if (launch_argmin(sp.cands, sp.W + sp.G, out + i, LMS_ALGO_SWEEP, sp.meta + 3, p->streams[s]) != cudaSuccess)
-            return LMS_ERR_CUDA;
+        failed = launch_sweep(sp, x + a, y + a, p->streams[s]) != cudaSuccess ||
+                 launch_argmin(sp.cands, sp.W + sp.G, out + i, LMS_ALGO_SWEEP, sp.meta + 3, p->streams[s]) !=
+                     cudaSuccess;
     }
+    // join every forked stream back to the caller's, also after a failed
+    // launch, so the caller's stream stays ordered after all queued work
     for (int s = 0; s < p->nstreams; ++s) {
         cudaEventRecord(p->ev_done[s], p->streams[s]);
         cudaStreamWaitEvent(st, p->ev_done[s], 0);
     }
-    return cudaGetLastError() == cudaSuccess ? LMS_OK : LMS_ERR_CUDA;
+    return (cudaGetLastError() == cudaSuccess && !failed) ? LMS_OK : LMS_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -363,11 +363,11 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         return LMS_ERR_CUDA;
     }
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_SEEDS, st);
         k_x_center<<<1, 1024, 0, st>>>(p.xy, n, xc);
     }
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_SEEDS, st);
         k_pick_seeds<<<1, 128, 0, st>>>(sorted_sample(p), p.S, pred_dev, seed_mode, BNB_SEEDS, seed_keys);
     }
     const int Ps = P < 1024 ? 1024 : P;   // the shared-memory sorts fill whole 1024-thread CTAs
@@ -377,12 +377,12 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     cudaFuncSetAttribute(k_score_dyadic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one_sort);
     cudaFuncSetAttribute(k_node_lb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_sorts);
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_SEEDS, st);
         k_score_dyadic<<<std::min(BNB_SEEDS, grid), 1024, one_sort, st>>>(p.xy, n, h, xc, seed_keys, BNB_SEEDS,
                                                                            seed_w, gscr);
     }
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_SEEDS, st);
         k_min_ub<<<1, 32, 0, st>>>(seed_w, BNB_SEEDS, ub);
     }
     const cudaError_t waited = cudaEventSynchronize(sampled);
@@ -429,7 +429,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
                                 st) != cudaSuccess)
                 return LMS_ERR_CUDA;
             {
-                StageTimer _t(STAGE_OTHER, st);
+                StageTimer _t(STAGE_NODE_LB, st);
                 k_node_lb<<<std::min(chunk, grid), 1024, two_sorts, st>>>(p.xy, n, h, xc, node_keys, chunk, ub, prune,
                                                                         lbv, gscr);
             }

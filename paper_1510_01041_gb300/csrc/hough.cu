@@ -481,11 +481,11 @@ int lms_hough_refine(const uint8_t *edges, int64_t B, int32_t H, int32_t W, int3
     cudaMemsetAsync(err, 0, sizeof(int) * 16, st);
     cudaMemsetAsync(scnt, 0, sizeof(int) * B * top_k, st);
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_HOUGH, st);
         k_edge_count<<<dim3(nchunk, (unsigned)B), 256, 0, st>>>(edges, HW, nchunk, ccnt);
     }
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_HOUGH, st);
         k_edge_scan<<<1, 32, 0, st>>>(ccnt, nchunk, (int)B, coff, img_off);
     }
     std::vector<long long> hoff(B + 1);
@@ -493,24 +493,24 @@ int lms_hough_refine(const uint8_t *edges, int64_t B, int32_t H, int32_t W, int3
     if (cudaStreamSynchronize(st) != cudaSuccess) { cudaFree(mem); return LMS_ERR_CUDA; }
     if (hoff[B] > pts_cap) { cudaFree(mem); return LMS_ERR_UNSUPPORTED; }
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_HOUGH, st);
         k_edge_write<<<dim3(nchunk, (unsigned)B), 32, 0, st>>>(edges, H, W, nchunk, coff, pts);
     }
     const size_t vsm = sizeof(int) * TT * (size_t)n_rho;
     if (vsm > 227 * 1024) { cudaFree(mem); return LMS_ERR_UNSUPPORTED; }
     cudaFuncSetAttribute(k_vote, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_HOUGH, st);
         k_vote<<<dim3((n_theta + TT - 1) / TT, (unsigned)B), 1024, vsm, st>>>(pts, img_off, cs, n_theta, n_rho, acc);
     }
     cudaFuncSetAttribute(k_peaks, cudaFuncAttributeMaxDynamicSharedMemorySize, PEAK_SMEM * 8);
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_HOUGH, st);
         k_peaks<<<(unsigned)B, 1024, PEAK_SMEM * 8, st>>>(acc, n_theta, n_rho, top_k, nms_theta, nms_rho, peaks, gcand,
                                                          gcap, err);
     }
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_HOUGH, st);
         k_gather<false><<<dim3(64, (unsigned)B), 256, 0, st>>>(pts, img_off, cs, n_rho, peaks, top_k, band_px, scnt,
                                                               nullptr, nullptr);
     }
@@ -536,13 +536,13 @@ int lms_hough_refine(const uint8_t *edges, int64_t B, int32_t H, int32_t W, int3
     cudaMemcpyAsync(soff, hsoff.data(), sizeof(long long) * (B * top_k + 1), cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(scnt, 0, sizeof(int) * B * top_k, st);
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_HOUGH, st);
         k_gather<true><<<dim3(64, (unsigned)B), 256, 0, st>>>(pts, img_off, cs, n_rho, peaks, top_k, band_px, scnt,
                                                              soff, keys);
     }
     cudaFuncSetAttribute(k_set_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768 * 4);
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_HOUGH, st);
         k_set_finish<<<(unsigned)(B * top_k), 1024, 32768 * 4, st>>>(pts, img_off, cs, peaks, top_k, soff, keys, sx,
                                                                     sy, err);
     }
@@ -597,7 +597,7 @@ int lms_hough_refine(const uint8_t *edges, int64_t B, int32_t H, int32_t W, int3
             std::vector<int> kept(F);
             if (max_points > 0) {
                 {
-                    StageTimer _t(STAGE_OTHER, st);
+                    StageTimer _t(STAGE_HOUGH, st);
                     k_subsample<true><<<(unsigned)F, 256, 0, st>>>(sx, sy, d_src, d_cnt, d_thr, d_id, sample_seed,
                                                                    nullptr, d_kept, nullptr, nullptr);
                 }
@@ -615,12 +615,12 @@ int lms_hough_refine(const uint8_t *edges, int64_t B, int32_t H, int32_t W, int3
         }
         if (rc == LMS_OK) {
             cudaMemcpyAsync(d_dst, dst.data(), sizeof(long long) * (F + 1), cudaMemcpyHostToDevice, st);
-            StageTimer _t(STAGE_OTHER, st);
+            StageTimer _t(STAGE_HOUGH, st);
             k_subsample<false><<<(unsigned)F, 256, 0, st>>>(sx, sy, d_src, d_cnt, d_thr, d_id, sample_seed, d_dst,
                                                             nullptr, tx, ty);
         }
         if (rc == LMS_OK) {
-            StageTimer _t(STAGE_OTHER, st);
+            StageTimer _t(STAGE_HOUGH, st);
             k_ols_sums<<<(unsigned)F, 256, 0, st>>>(tx, ty, d_dst, d_sums);
         }
         if (rc == LMS_OK) rc = lms_batch_plan_create((const int64_t *)dst.data(), (int64_t)F, nullptr, 0, 16, &plan);

@@ -1,13 +1,13 @@
 // noalloc.cu -- lms_fit_noalloc: the plain per-slope fit without any device
 // allocation.
 //
-// Some callers cannot let a library allocate GPU memory: code that runs
-// while a CUDA stream is being captured into a graph (an allocation there
-// breaks the capture), real-time or embedded loops that forbid allocation
-// after start-up, and frameworks that own all device memory through their
-// own pools.  For them this entry point keeps its only scratch buffer -- the
-// per-warp best windows that the final reduction reads -- in a fixed array
-// compiled into the library.  The array lives on every GPU that loads the
+// Some callers cannot let a library allocate GPU memory: real-time or
+// embedded loops that forbid allocation after start-up (cudaMalloc and
+// cudaFree can block and synchronise the device), and frameworks that own
+// all device memory through their own pools and budgets.  For them this
+// entry point keeps its only scratch buffer -- the per-warp best windows
+// that the final reduction reads -- in a fixed array compiled into the
+// library.  The array lives on every GPU that loads the
 // library until the process exits.
 //
 // Limits: int16 points, 2 <= n <= 1024 (the plain kernel's register sort),
@@ -40,11 +40,13 @@ static __device__ __align__(256) Cand g_noalloc_scratch[kNoallocMaxWarps];
 std::mutex g_na_mu;
 Cand *g_na_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array for the current device (set up once).
-int noalloc_scratch(Cand **out)
+// Device address of the scratch array for the current device (set up once),
+// and that device's index.
+int noalloc_scratch(Cand **out, int *device)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LMS_ERR_CUDA;
+    *device = dev;
     std::lock_guard<std::mutex> lock(g_na_mu);
     if (!g_na_ptr[dev]) {
         void *p = nullptr;
@@ -73,11 +75,13 @@ extern "C" int lms_fit_noalloc(const void *x, const void *y, int64_t n, int64_t 
     if (h < 1 || h > n) return LMS_ERR_ARG;
     if (n > LMS_NOALLOC_MAX_N) return LMS_ERR_TOO_LARGE;
     Cand *scratch = nullptr;
-    const int rc = noalloc_scratch(&scratch);
-    if (rc) return rc;
     int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int rc = noalloc_scratch(&scratch, &dev);
+    if (rc) return rc;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LMS_ERR_CUDA;
+    }
     // warps: up to 32 per SM, at least ~4 slopes each, a multiple of 8, and
     // never more than the array holds
     const long long npairs = n * (n - 1) / 2;

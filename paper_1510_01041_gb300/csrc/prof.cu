@@ -42,7 +42,8 @@ cudaEvent_t take_event()
 
 const char *const kNames[STAGE_COUNT] = {
     "pack", "sample", "sample_sort", "splitters", "count", "bucket_prefix", "bucket_scan", "scatter",
-    "segsort", "segsort_big", "plan", "sweep_init", "sweep", "argmin", "plain", "other"};
+    "segsort", "segsort_big", "plan", "sweep_init", "sweep", "argmin", "plain", "other", "node_bounds", "seeds",
+    "setnet", "hough"};
 
 }  // namespace
 

@@ -191,13 +191,13 @@ void setnet_forward(const __nv_bfloat16 *wb, float *state, unsigned long long *p
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int slices = (2 * (sms > 0 ? sms : 1) + B - 1) / B;
     slices = slices < 1 ? 1 : (slices > 64 ? 64 : slices);
-    { StageTimer _t(STAGE_OTHER, st); k_setnet_frame<<<B, 256, 0, st>>>(x, y, off, state, pool); }
+    { StageTimer _t(STAGE_SETNET, st); k_setnet_frame<<<B, 256, 0, st>>>(x, y, off, state, pool); }
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_SETNET, st);
         k_setnet_points<<<dim3(B, slices), 256, 0, st>>>(wb, x, y, off, state, pool);
     }
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_SETNET, st);
         k_setnet_head<<<B, 64, 0, st>>>(wb, B, targets, bweight, pred, state, pool, dout);
     }
 }
@@ -315,6 +315,8 @@ struct lms_setnet {
     float *state, *dout, *pred, *loss;    // device, per set
     unsigned long long *pool;             // device, per set x H2
     long long *off1;                      // device, {0, n} for single fits
+    short *hx, *hy;                       // device staging of host-buffer fits (65536 points each)
+    lms_result *hres;                     // device result of host-buffer fits
 };
 
 namespace {
@@ -398,6 +400,7 @@ void lms_setnet_destroy(lms_setnet *net)
     cudaFree(net->w); cudaFree(net->wb); cudaFree(net->m); cudaFree(net->v); cudaFree(net->g);
     cudaFree(net->state); cudaFree(net->dout); cudaFree(net->pred); cudaFree(net->pool);
     cudaFree(net->loss); cudaFree(net->off1);
+    cudaFree(net->hx); cudaFree(net->hy); cudaFree(net->hres);
     delete net;
 }
 
@@ -437,12 +440,12 @@ int lms_setnet_backward(lms_setnet *net, const int16_t *x, const int16_t *y, con
     setnet_forward(net->wb, net->state, net->pool, net->dout, (const short *)x, (const short *)y,
                    (const long long *)offsets, (int)B, targets, intercept_weight, net->pred, st);
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_SETNET, st);
         k_setnet_bwd<<<(int)B, 64, 0, st>>>(net->wb, (const short *)x, (const short *)y, (const long long *)offsets,
                                             (int)B, net->state, net->pool, net->dout, net->g);
     }
     {
-        StageTimer _t(STAGE_OTHER, st);
+        StageTimer _t(STAGE_SETNET, st);
         k_sum_loss<<<1, 32, 0, st>>>(net->state, (int)B, net->loss);
     }
     if (grads) cudaMemcpyAsync(grads, net->g, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, st);
@@ -460,7 +463,7 @@ int lms_setnet_train_step(lms_setnet *net, const int16_t *x, const int16_t *y, c
     net->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)net->step), c2 = 1.f - powf(b2, (float)net->step);
-    StageTimer _t(STAGE_OTHER, st);
+    StageTimer _t(STAGE_SETNET, st);
     k_adam<<<(NPARAM + 255) / 256, 256, 0, st>>>(net->w, net->wb, net->m, net->v, net->g, NPARAM, lr, b1, b2,
                                                 1e-8f, c1, c2);
     return cudaGetLastError() == cudaSuccess ? LMS_OK : LMS_ERR_CUDA;
@@ -519,6 +522,33 @@ int lms_fit_learned(lms_setnet *net, const void *x, const void *y, int64_t n, in
     if (rc) return rc;
     // pred[2] is the predicted slope in the original frame
     return lms_fit_bnb(x, y, n, h, net->pred + 2, opt, out, stats, stream);
+}
+
+int lms_fit_learned_host(lms_setnet *net, const void *x, const void *y, int64_t n, int64_t h,
+                         const lms_options *opt, lms_result *out, lms_bnb_stats *stats, lms_stream_t stream)
+{
+    if (!net || !x || !y || !out || n < 2 || n > 65536) return LMS_ERR_ARG;
+    if (!net->hx) {
+        if (cudaMalloc(&net->hx, sizeof(short) * 65536) != cudaSuccess ||
+            cudaMalloc(&net->hy, sizeof(short) * 65536) != cudaSuccess ||
+            cudaMalloc(&net->hres, sizeof(lms_result)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(net->hx); cudaFree(net->hy); cudaFree(net->hres);
+            net->hx = net->hy = nullptr;
+            net->hres = nullptr;
+            return LMS_ERR_CUDA;
+        }
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(net->hx, x, sizeof(short) * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(net->hy, y, sizeof(short) * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return LMS_ERR_CUDA;
+    const int rc = lms_fit_learned(net, net->hx, net->hy, n, h, opt, net->hres, stats, stream);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(out, net->hres, sizeof(lms_result), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return LMS_ERR_CUDA;
+    return LMS_OK;
 }
 
 }  // extern "C"

@@ -15,6 +15,7 @@ from . import build as _build
 
 LMS_OK, LMS_ERR_ARG, LMS_ERR_RANGE, LMS_ERR_VERTICAL = 0, 1, 2, 3
 LMS_ERR_TIMEOUT, LMS_ERR_CUDA, LMS_ERR_WORKSPACE, LMS_ERR_UNSUPPORTED, LMS_ERR_INTERNAL = 4, 5, 6, 7, 8
+LMS_ERR_TOO_LARGE = 9
 LMS_I16, LMS_F32 = 0, 1
 ALGOS = {"auto": 0, "plain": 1, "sweep": 2, "bnb": 3, "paper": 4}
 
@@ -222,6 +223,19 @@ def launch_count() -> int:
     return int(_prof_sigs().lms_launch_count())
 
 
+def measure_int_peak(kind: int = 0, iters: int = 20000, stream=None) -> float:
+    """lms_measure_int_peak: int32 instructions per second of this GPU
+    (kind 0: add/xor, kind 1: multiply-add)."""
+    L = lib()
+    L.lms_measure_int_peak.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    L.lms_measure_int_peak.restype = ctypes.c_int
+    v = ctypes.c_double(0.0)
+    rc = L.lms_measure_int_peak(int(kind), int(iters), ctypes.byref(v), _stream_handle(stream))
+    if rc != LMS_OK:
+        raise LmsError(rc, "lms_measure_int_peak")
+    return float(v.value)
+
+
 # ------------------------------------------------------------------ branch and bound
 class BnbStats(ctypes.Structure):
     _fields_ = [("events_total", ctypes.c_int64), ("events_swept", ctypes.c_int64),
@@ -285,6 +299,9 @@ def _setnet_sigs():
         L.lms_fit_learned.argtypes = [vp, vp, vp, i64, i64, ctypes.POINTER(Options), vp,
                                       ctypes.POINTER(BnbStats), vp]
         L.lms_fit_learned.restype = ctypes.c_int
+        L.lms_fit_learned_host.argtypes = [vp, vp, vp, i64, i64, ctypes.POINTER(Options), vp,
+                                           ctypes.POINTER(BnbStats), vp]
+        L.lms_fit_learned_host.restype = ctypes.c_int
         L._setnet_ready = True
     return L
 
@@ -385,6 +402,24 @@ class SetNet:
                                     ctypes.byref(st), _stream_handle(stream))
         if rc != LMS_OK:
             raise LmsError(rc, "lms_fit_learned")
+        return out, {f: getattr(st, f) for f, _ in BnbStats._fields_}
+
+    def fit_host(self, x, y, h: int = 0, out=None, stream=None):
+        """lms_fit_learned_host on host int16 arrays (numpy or CPU tensors;
+        pinned tensors copy asynchronously).  ``out``: optional host uint8
+        buffer of 88 bytes that receives the lms_result.  Returns (out, stats)."""
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        n = x.numel() if hasattr(x, "numel") else x.size
+        if out is None:
+            out = np.zeros(RESULT_DTYPE.itemsize, dtype=np.uint8)
+        st = BnbStats()
+        opt = options("bnb")
+        rc = self.L.lms_fit_learned_host(self.h, ctypes.c_void_p(ptr(x)), ctypes.c_void_p(ptr(y)), int(n), int(h),
+                                         ctypes.byref(opt), ctypes.c_void_p(ptr(out)), ctypes.byref(st),
+                                         _stream_handle(stream))
+        if rc != LMS_OK:
+            raise LmsError(rc, "lms_fit_learned_host")
         return out, {f: getattr(st, f) for f, _ in BnbStats._fields_}
 
 

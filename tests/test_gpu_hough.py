@@ -23,12 +23,14 @@ def L():
     return lms
 
 
-def run(L, imgs, n_theta, n_rho, top_k, band, nms, max_points=0, seed=0):
+def run(L, imgs, n_theta, n_rho, top_k, band, nms, max_points=0, seed=0, own_table=False):
+    """own_table: the library computes its (cos, sin) table itself (the path
+    every caller without a table takes); the oracle always uses its own."""
     cs = ohough.tables(n_theta)
     acc = torch.zeros((imgs.shape[0], n_theta, n_rho), dtype=torch.int32, device="cuda")
     lines = L.hough_refine(torch.from_numpy(imgs).cuda(), n_theta, n_rho, top_k, band, nms, nms,
-                           cos_sin=torch.from_numpy(cs).cuda(), acc_out=acc, max_points=max_points,
-                           sample_seed=seed)
+                           cos_sin=None if own_table else torch.from_numpy(cs).cuda(), acc_out=acc,
+                           max_points=max_points, sample_seed=seed)
     return cs, acc.cpu().numpy(), lines
 
 
@@ -79,6 +81,17 @@ def test_hough_small_images(L, orc):
     n_theta, n_rho, top_k, band, nms = 180, 2 * int(np.ceil(np.hypot(192, 256))) + 2, 8, 4.0, 5
     cs, acc, lines = run(L, imgs, n_theta, n_rho, top_k, band, nms)
     compare(orc, L, imgs, cs, acc, lines, n_theta, n_rho, top_k, band, nms)
+
+
+def test_hough_library_table(L, orc):
+    """No table passed: the library's own host-computed (cos, sin) table gives
+    the oracle's votes, peaks, bands and fits, at the full 1024-angle
+    resolution and at an odd one."""
+    imgs = datagen.edge_images(2, 22, height=384, width=512, segments=5, len_min=80, len_max=300, salt=0.01)
+    n_rho = 2 * int(np.ceil(np.hypot(192, 256))) + 2
+    for n_theta in (1024, 331):
+        cs, acc, lines = run(L, imgs, n_theta, n_rho, 8, 4.0, 5, own_table=True)
+        compare(orc, L, imgs, cs, acc, lines, n_theta, n_rho, 8, 4.0, 5)
 
 
 def test_hough_full_size_image(L, orc):

@@ -1,17 +1,24 @@
-"""Exact fits at n = 65536 (int16, 45% outliers: the branch-and-bound
-configuration of the largest workload).  At this size the sweep keeps each
-warp's position array in global memory (order and positions no longer fit
-in shared memory together) and every bucket is sorted by chunk sorts plus
-merges.  The full oracle sweep would take minutes on the host, so the check
-is by properties that hold at any size:
+"""Exact fits at the largest workload sizes against the oracle's stored
+results (tests/golden/lms_large.json, written by make_large.py from the O2
+exact sweep; the points are regenerated from their seeds):
 
-* the branch-and-bound and the plain sweep (every candidate slope) agree
-  bit for bit;
-* certificate: the oracle's narrowest window at the reported slope is the
-  reported window (width, centre) exactly;
-* no other candidate slope the oracle evaluates (pairs through the reported
-  window's region and random pairs) has a narrower window.
+* n = 32768 int16, 40% outliers (single-instance scaling workload): the
+  plain kinetic sweep and the branch-and-bound, bit for bit;
+* n = 65536 int16, random slope, 45% outliers (learned-proposal workload):
+  the plain sweep, the seedless branch-and-bound and the learned-seeded
+  branch-and-bound, bit for bit;
+* n = 32768 float32 (Gaussian variant of the scaling workload): med_sq
+  within 1e-6 relative of the exact value.
+
+At n = 65536 each sweeping warp keeps its position array in global memory
+and every bucket is sorted by chunk sorts plus merges.  A further check by
+properties that hold at any size: the oracle's narrowest window at the
+reported slope is the reported window, and no slope of a pair among the
+points nearest the reported line (where competitors live) does better.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -20,6 +27,9 @@ from paper_1510_01041_gb300 import datagen
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "lms_large.json")
+KEYS = ("status", "w_num", "w_den", "s_num", "s_den", "t_num", "t_den", "i", "j", "theta1", "theta2", "med_sq")
 
 
 @pytest.fixture(scope="module")
@@ -31,37 +41,99 @@ def L():
     return lms
 
 
-def _fit(L, x, y, algorithm):
-    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
-    yt = torch.from_numpy(np.ascontiguousarray(y)).cuda()
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        return json.load(f)["cases"]
+
+
+def points(case):
+    gen, n, seed, frac = case["generator"], case["n"], case["seed"], case["outlier_frac"]
+    if gen == "line_with_outliers":
+        return datagen.line_with_outliers(n, seed, frac)
+    if gen == "sloped":
+        x, y, _ = datagen.sloped(n, seed, frac)
+        return x, y
+    return datagen.gaussian_f32(n, seed, frac)
+
+
+def _dev(x, y):
+    return (torch.from_numpy(np.ascontiguousarray(x)).cuda(), torch.from_numpy(np.ascontiguousarray(y)).cuda())
+
+
+def _fit(L, xt, yt, algorithm):
     out = L.fit(xt, yt, 0, algorithm)
     torch.cuda.synchronize()
     return L.decode(out)[0]
 
 
-KEYS = ("status", "w_num", "w_den", "s_num", "s_den", "t_num", "t_den", "i", "j", "theta1", "theta2", "med_sq")
+def _exact(case):
+    return tuple(case[k] for k in KEYS)
 
 
-def test_n65536_branch_and_bound_equals_sweep_with_certificate(L, orc):
-    n = 65536
-    x, y = datagen.line_with_outliers(n, 11, 0.45)
-    rb = _fit(L, x, y, "bnb")
-    rs = _fit(L, x, y, "sweep")
+def test_n32768_int16_sweep_and_bnb_equal_oracle(L, golden):
+    case = golden["line_n32768_s1"]
+    xt, yt = _dev(*points(case))
+    rs = _fit(L, xt, yt, "sweep")
+    assert tuple(rs[k] for k in KEYS) == _exact(case)
+    out, st = L.fit_bnb(xt, yt, 0, None)
+    torch.cuda.synchronize()
+    rb = L.decode(out)[0]
+    assert tuple(rb[k] for k in KEYS) == _exact(case)
+    assert st["events_swept"] < st["events_total"]
+
+
+def test_n65536_sweep_bnb_learned_equal_oracle(L, golden):
+    case = golden["sloped_n65536_s65"]
+    x, y = points(case)
+    xt, yt = _dev(x, y)
+    rs = _fit(L, xt, yt, "sweep")
+    assert tuple(rs[k] for k in KEYS) == _exact(case)
+    rb = _fit(L, xt, yt, "bnb")
+    assert tuple(rb[k] for k in KEYS) == _exact(case)
+    if os.path.exists(L.WEIGHTS):
+        out, st = L.pretrained().fit(xt, yt)
+        torch.cuda.synchronize()
+        rl = L.decode(out)[0]
+        assert tuple(rl[k] for k in KEYS) == _exact(case)
+        assert st["events_swept"] < st["events_total"] // 10
+
+
+def test_n32768_float32_within_tolerance(L, golden):
+    case = golden["gauss_f32_n32768_s1"]
+    x, y = points(case)
+    xt, yt = _dev(x, y)
+    r = _fit(L, xt, yt, "auto")
+    assert r["status"] == case["status"] == L.LMS_OK
+    assert abs(r["med_sq"] - case["med_sq"]) <= 1e-6 * case["med_sq"], (r["med_sq"], case["med_sq"])
+    # the reported line attains the reported value (h-th smallest squared residual in float64)
+    h = x.size // 2 + 1
+    res = np.abs(y.astype(np.float64) - r["theta1"] * x.astype(np.float64) - r["theta2"])
+    assert abs(float(np.sort(res)[h - 1]) ** 2 - r["med_sq"]) <= 1e-6 * r["med_sq"]
+
+
+def test_n65536_certificate_and_near_pairs(L, orc, golden):
+    case = golden["sloped_n65536_s65"]
+    x, y = points(case)
+    n = x.size
+    xt, yt = _dev(x, y)
+    rb = _fit(L, xt, yt, "bnb")
     assert rb["status"] == L.LMS_OK
-    assert tuple(rb[k] for k in KEYS) == tuple(rs[k] for k in KEYS)
     # the reported slope's narrowest window, exactly
     c = orc.eval_slope_i16(x, y, int(rb["s_num"]), int(rb["s_den"]), 0)
     assert (c.w_num, c.w_den) == (rb["w_num"], rb["w_den"])
     assert (c.t_num, c.t_den) == (rb["t_num"], rb["t_den"])
-    # no evaluated candidate slope does better (width compared as exact rationals)
-    rng = np.random.default_rng(5)
+    # pairs among the points nearest the reported line: the residual of
+    # point k times t_den = 2 s_den is 2 s_den y - 2 s_num x - t_num (exact)
     xi, yi = x.astype(np.int64), y.astype(np.int64)
-    pairs = [(int(rb["i"]), int(rb["j"]))]
-    pairs += [tuple(int(v) for v in rng.choice(n, 2, replace=False)) for _ in range(24)]
-    # pairs among points close to the reported line (where competitors live)
-    resid = np.abs(yi * int(rb["s_den"]) - xi * int(rb["s_num"]) - 0)
-    near = np.argsort(resid - np.median(resid))[: 2000]
-    pairs += [tuple(int(v) for v in rng.choice(near, 2, replace=False)) for _ in range(24)]
+    sn, sd, tn = int(rb["s_num"]), int(rb["s_den"]), int(rb["t_num"])
+    resid = np.abs(2 * sd * yi - 2 * sn * xi - tn)
+    near = np.argsort(resid, kind="stable")[:2000]
+    # at least h points lie in the slab: |residual| <= w / 2 = w_num / (2 s_den)
+    assert np.all(resid[near] <= int(rb["w_num"]))
+    rng = np.random.default_rng(5)
+    pairs = [tuple(int(v) for v in rng.choice(near, 2, replace=False)) for _ in range(40)]
+    pairs += [tuple(int(v) for v in rng.choice(n, 2, replace=False)) for _ in range(8)]
     W, D = int(rb["w_num"]), int(rb["w_den"])
     for i, j in pairs:
         dx, dy = int(xi[j] - xi[i]), int(yi[j] - yi[i])

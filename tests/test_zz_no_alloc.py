@@ -1,9 +1,12 @@
 """lms_fit_noalloc, the entry point for callers that cannot let the library
-allocate device memory (graph capture, allocation-free real-time loops,
-framework-owned memory pools), gives the same result as lms_fit's plain
-path.  Called directly through the C ABI, twice in a row on different
-inputs, so the second call reuses the shared fixed scratch array left by
-the first.  Kept in a file that pytest collects last."""
+allocate device memory (real-time loops that forbid allocation once
+running, frameworks that own every device byte through their own pools),
+gives the same result as lms_fit's plain path and as the oracle.  Called
+directly through the C ABI, twice in a row on different inputs, so the
+second call reuses the shared fixed scratch array left by the first; the
+capacity edge (n = 1024) and a non-default order statistic are compared with
+the oracle, and n = 1025 is refused.  Kept in a file that pytest collects
+last."""
 import ctypes
 
 import numpy as np
@@ -39,6 +42,10 @@ def _noalloc(L, xt, yt, h=0):
     return L.decode(out)[0]
 
 
+def _same(got, ref):
+    return {k: v for k, v in got.items() if k != "algorithm"} == {k: v for k, v in ref.items() if k != "algorithm"}
+
+
 def test_noalloc_matches_lms_fit_twice(L):
     for seed, n in ((31, 512), (32, 777)):
         x, y = datagen.line_with_outliers(n, seed)
@@ -47,14 +54,29 @@ def test_noalloc_matches_lms_fit_twice(L):
         got = _noalloc(L, xt, yt)
         ref = L.decode(L.fit(xt, yt, 0, "plain"))[0]
         torch.cuda.synchronize()
-        assert {k: v for k, v in got.items() if k != "algorithm"} == \
-               {k: v for k, v in ref.items() if k != "algorithm"}
+        assert _same(got, ref)
         assert got["status"] == L.LMS_OK
 
 
-def test_noalloc_rejects_oversize(L):
-    x = torch.zeros(2000, dtype=torch.int16, device="cuda")
-    out = torch.zeros(L.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
-    rc = L.lib().lms_fit_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 2000, 0,
-                                 ctypes.c_void_p(out.data_ptr()), None)
-    assert rc == 9 and "capacity" in L.status_str(rc)
+@pytest.mark.parametrize("n,h,seed", [(1024, 0, 33), (700, 300, 34), (1024, 1000, 35)])
+def test_noalloc_capacity_edge_and_h_vs_oracle(L, orc, n, h, seed):
+    x, y = datagen.line_with_outliers(n, seed)
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.from_numpy(y).cuda()
+    for _ in range(2):
+        got = _noalloc(L, xt, yt, h)
+        o = orc.lms_i16(x, y, h, "sweep")
+        assert L.exact_fields(got) == o.exact()
+        assert (got["theta1"], got["theta2"], got["med_sq"]) == (o.theta1, o.theta2, o.med_sq)
+        ref = L.decode(L.fit(xt, yt, h, "plain"))[0]
+        torch.cuda.synchronize()
+        assert _same(got, ref)
+
+
+def test_noalloc_rejects_above_capacity(L):
+    for n in (1025, 2000):
+        x = torch.zeros(n, dtype=torch.int16, device="cuda")
+        out = torch.zeros(L.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        rc = L.lib().lms_fit_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), n, 0,
+                                     ctypes.c_void_p(out.data_ptr()), None)
+        assert rc == L.LMS_ERR_TOO_LARGE and "capacity" in L.status_str(rc)
