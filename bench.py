@@ -682,10 +682,14 @@ def main():
         "candidate_slopes_per_sec": rate["learned"] * slopes,
         "learned": arm_line("learned", {"events_swept_mean": mean("learned", "events_swept"),
                                         "nodes_evaluated_mean": mean("learned", "nodes_evaluated"),
+                                        "levels_mean": mean("learned", "levels"),
+                                        "buckets_swept_mean": mean("learned", "buckets_swept"),
                                         "upper_bound_mean": mean("learned", "upper_bound"),
                                         "algorithm": "set-network seed + branch-and-bound"}),
         "quantile_bnb": arm_line("quantile", {"events_swept_mean": mean("quantile", "events_swept"),
                                               "nodes_evaluated_mean": mean("quantile", "nodes_evaluated"),
+                                              "levels_mean": mean("quantile", "levels"),
+                                              "buckets_swept_mean": mean("quantile", "buckets_swept"),
                                               "upper_bound_mean": mean("quantile", "upper_bound"),
                                               "algorithm": "branch-and-bound seeded at sample quantiles "
                                                            "(the method without the network)"}),

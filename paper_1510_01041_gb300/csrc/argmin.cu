@@ -63,7 +63,10 @@ __global__ void __launch_bounds__(1024) k_argmin(const Cand *__restrict__ cands,
     r.i = best.i;
     r.j = best.j;
     r.status = (best.i < 0) ? LMS_ERR_VERTICAL : LMS_OK;
-    if (err && *err) r.status = LMS_ERR_INTERNAL;
+    // err points at the sweep's error word; err[4] / err[5] are the events
+    // its ranges covered and the events there were: every event must be
+    // swept exactly once
+    if (err && (*err || err[4] != err[5])) r.status = LMS_ERR_INTERNAL;
     *out = r;
 }
 

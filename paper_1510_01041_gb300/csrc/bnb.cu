@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -131,7 +132,8 @@ __global__ void __launch_bounds__(1024) k_score_dyadic(const int *__restrict__ x
 // Lower bounds of slope intervals [K_lo, K_hi] (keys) and the prune flags.
 __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, int n, int h,
                                                   const int *__restrict__ xcp,
-                                                  const long long *__restrict__ node_keys, int nnodes,
+                                                  const long long *__restrict__ node_keys,
+                                                  const int *__restrict__ nnodes_dev,
                                                   const long long *__restrict__ ub,
                                                   unsigned char *__restrict__ prune,
                                                   long long *__restrict__ lb_out,
@@ -141,6 +143,7 @@ __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, in
     int P = 1;
     while (P < n) P <<= 1;
     const bool in_smem = n <= SORT_SMEM_N;
+    const int nnodes = *nnodes_dev;
     for (int q = blockIdx.x; q < nnodes; q += gridDim.x) {
         const long long Klo = node_keys[2 * q], Khi = node_keys[2 * q + 1];
         if (Klo <= -K_GUARD || Khi >= K_GUARD || Klo >= K_GUARD || Khi <= -K_GUARD) {
@@ -185,10 +188,7 @@ __global__ void k_min_ub(const long long *__restrict__ w, int nk, long long *__r
     if (threadIdx.x == 0) *ub = m;
 }
 
-#ifndef LMS_BNB_MIN_RANGE
-#define LMS_BNB_MIN_RANGE 512
-#endif
-constexpr unsigned long long BNB_MIN_RANGE = LMS_BNB_MIN_RANGE;   // events per swept range, at least
+constexpr unsigned long long BNB_MIN_RANGE = 64;   // events per swept range, at least
 constexpr double PRED_WINDOW = 0.35;   // radians around a predicted slope angle
 
 // Seed slopes.  With a predicted slope: half of them evenly spaced quantiles
@@ -262,36 +262,507 @@ __global__ void k_pick_seeds(const long long *__restrict__ sorted, int S, const 
     }
 }
 
+// Zoom round of the upper bound: around the best seed of the previous round
+// (smallest width, ties to the smaller index), KS sample ranks evenly
+// spaced over [r* - span, r* + span], r* the rank of that seed's key in the
+// sorted sample and span the previous round's spacing of sample ranks
+// (round 2: m / KS, m the valid samples; round 3: 2 span_2 / KS).  The
+// upper bound only needs some real slope with a narrow window; narrowing the
+// search where the previous round found the narrowest windows brings it
+// close to the optimum, and the tighter the bound the fewer slope intervals
+// survive.  A round whose previous round found nothing repeats its keys.
+__global__ void k_zoom_seeds(const long long *__restrict__ sorted, int S, const long long *__restrict__ prev_keys,
+                             const long long *__restrict__ prev_w, int KS, int round, long long *__restrict__ out)
+{
+    __shared__ int s_lo, s_hi, s_ok;
+    if (threadIdx.x == 0) {
+        int m0 = 0, m1 = S;
+        while (m0 < m1) { const int md = (m0 + m1) >> 1; if (sorted[md] < I64_MAX) m0 = md + 1; else m1 = md; }
+        const int m = m0;
+        int q = -1;
+        long long bw = I64_MAX;
+        for (int k = 0; k < KS; ++k)
+            if (prev_w[k] < bw) { bw = prev_w[k]; q = k; }
+        s_ok = (q >= 0 && m > 0) ? 1 : 0;
+        if (s_ok) {
+            const long long key = prev_keys[q];
+            int a = 0, b = m;
+            while (a < b) { const int md = (a + b) >> 1; if (sorted[md] < key) a = md + 1; else b = md; }
+            const int r = min(a, m - 1);
+            int span = max(1, m / KS);
+            for (int k = 2; k < round; ++k) span = max(1, (2 * span + 1) / KS);
+            s_lo = max(0, r - span);
+            s_hi = min(m, r + span + 1);
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < KS; q += blockDim.x) {
+        if (!s_ok) {
+            out[q] = prev_keys[q];
+            continue;
+        }
+        const long long len = s_hi - s_lo;
+        out[q] = sorted[s_lo + (int)(((2LL * q + 1) * len) / (2LL * KS))];
+    }
+}
+
 constexpr size_t a256_const(size_t v) { return (v + 255) & ~(size_t)255; }
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Page-locked host staging for the device-to-host reads of a fit, so that
-// they are queued asynchronously and waited for once.  One buffer per host
-// thread, allocated on first use and kept for the life of the process (a fit
-// waits for its reads before it returns, so nothing is in flight between
-// fits).  Layout: meta (8 ints), upper bound, bucket counts, boundaries,
-// kept-bucket starts, prune flags.
-constexpr size_t HS_META = 0, HS_UB = 32, HS_CNT = 64;
-constexpr size_t HS_BND = HS_CNT + (size_t)BND_MAX * 4;
-constexpr size_t HS_KBASE = HS_BND + (size_t)BND_MAX * 8;
-constexpr size_t HS_PRUNE = HS_KBASE + a256_const((size_t)(BND_MAX + 1) * 4);
-constexpr size_t HS_BYTES = HS_PRUNE + (size_t)BND_MAX;
+}  // namespace
 
+// Upper-bound slopes per round (one CTA each, one wave) and rounds: a first
+// round of seeds, then zoom rounds around the best slope found so far.
+constexpr int BNB_SEEDS_MAX = 256;
+constexpr int BNB_ROUNDS = 3;
+int bnb_seeds(int sms) { return std::max(64, std::min(BNB_SEEDS_MAX, sms)); }
+constexpr int BNB_FIRST_NODES = 128;
+// Levels of the interval tree.  The split after the second-to-last level
+// makes every child a single bucket, so the last level leaves no node open.
+constexpr int BNB_LEVELS = 4;
+constexpr int TREE_THREADS = 1024;
+
+// Device-side state of one branch-and-bound fit (read back only for the
+// statistics).
+struct TreeState {
+    int count[2];            // nodes of the current / next level (ping-pong by level parity)
+    int evaluated, pruned;   // nodes bounded, nodes dropped
+    int levels;              // levels that held nodes
+    int kept;                // buckets kept for the exact sweep
+    unsigned swept;          // events in the kept buckets
+    int covers;              // slope covers handed to the restricted pair pass
+    int nruns;               // runs of consecutive kept buckets
+};
+
+// Page-locked host buffer for the statistics of a fit, one per host thread
+// (allocated on first use, kept until the process exits).
 unsigned char *host_stage()
 {
     thread_local unsigned char *buf = nullptr;
     if (!buf) {
         void *q = nullptr;
-        if (cudaHostAlloc(&q, HS_BYTES, cudaHostAllocPortable) != cudaSuccess) return nullptr;
+        if (cudaHostAlloc(&q, 256, cudaHostAllocPortable) != cudaSuccess) return nullptr;
         buf = static_cast<unsigned char *>(q);
     }
     return buf;
 }
 
-}  // namespace
+// ------------------------------------------------------------ block scans
+// Inclusive scan of one value per thread over the CTA (sum or max).
+template <bool MAX>
+__device__ __forceinline__ long long block_scan(long long v, long long *s_warp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const long long o = __shfl_up_sync(FULL, v, d);
+        if (lane >= d) v = MAX ? max(v, o) : v + o;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        long long t = lane < nw ? s_warp[lane] : (MAX ? LLONG_MIN : 0);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long o = __shfl_up_sync(FULL, t, d);
+            if (lane >= d) t = MAX ? max(t, o) : t + o;
+        }
+        s_warp[lane] = t;
+    }
+    __syncthreads();
+    if (warp > 0) {
+        const long long o = s_warp[warp - 1];
+        v = MAX ? max(v, o) : v + o;
+    }
+    __syncthreads();
+    return v;
+}
 
-constexpr int BNB_SEEDS = 64;
-constexpr int BNB_FIRST_NODES = 128;
+// First index in [lo, hi) with a[index] >= t (hi if none).
+__device__ __forceinline__ int lower_bound_u(const unsigned *a, int lo, int hi, unsigned long long t)
+{
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if ((unsigned long long)a[m] < t) lo = m + 1; else hi = m;
+    }
+    return lo;
+}
+// First index in [lo, hi) with a[index] > t (hi if none).
+__device__ __forceinline__ int upper_bound_u(const unsigned *a, int lo, int hi, unsigned long long t)
+{
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if ((unsigned long long)a[m] <= t) lo = m + 1; else hi = m;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void node_keys_of(const long long *bnd, int NB, int b0, int b1, long long *keys)
+{
+    keys[0] = b0 == 0 ? -I64_MAX : bnd[b0 - 1];
+    keys[1] = b1 >= NB ? I64_MAX : bnd[b1 - 1];
+}
+
+// Exclusive prefix of the sampled pairs per bucket (sbase[NB] = all of them),
+// then the first level of the tree: m0 intervals of about equal sampled
+// pairs, each at least one bucket.  Interval k ends at f_k =
+// min(NB, max(b_k, f_{k-1} + 1)), b_k the first bucket boundary reaching
+// k/m0 of the sampled pairs (b_m0 = NB), f_0 = 0; written as a prefix
+// maximum, f_k = min(NB, k + max_{j<=k} (b_j - j)).
+__global__ void __launch_bounds__(TREE_THREADS) k_tree_first(const unsigned *__restrict__ counts,
+                                                             const int *__restrict__ meta,
+                                                             const long long *__restrict__ bnd, int sms,
+                                                             unsigned *__restrict__ sbase, int2 *__restrict__ nodes,
+                                                             long long *__restrict__ keys,
+                                                             unsigned char *__restrict__ keep,
+                                                             TreeState *__restrict__ ts)
+{
+    __shared__ long long s_warp[32];
+    __shared__ unsigned s_tot;
+    const int NB = meta[0] + 1;
+    constexpr int PER = BND_MAX / TREE_THREADS;
+    // exclusive scan of the counts, PER consecutive buckets per thread
+    const int b_beg = threadIdx.x * PER;
+    unsigned loc[PER];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int b = b_beg + r;
+        loc[r] = b < NB ? counts[b] : 0u;
+        sum += loc[r];
+    }
+    const long long incl = block_scan<false>((long long)sum, s_warp);
+    unsigned run = (unsigned)(incl - (long long)sum);
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int b = b_beg + r;
+        if (b < NB) sbase[b] = run;
+        run += loc[r];
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        sbase[NB] = (unsigned)incl;
+        s_tot = (unsigned)incl;
+    }
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) keep[b] = 0;
+    __syncthreads();
+    const unsigned long long E = s_tot;
+    const int m0 = min(NB, max(BNB_FIRST_NODES, sms));
+    // thread k - 1 computes b_k (k = 1 .. m0; m0 is at most the SM count or 128, below blockDim)
+    const int k = threadIdx.x + 1;
+    long long v = LLONG_MIN;
+    if (k <= m0) {
+        int b = lower_bound_u(sbase, 0, NB + 1, E * (unsigned long long)k / (unsigned long long)m0);
+        if (k == m0) b = NB;
+        v = (long long)b - k;
+    }
+    // f_k with f_0 = 0 included in the maximum (the j = 0 term is 0)
+    long long mx = block_scan<true>(v, s_warp);
+    mx = max(mx, 0LL);
+    const int f_k = (int)min((long long)NB, mx + k);
+    const int f_km1 = __shfl_up_sync(FULL, f_k, 1);
+    __shared__ int s_last[32];
+    if ((threadIdx.x & 31) == 31) s_last[threadIdx.x >> 5] = f_k;
+    __syncthreads();
+    const int prev = k == 1 ? 0 : ((threadIdx.x & 31) == 0 ? s_last[(threadIdx.x >> 5) - 1] : f_km1);
+    if (k <= m0 && prev < NB) {
+        nodes[k - 1] = make_int2(prev, f_k);
+        node_keys_of(bnd, NB, prev, f_k, keys + 2 * (k - 1));
+    }
+    // nodes: every k with f_{k-1} < NB (f is increasing and f_m0 = NB)
+    const int is_node = (k <= m0 && prev < NB) ? 1 : 0;
+    const long long cnt = block_scan<false>(is_node, s_warp);
+    if (threadIdx.x == blockDim.x - 1) {
+        ts->count[0] = (int)cnt;
+        ts->count[1] = 0;
+        ts->evaluated = ts->pruned = ts->levels = ts->kept = 0;
+        ts->swept = 0;
+        ts->covers = ts->nruns = 0;
+    }
+}
+
+// One tree step after the bounds of level L: surviving single buckets are
+// kept; every other survivor splits into F children of about equal sampled
+// pairs (F about fills the SMs at the next level; at the second-to-last
+// level every child is a single bucket).  Child boundaries follow
+// m'_q = min(max(m_q, m'_{q-1} + 1), b1 - parts + q), m_q the first bucket
+// boundary above q/parts of the node's sampled pairs; with u_q = m'_q - q this
+// is u_q = max(b0, max_{j<=q} min(m_j - j, b1 - parts)), one warp per node.
+__global__ void __launch_bounds__(TREE_THREADS) k_tree_step(int level, int sms, const int *__restrict__ meta,
+                                                            const long long *__restrict__ bnd,
+                                                            const unsigned *__restrict__ sbase,
+                                                            const int2 *__restrict__ cur,
+                                                            const unsigned char *__restrict__ prune,
+                                                            int2 *__restrict__ nxt, long long *__restrict__ nkeys,
+                                                            int *__restrict__ offs,
+                                                            unsigned char *__restrict__ keep,
+                                                            TreeState *__restrict__ ts)
+{
+    __shared__ long long s_warp[32];
+    __shared__ int s_F, s_total;
+    const int NB = meta[0] + 1;
+    const int nn = ts->count[level & 1];
+    const bool last_split = level >= BNB_LEVELS - 2;
+    // survivors that split, dropped nodes, kept single buckets
+    int split = 0, dropped = 0;
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+        const int2 nd = cur[k];
+        if (prune[k]) ++dropped;
+        else if (nd.y - nd.x == 1) keep[nd.x] = 1;
+        else ++split;
+    }
+    const long long tsplit = block_scan<false>(split, s_warp);
+    const long long tdrop = block_scan<false>(dropped, s_warp);
+    if (threadIdx.x == blockDim.x - 1) {
+        const int S = (int)tsplit;
+        s_F = last_split ? 0x7fffffff : (S ? max(2, min(64, sms / S)) : 2);
+        ts->evaluated += nn;
+        ts->pruned += (int)tdrop;
+        ts->levels += nn > 0;
+    }
+    __syncthreads();
+    const int F = s_F;
+    // children per node, exclusive offsets (contiguous node chunks per thread)
+    const int per = (nn + blockDim.x - 1) / blockDim.x;
+    const int k0 = threadIdx.x * per, k1 = min(nn, k0 + per);
+    long long csum = 0;
+    for (int k = k0; k < k1; ++k) {
+        const int2 nd = cur[k];
+        csum += (!prune[k] && nd.y - nd.x > 1) ? min(F, nd.y - nd.x) : 0;
+    }
+    const long long cinc = block_scan<false>(csum, s_warp);
+    int o = (int)(cinc - csum);
+    for (int k = k0; k < k1; ++k) {
+        const int2 nd = cur[k];
+        offs[k] = o;
+        o += (!prune[k] && nd.y - nd.x > 1) ? min(F, nd.y - nd.x) : 0;
+    }
+    if (threadIdx.x == blockDim.x - 1) s_total = (int)cinc;
+    __syncthreads();
+    // children, one warp per splitting node
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < nn; k += nw) {
+        const int2 nd = cur[k];
+        const int len = nd.y - nd.x;
+        if (prune[k] || len <= 1) continue;
+        const int parts = min(F, len);
+        const int C = nd.y - parts;
+        const unsigned long long s0 = sbase[nd.x], s1 = sbase[nd.y];
+        int carry = nd.x;   // u_{q-1} before the chunk (u_0 = b0)
+        int mprev = nd.x;   // m'_{q-1}
+        for (int q0 = 1; q0 <= parts; q0 += 32) {
+            const int q = q0 + lane;
+            int v = INT_MIN;
+            if (q <= parts) {
+                int m = nd.y;
+                if (q < parts) m = upper_bound_u(sbase, nd.x + 1, nd.y, s0 + (s1 - s0) * (unsigned long long)q / parts);
+                v = min(m - q, C);
+            }
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int ov = __shfl_up_sync(FULL, v, d);
+                if (lane >= d) v = max(v, ov);
+            }
+            const int u = max(carry, v);
+            const int mq = u + q;
+            int mp = __shfl_up_sync(FULL, mq, 1);
+            if (lane == 0) mp = mprev;
+            if (q <= parts) {
+                const int at = offs[k] + q - 1;
+                nxt[at] = make_int2(mp, mq);
+                node_keys_of(bnd, NB, mp, mq, nkeys + 2 * at);
+            }
+            carry = __shfl_sync(FULL, u, 31);
+            mprev = __shfl_sync(FULL, mq, 31);
+        }
+    }
+    if (threadIdx.x == 0) ts->count[(level + 1) & 1] = s_total;
+}
+
+// Slope covers of the runs of kept buckets for the restricted pair pass:
+// bucket b holds keys [bnd[b - 1], bnd[b]), a key being floor(slope 2^32);
+// each run's cover is widened by more than the float slope error (2^-21
+// relative) and rounded outward to floats.  At most PRE_MAX covers: the
+// runs are grouped at the PRE_MAX - 1 widest gaps between neighbouring
+// covers (the same grouping as merging the closest neighbours one at a
+// time); covers that touch after rounding are merged.  The unused entries
+// are +inf, which no slope reaches.
+__global__ void __launch_bounds__(TREE_THREADS) k_tree_covers(const int *__restrict__ meta,
+                                                              const long long *__restrict__ bnd,
+                                                              const unsigned char *__restrict__ keep,
+                                                              int *__restrict__ runs, float2 *__restrict__ pre,
+                                                              TreeState *__restrict__ ts)
+{
+    __shared__ long long s_warp[32];
+    __shared__ int s_R, s_sep[PRE_MAX];
+    __shared__ double s_gv[32];
+    __shared__ int s_gi[32];
+    const int NB = meta[0] + 1;
+    constexpr int PER = BND_MAX / TREE_THREADS;
+    const int b_beg = threadIdx.x * PER;
+    int starts = 0, kept = 0;
+    for (int r = 0; r < PER; ++r) {
+        const int b = b_beg + r;
+        if (b < NB && keep[b]) {
+            ++kept;
+            starts += (b == 0 || !keep[b - 1]);
+        }
+    }
+    const long long kinc = block_scan<false>(kept, s_warp);
+    const long long sinc = block_scan<false>(starts, s_warp);
+    int at = (int)(sinc - starts);
+    for (int r = 0; r < PER; ++r) {
+        const int b = b_beg + r;
+        if (b < NB && keep[b] && (b == 0 || !keep[b - 1])) {
+            int e = b + 1;
+            while (e < NB && keep[e]) ++e;
+            runs[2 * at] = b;
+            runs[2 * at + 1] = e;
+            ++at;
+        }
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        s_R = (int)sinc;
+        ts->kept = (int)kinc;
+        ts->nruns = (int)sinc;
+    }
+    __syncthreads();
+    const int R = s_R;
+    auto lo_of = [&](int r) -> double {
+        const int b = runs[2 * r];
+        if (b == 0) return -INFINITY;
+        const double v = (double)bnd[b - 1] * 0x1p-32;
+        return v - (fabs(v) * 0x1p-18 + 0x1p-30);
+    };
+    auto hi_of = [&](int r) -> double {
+        const int e = runs[2 * r + 1];
+        if (e >= NB) return (double)INFINITY;
+        const double v = (double)bnd[e - 1] * 0x1p-32;
+        return v + (fabs(v) * 0x1p-18 + 0x1p-30);
+    };
+    // separators: the PRE_MAX - 1 widest gaps (gap r lies between runs r - 1 and r)
+    const int nsep = min(R - 1, PRE_MAX - 1);
+    for (int t = 0; t < nsep; ++t) {
+        double bv = -1.0;
+        int bi = 0x7fffffff;
+        for (int r = 1 + threadIdx.x; r < R; r += blockDim.x) {
+            bool taken = false;
+            for (int u = 0; u < t; ++u) taken |= s_sep[u] == r;
+            if (taken) continue;
+            const double g = lo_of(r) - hi_of(r - 1);
+            if (g > bv || (g == bv && r < bi)) { bv = g; bi = r; }
+        }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+            const double ov = __shfl_xor_sync(FULL, bv, d);
+            const int oi = __shfl_xor_sync(FULL, bi, d);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { s_gv[threadIdx.x >> 5] = bv; s_gi[threadIdx.x >> 5] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double v = -1.0;
+            int vi = 0x7fffffff;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (s_gv[w] > v || (s_gv[w] == v && s_gi[w] < vi)) { v = s_gv[w]; vi = s_gi[w]; }
+            s_sep[t] = vi;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // separators in increasing order
+        int sep[PRE_MAX];
+        for (int t = 0; t < nsep; ++t) sep[t] = s_sep[t];
+        for (int a = 1; a < nsep; ++a)
+            for (int b = a; b > 0 && sep[b - 1] > sep[b]; --b) { const int tt = sep[b]; sep[b] = sep[b - 1]; sep[b - 1] = tt; }
+        float2 out[PRE_MAX];
+        int nc = 0;
+        if (R == 0) {
+            out[nc++] = make_float2(-INFINITY, INFINITY);   // nothing kept: test every pair
+        } else {
+            int first = 0;
+            for (int t = 0; t <= nsep; ++t) {
+                const int last = t < nsep ? sep[t] - 1 : R - 1;
+                float2 f;
+                f.x = nextafterf((float)lo_of(first), -INFINITY);
+                f.y = nextafterf((float)hi_of(last), INFINITY);
+                if (nc > 0 && f.x <= out[nc - 1].y) out[nc - 1].y = fmaxf(out[nc - 1].y, f.y);
+                else out[nc++] = f;
+                first = last + 1;
+            }
+        }
+        for (int c = 0; c < PRE_MAX; ++c) pre[c] = c < nc ? out[c] : make_float2(INFINITY, INFINITY);
+        ts->covers = nc;
+    }
+}
+
+// Sweep ranges over the kept events (after the restricted count: base holds
+// the kept buckets' event starts): the kept events of each maximal run of
+// kept buckets are cut into pieces of about `target` events (a range never
+// spans a dropped bucket: the kinetic order must see every event between its
+// first and last slope); k_snap_ranges then moves every bound to the next
+// start of a group of equal slopes.  A range costs one start sort of all n
+// points (about a wave of start sorts per SM count of ranges) plus its events
+// one after another, so R ranges of K kept events take about
+// (R / SMs) T_sort + (K / R) T_event; with T_sort / T_event about 128
+// events' worth at 152 SMs that is least near K / R = sqrt(0.8 K) events per
+// range.  At least BNB_MIN_RANGE events per range and at most W ranges.
+__global__ void __launch_bounds__(TREE_THREADS) k_tree_ranges(const int *__restrict__ meta,
+                                                              const unsigned *__restrict__ base,
+                                                              const int *__restrict__ runs, int W, int G,
+                                                              unsigned *__restrict__ range,
+                                                              TreeState *__restrict__ ts)
+{
+    __shared__ long long s_warp[32];
+    __shared__ unsigned long long s_target;
+    const int NB = meta[0] + 1;
+    const unsigned total = base[NB];
+    const int nr = ts->nruns;
+    if (threadIdx.x == 0) {
+        unsigned long long t = max((unsigned long long)BNB_MIN_RANGE,
+                                   (unsigned long long)sqrt(0.8 * (double)total));
+        t = max(t, ((unsigned long long)total + G - 1) / G);
+        for (;;) {
+            unsigned long long cnt = 0;
+            for (int r = 0; r < nr; ++r) {
+                const unsigned len = base[runs[2 * r + 1]] - base[runs[2 * r]];
+                cnt += (len + t - 1) / t;
+            }
+            if (cnt <= (unsigned long long)W) break;
+            t *= 2;
+        }
+        s_target = t;
+        ts->swept = total;
+    }
+    __syncthreads();
+    const unsigned long long t = s_target;
+    // pieces per run, exclusive offsets (runs in chunks per thread)
+    const int per = (nr + blockDim.x - 1) / blockDim.x;
+    const int r0 = threadIdx.x * per, r1 = min(nr, r0 + per);
+    long long psum = 0;
+    for (int r = r0; r < r1; ++r) {
+        const unsigned len = base[runs[2 * r + 1]] - base[runs[2 * r]];
+        psum += (long long)((len + t - 1) / t);
+    }
+    const long long pinc = block_scan<false>(psum, s_warp);
+    __shared__ long long s_pieces;
+    if (threadIdx.x == blockDim.x - 1) s_pieces = pinc;
+    long long o = pinc - psum;
+    for (int r = r0; r < r1; ++r) {
+        const unsigned a = base[runs[2 * r]], len = base[runs[2 * r + 1]] - a;
+        const unsigned long long pieces = (len + t - 1) / t;
+        for (unsigned long long q = 0; q < pieces; ++q) {
+            range[2 * o] = a + (unsigned)(len * q / pieces);
+            range[2 * o + 1] = a + (unsigned)(len * (q + 1) / pieces);
+            ++o;
+        }
+    }
+    __syncthreads();
+    // the ranges past the last piece are empty
+    for (long long w = s_pieces + threadIdx.x; w < W; w += blockDim.x) {
+        range[2 * w] = total;
+        range[2 * w + 1] = total;
+    }
+}
 
 size_t bnb_extra_bytes(int n, int sms)
 {
@@ -300,19 +771,28 @@ size_t bnb_extra_bytes(int n, int sms)
     const int grid = 2 * sms;
     size_t b = 0;
     b += a256(64);                                   // xc, ub
-    b += a256((size_t)BNB_SEEDS * 8 * 2);            // seed keys, seed widths
-    b += a256((size_t)BND_MAX * 2 * 8);              // node keys
+    b += a256((size_t)BNB_SEEDS_MAX * BNB_ROUNDS * 8 * 2);   // seed keys, seed widths of every round
+    b += a256(sizeof(TreeState));                    // tree state
+    b += 2 * a256((size_t)BND_MAX * sizeof(int2));   // nodes, two levels
+    b += 2 * a256((size_t)BND_MAX * 2 * 8);          // node keys, two levels
     b += a256((size_t)BND_MAX);                      // prune flags
     b += a256((size_t)BND_MAX * 8);                  // node lower bounds
+    b += a256((size_t)BND_MAX * 4);                  // child offsets
     b += a256((size_t)BND_MAX);                      // keep mask
     b += a256((size_t)BND_MAX * 4);                  // sampled pairs per bucket
+    b += a256((size_t)(BND_MAX + 1) * 4);            // their prefix
+    b += a256((size_t)(BND_MAX + 1) * 2 * 4);        // runs of kept buckets
     b += a256((size_t)PRE_MAX * sizeof(float2));     // slope pre-filter of the restricted pair passes
     b += (n > SORT_SMEM_N) ? a256((size_t)grid * 2 * P * 8) : 0;
     return b;
 }
 
-// Host-driven B&B: the bucket counts decide the tree, the device evaluates
-// bounds level by level.  Synchronises with the stream between levels.
+// The whole branch-and-bound is queued on the stream without a host round
+// trip: seeds and upper bound, BNB_LEVELS levels of interval bounds with
+// their splits, the slope covers of the kept buckets, the restricted pair
+// pass, the sweep ranges, the exact sweep of the kept events and the argmin.
+// Levels left without nodes cost two empty launches.  With stats the call
+// waits for the fit to read them back; without, it returns at once.
 int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pred_dev, int seed_mode, lms_result *out,
             lms_bnb_stats *stats, void *extra, int sms, cudaStream_t st)
 {
@@ -321,54 +801,38 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     auto take = [&](size_t bytes) { void *r = cur; cur += a256(bytes); return r; };
     int *xc = (int *)take(64);
     long long *ub = (long long *)(xc + 4);
-    long long *seed_keys = (long long *)take((size_t)BNB_SEEDS * 8 * 2);
-    long long *seed_w = seed_keys + BNB_SEEDS;
-    long long *node_keys = (long long *)take((size_t)BND_MAX * 2 * 8);
+    const int KS = bnb_seeds(sms);
+    long long *seed_keys = (long long *)take((size_t)BNB_SEEDS_MAX * BNB_ROUNDS * 8 * 2);
+    long long *seed_w = seed_keys + (size_t)KS * BNB_ROUNDS;
+    TreeState *ts = (TreeState *)take(sizeof(TreeState));
+    int2 *nodes[2];
+    nodes[0] = (int2 *)take((size_t)BND_MAX * sizeof(int2));
+    nodes[1] = (int2 *)take((size_t)BND_MAX * sizeof(int2));
+    long long *nkeys[2];
+    nkeys[0] = (long long *)take((size_t)BND_MAX * 2 * 8);
+    nkeys[1] = (long long *)take((size_t)BND_MAX * 2 * 8);
     unsigned char *prune = (unsigned char *)take(BND_MAX);
     long long *lbv = (long long *)take((size_t)BND_MAX * 8);
+    int *offs = (int *)take((size_t)BND_MAX * 4);
     unsigned char *keep = (unsigned char *)take(BND_MAX);
     unsigned *scount = (unsigned *)take((size_t)BND_MAX * 4);
+    unsigned *sbase = (unsigned *)take((size_t)(BND_MAX + 1) * 4);
+    int *runs = (int *)take((size_t)(BND_MAX + 1) * 2 * 4);
     float2 *pre = (float2 *)take((size_t)PRE_MAX * sizeof(float2));
     int P = 1;
     while (P < n) P <<= 1;
     long long *gscr = (n > SORT_SMEM_N) ? (long long *)take((size_t)2 * sms * 2 * P * 8) : nullptr;
     const int grid = 2 * sms;
 
-    unsigned char *hs = host_stage();
-    if (!hs) return LMS_ERR_CUDA;
-    int *h_meta = reinterpret_cast<int *>(hs + HS_META);
-    long long *h_ub = reinterpret_cast<long long *>(hs + HS_UB);
-    const unsigned *cnt = reinterpret_cast<const unsigned *>(hs + HS_CNT);
-    const long long *bnd = reinterpret_cast<const long long *>(hs + HS_BND);
-    const unsigned *kbase = reinterpret_cast<const unsigned *>(hs + HS_KBASE);
-    unsigned char *h_prune = hs + HS_PRUNE;
-
     if (launch_sweep_sample(p, x, y, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (launch_sample_counts(p, scount, st) != cudaSuccess) return LMS_ERR_CUDA;
-    // bucket structure to the host; the tree weighs buckets by sampled pairs
-    // (the buckets are quantile ranges of the sample), so no pass over all
-    // pairs is needed before the bounds have pruned.  The reads are waited
-    // for after the seed stage is queued, so the host builds the first level
-    // while the GPU scores the seeds.
-    cudaEvent_t sampled;
-    if (cudaEventCreateWithFlags(&sampled, cudaEventDisableTiming) != cudaSuccess) return LMS_ERR_CUDA;
-    const bool queued = cudaMemcpyAsync(h_meta, p.meta, sizeof(int) * 4, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-                        cudaMemcpyAsync(hs + HS_CNT, scount, sizeof(unsigned) * BND_MAX, cudaMemcpyDeviceToHost,
-                                        st) == cudaSuccess &&
-                        cudaMemcpyAsync(hs + HS_BND, p.bnd, sizeof(long long) * BND_MAX, cudaMemcpyDeviceToHost,
-                                        st) == cudaSuccess &&
-                        cudaEventRecord(sampled, st) == cudaSuccess;
-    if (!queued) {
-        cudaEventDestroy(sampled);
-        return LMS_ERR_CUDA;
-    }
     {
         StageTimer _t(STAGE_SEEDS, st);
         k_x_center<<<1, 1024, 0, st>>>(p.xy, n, xc);
     }
     {
         StageTimer _t(STAGE_SEEDS, st);
-        k_pick_seeds<<<1, 128, 0, st>>>(sorted_sample(p), p.S, pred_dev, seed_mode, BNB_SEEDS, seed_keys);
+        k_pick_seeds<<<1, 128, 0, st>>>(sorted_sample(p), p.S, pred_dev, seed_mode, KS, seed_keys);
     }
     const int Ps = P < 1024 ? 1024 : P;   // the shared-memory sorts fill whole 1024-thread CTAs
     // one sorted array plus merge scratch; two sorted arrays plus scratch
@@ -378,196 +842,75 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     cudaFuncSetAttribute(k_node_lb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_sorts);
     {
         StageTimer _t(STAGE_SEEDS, st);
-        k_score_dyadic<<<std::min(BNB_SEEDS, grid), 1024, one_sort, st>>>(p.xy, n, h, xc, seed_keys, BNB_SEEDS,
-                                                                           seed_w, gscr);
+        k_score_dyadic<<<std::min(KS, grid), 1024, one_sort, st>>>(p.xy, n, h, xc, seed_keys, KS, seed_w, gscr);
+    }
+    for (int r = 2; r <= BNB_ROUNDS; ++r) {
+        long long *keys_r = seed_keys + (size_t)(r - 1) * KS, *w_r = seed_w + (size_t)(r - 1) * KS;
+        {
+            StageTimer _t(STAGE_SEEDS, st);
+            k_zoom_seeds<<<1, 256, 0, st>>>(sorted_sample(p), p.S, keys_r - KS, w_r - KS, KS, r, keys_r);
+        }
+        {
+            StageTimer _t(STAGE_SEEDS, st);
+            k_score_dyadic<<<std::min(KS, grid), 1024, one_sort, st>>>(p.xy, n, h, xc, keys_r, KS, w_r, gscr);
+        }
     }
     {
         StageTimer _t(STAGE_SEEDS, st);
-        k_min_ub<<<1, 32, 0, st>>>(seed_w, BNB_SEEDS, ub);
+        k_min_ub<<<1, 32, 0, st>>>(seed_w, KS * BNB_ROUNDS, ub);
     }
-    const cudaError_t waited = cudaEventSynchronize(sampled);
-    cudaEventDestroy(sampled);
-    if (waited != cudaSuccess) return LMS_ERR_CUDA;
-    const int NB = h_meta[0] + 1;
-    std::vector<unsigned> base(NB + 1);
-    base[0] = 0;
-    for (int b = 0; b < NB; ++b) base[b + 1] = base[b] + cnt[b];
-    const unsigned E = base[NB];
-    std::vector<unsigned char> keepv(NB, 0);
-    // first level: equal-event ranges of buckets
-    struct Node { int b0, b1; };
-    std::vector<Node> nodes;
+    // the interval tree, level by level, all on the device
     {
-        const int m0 = std::min(NB, std::max(BNB_FIRST_NODES, sms));
-        int prev = 0;
-        for (int k = 1; k <= m0; ++k) {
-            const unsigned long long target = (unsigned long long)E * k / m0;
-            int b = (int)(std::lower_bound(base.begin(), base.begin() + NB + 1, (unsigned)target) - base.begin());
-            if (k == m0) b = NB;
-            b = std::max(b, prev + 1);
-            if (b > NB) b = NB;
-            if (b > prev) nodes.push_back({prev, b});
-            prev = b;
-            if (prev >= NB) break;
+        StageTimer _t(STAGE_NODE_LB, st);
+        k_tree_first<<<1, TREE_THREADS, 0, st>>>(scount, p.meta, p.bnd, sms, sbase, nodes[0], nkeys[0], keep, ts);
+    }
+    for (int L = 0; L < BNB_LEVELS; ++L) {
+        {
+            StageTimer _t(STAGE_NODE_LB, st);
+            k_node_lb<<<sms, 1024, two_sorts, st>>>(p.xy, n, h, xc, nkeys[L & 1], &ts->count[L & 1], ub, prune, lbv,
+                                                    gscr);
+        }
+        {
+            StageTimer _t(STAGE_NODE_LB, st);
+            k_tree_step<<<1, TREE_THREADS, 0, st>>>(L, sms, p.meta, p.bnd, sbase, nodes[L & 1], prune,
+                                                    nodes[(L + 1) & 1], nkeys[(L + 1) & 1], offs, keep, ts);
         }
     }
-    long long evaluated = 0, pruned = 0;
-    int levels = 0;
-    std::vector<long long> hk;
-    std::vector<unsigned char> hp;
-    while (!nodes.empty()) {
-        ++levels;
-        const int nn = (int)nodes.size();
-        hk.resize(2 * nn);
-        for (int k = 0; k < nn; ++k) {
-            hk[2 * k] = nodes[k].b0 == 0 ? -I64_MAX : bnd[nodes[k].b0 - 1];
-            hk[2 * k + 1] = nodes[k].b1 >= NB ? I64_MAX : bnd[nodes[k].b1 - 1];
-        }
-        for (int off = 0; off < nn; off += BND_MAX) {
-            const int chunk = std::min(BND_MAX, nn - off);
-            if (cudaMemcpyAsync(node_keys, hk.data() + 2 * off, sizeof(long long) * 2 * chunk, cudaMemcpyHostToDevice,
-                                st) != cudaSuccess)
-                return LMS_ERR_CUDA;
-            {
-                StageTimer _t(STAGE_NODE_LB, st);
-                k_node_lb<<<std::min(chunk, grid), 1024, two_sorts, st>>>(p.xy, n, h, xc, node_keys, chunk, ub, prune,
-                                                                        lbv, gscr);
-            }
-            hp.resize(nn);
-            if (cudaMemcpyAsync(h_prune, prune, chunk, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-                return LMS_ERR_CUDA;
-            if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
-            std::memcpy(hp.data() + off, h_prune, chunk);
-        }
-        evaluated += nn;
-        // survivors split into F children of about equal sampled events, F
-        // chosen so that the next level about fills the SMs (fewer levels,
-        // each a host round trip)
-        int split = 0;
-        for (int k = 0; k < nn; ++k)
-            if (!hp[k] && nodes[k].b1 - nodes[k].b0 > 1) ++split;
-        const int F = split ? std::max(2, std::min(16, sms / split)) : 2;
-        std::vector<Node> next;
-        for (int k = 0; k < nn; ++k) {
-            const Node nd = nodes[k];
-            if (hp[k]) { ++pruned; continue; }
-            if (nd.b1 - nd.b0 == 1) { keepv[nd.b0] = 1; continue; }
-            const int parts = std::min(F, nd.b1 - nd.b0);
-            int prev_b = nd.b0;
-            for (int q = 1; q <= parts; ++q) {
-                int m = nd.b1;
-                if (q < parts) {
-                    const unsigned long long tgt =
-                        base[nd.b0] + (unsigned long long)(base[nd.b1] - base[nd.b0]) * q / parts;
-                    m = (int)(std::upper_bound(base.begin() + prev_b + 1, base.begin() + nd.b1, (unsigned)tgt) -
-                              base.begin());
-                    m = std::min(std::max(m, prev_b + 1), nd.b1 - (parts - q));
-                }
-                next.push_back({prev_b, m});
-                prev_b = m;
-            }
-        }
-        nodes.swap(next);
+    {
+        StageTimer _t(STAGE_NODE_LB, st);
+        k_tree_covers<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, runs, pre, ts);
     }
-    // slope covers of the runs of kept buckets for the pair passes: bucket b
-    // holds keys [bnd[b - 1], bnd[b]), a key being floor(slope 2^32); each
-    // cover is widened by more than the float slope error (2^-21 relative)
-    // and rounded outward; at most PRE_MAX covers (closest runs merged)
-    std::vector<std::pair<double, double>> cov;
-    unsigned kept_buckets = 0;
-    for (int b = 0; b < NB;) {
-        if (!keepv[b]) { ++b; continue; }
-        int e = b + 1;
-        while (e < NB && keepv[e]) ++e;
-        kept_buckets += (unsigned)(e - b);
-        const double lo = b == 0 ? -INFINITY : (double)bnd[b - 1] * 0x1p-32;
-        const double hi = e >= NB ? INFINITY : (double)bnd[e - 1] * 0x1p-32;
-        cov.push_back({lo - (std::isinf(lo) ? 0.0 : std::fabs(lo) * 0x1p-18 + 0x1p-30),
-                       hi + (std::isinf(hi) ? 0.0 : std::fabs(hi) * 0x1p-18 + 0x1p-30)});
-        b = e;
-    }
-    while (cov.size() > (size_t)PRE_MAX) {
-        size_t best = 1;
-        for (size_t k = 2; k < cov.size(); ++k)
-            if (cov[k].first - cov[k - 1].second < cov[best].first - cov[best - 1].second) best = k;
-        cov[best - 1].second = cov[best].second;
-        cov.erase(cov.begin() + best);
-    }
-    // rounded outward to floats; covers that now touch or overlap are merged
-    // so that they stay sorted and disjoint (the device searches them)
-    std::vector<float2> prev;
-    for (size_t k = 0; k < cov.size(); ++k) {
-        float2 f;
-        f.x = std::nextafter((float)cov[k].first, -INFINITY);
-        f.y = std::nextafter((float)cov[k].second, INFINITY);
-        if (!prev.empty() && f.x <= prev.back().y) prev.back().y = std::max(prev.back().y, f.y);
-        else prev.push_back(f);
-    }
-    const int npre = (int)prev.size();
-    if (cudaMemcpyAsync(keep, keepv.data(), NB, cudaMemcpyHostToDevice, st) != cudaSuccess) return LMS_ERR_CUDA;
-    if (npre > 0 && cudaMemcpyAsync(pre, prev.data(), sizeof(float2) * npre, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return LMS_ERR_CUDA;
     // exact events of the kept buckets only: p.base becomes their starts
-    if (launch_sweep_count(p, keep, npre > 0 ? pre : nullptr, npre, st) != cudaSuccess) return LMS_ERR_CUDA;
-    if (cudaMemcpyAsync(hs + HS_KBASE, p.base, sizeof(unsigned) * (NB + 1), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(h_meta, p.meta, sizeof(int) * 6, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(h_ub, ub, sizeof(long long), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        return LMS_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
-    const unsigned events_total = (unsigned)h_meta[5];
-    const long long ub_host = *h_ub;
-    const unsigned run = kbase[NB];
-    // ranges: pieces of about `target` events inside each run of consecutive
-    // kept buckets (a range never spans a dropped bucket: the kinetic order
-    // must see every event between its first and last slope); the device
-    // then moves every bound forward to the next start of a group of equal
-    // slopes.  About one range per sweeping warp, but at least
-    // BNB_MIN_RANGE events each, so that a range's start sort pays off.
-    std::vector<unsigned> rng(2 * (size_t)p.W, 0u);
+    if (launch_sweep_count(p, keep, pre, PRE_MAX, st) != cudaSuccess) return LMS_ERR_CUDA;
     {
-        std::vector<std::pair<unsigned, unsigned>> runs;
-        for (int b = 0; b < NB;) {
-            if (!keepv[b] || kbase[b + 1] == kbase[b]) { ++b; continue; }
-            int e = b + 1;
-            while (e < NB && keepv[e]) ++e;
-            runs.push_back({kbase[b], kbase[e]});
-            b = e;
-        }
-        unsigned long long target = std::max<unsigned long long>(BNB_MIN_RANGE, ((unsigned long long)run + p.G - 1) / p.G);
-        for (;;) {
-            unsigned long long count = 0;
-            for (const auto &r : runs) count += (r.second - r.first + target - 1) / target;
-            if (count <= (unsigned long long)p.W) break;
-            target *= 2;
-        }
-        size_t used = 0;
-        for (const auto &r : runs) {
-            const unsigned long long len = r.second - r.first;
-            const unsigned long long pieces = (len + target - 1) / target;
-            for (unsigned long long k = 0; k < pieces; ++k) {
-                rng[2 * used] = r.first + (unsigned)(len * k / pieces);
-                rng[2 * used + 1] = r.first + (unsigned)(len * (k + 1) / pieces);
-                ++used;
-            }
-        }
-        for (size_t w = used; w < (size_t)p.W; ++w) { rng[2 * w] = run; rng[2 * w + 1] = run; }
+        StageTimer _t(STAGE_PLAN, st);
+        k_tree_ranges<<<1, TREE_THREADS, 0, st>>>(p.meta, p.base, runs, p.W, p.G, p.range, ts);
     }
-    if (cudaMemcpyAsync(p.range, rng.data(), sizeof(unsigned) * 2 * p.W, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return LMS_ERR_CUDA;
-    if (launch_sweep_finish(p, keep, st, false, npre > 0 ? pre : nullptr, npre) != cudaSuccess) return LMS_ERR_CUDA;
+    if (launch_sweep_finish(p, keep, st, false, pre, PRE_MAX) != cudaSuccess) return LMS_ERR_CUDA;
     if (launch_argmin(p.cands, p.W + p.G, out, LMS_ALGO_BNB, p.meta + 3, st) != cudaSuccess) return LMS_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return LMS_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return LMS_ERR_CUDA;
     if (stats) {
-        stats->events_total = events_total;
-        stats->events_swept = run;
-        stats->buckets_total = NB;
-        stats->buckets_swept = kept_buckets;
-        stats->nodes_evaluated = evaluated;
-        stats->nodes_pruned = pruned;
-        stats->levels = levels;
+        unsigned char *hs = host_stage();
+        if (!hs) return LMS_ERR_CUDA;
+        if (cudaMemcpyAsync(hs, ts, sizeof(TreeState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hs + 64, p.meta, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hs + 128, ub, sizeof(long long), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return LMS_ERR_CUDA;
+        TreeState t;
+        std::memcpy(&t, hs, sizeof(t));
+        const int *meta = reinterpret_cast<const int *>(hs + 64);
+        long long ubh;
+        std::memcpy(&ubh, hs + 128, sizeof(ubh));
+        stats->events_total = (unsigned)meta[5];
+        stats->events_swept = t.swept;
+        stats->buckets_total = meta[0] + 1;
+        stats->buckets_swept = t.kept;
+        stats->nodes_evaluated = t.evaluated;
+        stats->nodes_pruned = t.pruned;
+        stats->levels = t.levels;
         stats->seeded = pred_dev ? 1 : 0;
-        stats->upper_bound = ub_host == I64_MAX ? -1.0 : (double)ub_host / 4294967296.0;
+        stats->upper_bound = ubh == I64_MAX ? -1.0 : (double)ubh / 4294967296.0;
     }
     return LMS_OK;
 }

@@ -584,7 +584,11 @@ __global__ void __launch_bounds__(1024) k_segsort(const void *__restrict__ xy, u
             };
             __syncthreads();
             const int Pw = P < (int)blockDim.x ? (int)blockDim.x : P;
-            if (cta_fill_sort_any(w, Pw, word)) {
+            // merge sort (registers, then merge-path levels) where its scratch
+            // copy fits beside the words, else the register-blocked bitonic sort
+            const bool sorted = 2 * Pw <= SEG_CAP * 3 / 2 ? cta_fill_merge_sort_any(w, w + Pw, Pw, word)
+                                                           : cta_fill_sort_any(w, Pw, word);
+            if (sorted) {
                 for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
                     const unsigned long long v = w[k];
                     const bool cont = k > 0 && (w[k - 1] >> 32) == (v >> 32);
@@ -795,6 +799,50 @@ __global__ void k_snap_ranges(const unsigned *__restrict__ ev, const unsigned *_
     if (lane == 0) range[k] = v;
 }
 
+// The snapped bounds are group starts but need not be monotone: a bound
+// deep inside a group longer than SNAP_SCAN events moves to its bucket's
+// end, one near the group's end to the group's end.  A running maximum over
+// the bounds in order (start_0, end_0, start_1, ...) makes them monotone:
+// every value is still a group start, a raised start only drops events that
+// the previous range already covers, and the ranges become disjoint, so every
+// event is swept exactly once (k_sweep checks the total).  One CTA, in
+// chunks of consecutive bounds per thread.
+__global__ void __launch_bounds__(1024) k_monotone_ranges(unsigned *__restrict__ range, int count)
+{
+    __shared__ unsigned s_warp[32];
+    const int per = (count + blockDim.x - 1) / blockDim.x;
+    const int k0 = threadIdx.x * per, k1 = min(count, k0 + per);
+    unsigned m = 0;
+    for (int k = k0; k < k1; ++k) m = max(m, range[k]);
+    // exclusive running maximum of the chunks before this thread's
+    unsigned v = m;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned o = __shfl_up_sync(FULL, v, d);
+        if (lane >= d) v = max(v, o);
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned t = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned o = __shfl_up_sync(FULL, t, d);
+            if (lane >= d) t = max(t, o);
+        }
+        s_warp[lane] = t;
+    }
+    __syncthreads();
+    unsigned run = __shfl_up_sync(FULL, v, 1);
+    if (lane == 0) run = 0u;
+    if (warp > 0) run = max(run, s_warp[warp - 1]);
+    for (int k = k0; k < k1; ++k) {
+        run = max(run, range[k]);
+        range[k] = run;
+    }
+}
+
 // ---------------------------------------------------------------- init
 // Bitonic sort of P (power of two) packed words in `a` by one CTA.
 __device__ void cta_bitonic_u64(unsigned long long *a, int P)
@@ -869,7 +917,11 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
     const unsigned E = base[meta[0] + 1];
     const unsigned start = range[2 * w], end = range[2 * w + 1];
     const bool vertical = (E == 0 && w == 0);
-    if (w == 0 && threadIdx.x == 0) meta_mut[4] = 0;   // range counter of k_sweep
+    if (w == 0 && threadIdx.x == 0) {
+        meta_mut[4] = 0;          // range counter of k_sweep
+        meta_mut[7] = 0;          // events the sweep's ranges cover, summed by k_sweep
+        meta_mut[8] = (int)E;     // events to cover (checked by the final reduction)
+    }
     if (start >= end && !vertical) {
         if (threadIdx.x == 0) cands[w] = cand_empty();
         return;
@@ -975,6 +1027,47 @@ __device__ __forceinline__ int load_xy(const int *s_xy, const int *__restrict__ 
 __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 constexpr int RUN_LANE_MAX = 24;   // runs up to this length are handled by one lane
+
+// A range's start order (global, written by k_sweep_init) into the warp's
+// order and position arrays.  When n is a multiple of 8 the order is read as
+// 16-byte words, four per lane in flight (the slice starts at w n 2 bytes of
+// a 256-byte aligned array, so it is 16-byte aligned), and stored to shared
+// memory as 16-byte words; else one 16-bit entry at a time.
+__device__ __forceinline__ void load_order(const unsigned short *__restrict__ src, int n, unsigned short *order,
+                                           unsigned short *pos, int lane)
+{
+    if ((n & 7) == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *o4 = reinterpret_cast<uint4 *>(order);
+        const int n8 = n >> 3;
+        for (int v0 = 0; v0 < n8; v0 += 4 * 32) {
+            uint4 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int v = v0 + u * 32 + lane;
+                q[u] = v < n8 ? s4[v] : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int v = v0 + u * 32 + lane;
+                if (v >= n8) continue;
+                o4[v] = q[u];
+                const unsigned wds[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    pos[wds[r] & 0xffffu] = (unsigned short)(8 * v + 2 * r);
+                    pos[wds[r] >> 16] = (unsigned short)(8 * v + 2 * r + 1);
+                }
+            }
+        }
+    } else {
+        for (int a = lane; a < n; a += 32) {
+            const unsigned short p = src[a];
+            order[a] = p;
+            pos[p] = (unsigned short)a;
+        }
+    }
+}
 #ifndef SWEEP_SERIAL_DEFAULT
 #define SWEEP_SERIAL_DEFAULT false
 #endif
@@ -991,16 +1084,23 @@ constexpr bool SWEEP_SERIAL = SWEEP_SERIAL_DEFAULT;   // every batch one event a
 constexpr int SERIAL_BELOW = SWEEP_SERIAL_BELOW, SERIAL_CHUNKS = SWEEP_SERIAL_CHUNKS;
 
 // A whole group of one slope dy/dx in one pass over the positions, for
-// groups of about n/4 events or more.  Two points with equal projections at
+// groups of about n/2 events or more.  Two points with equal projections at
 // the slope and different x are joined by an event of the group, so every
 // maximal block of two or more positions with equal projections is one line
 // of that slope (plus duplicates of its points, whose order is immaterial);
 // the group reverses exactly these blocks.  The warp slides a window of 32
 // positions over the order (lane l holds position p0 + l), compares each
 // key with its neighbours' by shuffles, and finds the blocks ending inside
-// the window; each is reversed by the whole warp and its two windows are
-// re-scored.  A block never reaches past its end, so the next window's
-// entries can be fetched before this window's blocks are rewritten.
+// the window.  The lane holding a block's end reverses it and re-scores its
+// two windows, all such lanes at once (the blocks are disjoint); blocks
+// longer than HEAVY_LANE_MAX positions are then reversed by the whole warp,
+// one after another.  The key at a position depends only on which block
+// holds it, not on the order inside the block, so the window-end keys read
+// while other blocks are being reversed are the same before and after; and a
+// block never reaches past its end, so the next window's entries can be
+// fetched before this window's blocks are rewritten.
+constexpr int HEAVY_LANE_MAX = 32;
+
 template <bool XY_SMEM>
 __device__ void heavy_scan(unsigned short *order, unsigned short *pos, const int *s_xy,
                            const int *__restrict__ g_xy, int n, int h, int dy, int dx, unsigned gmin, int lane,
@@ -1009,6 +1109,18 @@ __device__ void heavy_scan(unsigned short *order, unsigned short *pos, const int
     auto XY = [&](int k) { return load_xy<XY_SMEM>(s_xy, g_xy, k); };
     Cand c;
     c.dy = dy; c.dx = dx; c.i = (int)(gmin >> 16); c.j = (int)(gmin & 0xffffu);
+    auto rescore = [&](int s0, int e0, long long K) {
+        if (s0 + h - 1 < n) {
+            const long long kt = proj(XY(order[s0 + h - 1]), dy, dx);
+            c.w = kt - K; c.t = K + kt;
+            if (cand_better(c, best)) best = c;
+        }
+        if (e0 - h + 1 >= 0) {
+            const long long kb = proj(XY(order[e0 - h + 1]), dy, dx);
+            c.w = K - kb; c.t = kb + K;
+            if (cand_better(c, best)) best = c;
+        }
+    };
     int open = -1;                 // start of a block still open at p0 (warp-uniform)
     long long kprev = 0;           // key at p0 - 1 (p0 > 0)
     int idx = lane < n ? order[lane] : 0;
@@ -1028,47 +1140,51 @@ __device__ void heavy_scan(unsigned short *order, unsigned short *pos, const int
         if (lane == 0) kp = kprev;
         const bool eq_next = p + 1 < n && kn == k;
         const bool eq_prev = p > 0 && p < n && kp == k;
-        unsigned starts = __ballot_sync(FULL, eq_next && !eq_prev);
-        unsigned ends = __ballot_sync(FULL, eq_prev && !eq_next);
-        while (ends) {
-            const int el = __ffs(ends) - 1;
-            ends &= ends - 1;
-            const unsigned before = starts & ((2u << el) - 1u);
-            int s0;
-            if (before) {
-                const int sl = 31 - __clz(before);
-                s0 = p0 + sl;
-                starts &= ~(1u << sl);
-            } else {
-                s0 = open;
+        const unsigned starts = __ballot_sync(FULL, eq_next && !eq_prev);
+        const unsigned ends = __ballot_sync(FULL, eq_prev && !eq_next);
+        // this lane's block: from the last start at or before it (or the
+        // block open since an earlier window) to this lane's end
+        const bool is_end = (ends >> lane) & 1u;
+        int s0 = -1;
+        if (is_end) {
+            const unsigned before = starts & ((2u << lane) - 1u);
+            s0 = before ? p0 + 31 - __clz(before) : open;
+        }
+        const int e0 = p0 + lane;
+        const bool mine = is_end && s0 >= 0 && e0 - s0 + 1 <= HEAVY_LANE_MAX;
+        const bool longb = is_end && s0 >= 0 && !mine;
+        __syncwarp();
+        if (mine) {
+            for (int u = s0, v = e0; u < v; ++u, --v) {
+                const unsigned short ou = order[u], ov = order[v];
+                order[u] = ov;
+                order[v] = ou;
+                pos[ov] = (unsigned short)u;
+                pos[ou] = (unsigned short)v;
             }
-            const int e0 = p0 + el;
-            open = -1;
-            if (s0 < 0) continue;   // an end always follows its start; never taken
+            rescore(s0, e0, k);
+        }
+        __syncwarp();
+        for (unsigned lm = __ballot_sync(FULL, longb); lm; lm &= lm - 1) {
+            const int el = __ffs(lm) - 1;
+            const int ls0 = __shfl_sync(FULL, s0, el), le0 = p0 + el;
             const long long K = __shfl_sync(FULL, k, el);
-            const int len = e0 - s0 + 1;
+            const int len = le0 - ls0 + 1;
             for (int t = lane; t < len / 2; t += 32) {
-                const unsigned short u = order[s0 + t], v = order[e0 - t];
-                order[s0 + t] = v;
-                order[e0 - t] = u;
+                const unsigned short u = order[ls0 + t], v = order[le0 - t];
+                order[ls0 + t] = v;
+                order[le0 - t] = u;
             }
             __syncwarp();
-            for (int t = lane; t < len; t += 32) pos[order[s0 + t]] = (unsigned short)(s0 + t);
-            if (lane == 0) {
-                if (s0 + h - 1 < n) {
-                    const long long kt = proj(XY(order[s0 + h - 1]), dy, dx);
-                    c.w = kt - K; c.t = K + kt;
-                    if (cand_better(c, best)) best = c;
-                }
-                if (e0 - h + 1 >= 0) {
-                    const long long kb = proj(XY(order[e0 - h + 1]), dy, dx);
-                    c.w = K - kb; c.t = kb + K;
-                    if (cand_better(c, best)) best = c;
-                }
-            }
+            for (int t = lane; t < len; t += 32) pos[order[ls0 + t]] = (unsigned short)(ls0 + t);
+            if (lane == 0) rescore(ls0, le0, K);
             __syncwarp();
         }
-        if (starts) open = p0 + 31 - __clz(starts);
+        // the block left open at the end of this window, if any
+        const int last_s = starts ? 31 - __clz(starts) : -1;
+        const int last_e = ends ? 31 - __clz(ends) : -1;
+        if (last_s > last_e) open = p0 + last_s;
+        else if (ends) open = -1;
         kprev = __shfl_sync(FULL, k, 31);
     }
     __syncwarp();
@@ -1371,12 +1487,9 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
         if (w >= (unsigned)W) break;
         const unsigned start = range[2 * w], end = range[2 * w + 1];
         if (start >= end) continue;
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned *>(meta + 7), end - start);
         __syncwarp();
-        for (int a = lane; a < n; a += 32) {
-            const unsigned short p = orders[(size_t)w * n + a];
-            order[a] = p;
-            pos[p] = (unsigned short)a;
-        }
+        load_order(orders + (size_t)w * n, n, order, pos, lane);
         __syncwarp();
         const unsigned lanemask_le = 0xffffffffu >> (31 - lane);
         const unsigned lanemask_lt = lanemask_le >> 1;
@@ -1397,8 +1510,8 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
                 int gdy, gdx;
                 event_slope<XY_SMEM>(s_xy, g_xy, e0, gdy, gdx);
                 const unsigned g1 = group_end<XY_SMEM>(s_xy, g_xy, ev, k + 33, end, gdy, gdx, lane);
-                // one pass over the positions pays off for groups of about n/4 events or more
-                if (g1 - k >= (unsigned)n / 4)
+                // one pass over the positions pays off for groups of about n/2 events or more
+                if (g1 - k >= (unsigned)n / 2)
                     heavy_scan<XY_SMEM>(order, pos, s_xy, g_xy, n, h, gdy, gdx,
                                         ((unsigned)ev_i(e0) << 16) | (unsigned)ev_j(e0), lane, best);
                 else
@@ -1879,6 +1992,10 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
         StageTimer _t(STAGE_PLAN, st);
         if (plan) k_plan<<<(p.W + 7) / 8, 256, 0, st>>>(p.ev, p.base, p.meta, p.W, p.range);
         else k_snap_ranges<<<(2 * p.W + 7) / 8, 256, 0, st>>>(p.ev, p.base, p.meta, 2 * p.W, p.range);
+    }
+    {
+        StageTimer _t(STAGE_PLAN, st);
+        k_monotone_ranges<<<1, 1024, 0, st>>>(p.range, 2 * p.W);
     }
     return cudaGetLastError();
 }

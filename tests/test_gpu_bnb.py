@@ -79,3 +79,27 @@ def test_bnb_n8192_prunes_and_matches(L, orc):
     assert st["events_swept"] < st["events_total"] // 4, st
     r2, st2 = bnb(L, x, y, 0, None)
     assert not diff(r2, o), diff(r2, o)
+
+
+def test_bnb_equals_plain_sweep_on_many_instances(L):
+    """Both workload generators at n = 2048 .. 8192 over many seeds (fixed
+    slope 0.7 with its large equal-slope groups; random slopes with up to 45%
+    outliers): every seeding of the branch-and-bound (sample quantiles,
+    evenly spaced angles, a wildly wrong predicted slope) returns the plain
+    sweep's result bit for bit, and the sweep covers exactly the kept
+    events (a range left out is reported as LMS_ERR_INTERNAL)."""
+    cases = [("line", 8192, s, 0.4) for s in range(1, 25)]
+    cases += [("sloped", n, 500 + s, f) for s in range(12) for n, f in ((2048, 0.3), (8192, 0.45))]
+    for gen, n, seed, frac in cases:
+        if gen == "line":
+            x, y = datagen.line_with_outliers(n, seed, frac)
+        else:
+            x, y, _ = datagen.sloped(n, seed, frac, phi_max=1.4)
+        xt = torch.from_numpy(x).cuda()
+        yt = torch.from_numpy(y).cuda()
+        ref = L.decode(L.fit(xt, yt, 0, "sweep"))[0]
+        assert ref["status"] == L.LMS_OK, (gen, n, seed)
+        for mode, sd in (("quantiles", None), ("angles", None), ("quantiles", 40.0)):
+            r, st = bnb(L, x, y, 0, sd, mode)
+            assert {k: r[k] for k in F} == {k: ref[k] for k in F}, (gen, n, seed, mode, sd, r, ref)
+            assert st["events_swept"] <= st["events_total"]
