@@ -465,6 +465,75 @@ def _timed(fit, steps, warmup, flush, stream, barrier):
     return sum(a.elapsed_time(b) for a, b in ev)
 
 
+def batched_short(steps: int, warmup: int):
+    """The batch workload (4096 uneven sets) with a fixed plan (plain kernel up
+    to 128 points, 48 streams, branch-and-bound from 1536 points), captured
+    into one CUDA graph; each step replays it on a fresh batch already in HBM
+    (y coordinates of another seed), timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_1510_01041_gb300 import datagen, lms
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x0, y0, off = datagen.batch(4096, 5000)
+    # a second batch of the same set sizes: every y moved by a seeded U{-2..2}
+    y1 = (y0.astype(np.int64) + datagen.Stream(5001).integers(-2, 3, y0.size)).clip(-32768, 32767).astype(np.int16)
+    xt, yt, ot = (torch.from_numpy(a).to(dev) for a in (x0, y0, off))
+    ys = [torch.from_numpy(y0).to(dev), torch.from_numpy(y1).to(dev)]
+    plan = lms.BatchPlan(off, plain_max_n=128, streams=48, bnb_min_n=1536)
+    out = torch.empty((4096, lms.RESULT_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    plan.fit(xt, yt, ot, out=out)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.fit(xt, yt, ot, out=out, stream=s)
+    for k in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for k in range(steps):
+        yt.copy_(ys[k % len(ys)])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+    res = lms.decode(out)
+    assert all(r["status"] in (lms.LMS_OK, lms.LMS_ERR_VERTICAL) for r in res)
+    sizes = np.diff(off)
+    slopes = int(np.sum(sizes * (sizes - 1) // 2))
+    v = 4096 * steps / (ms / 1000.0)
+    return {"value": v, "unit": UNIT, "ms_per_step": ms / steps, "candidate_slopes_per_sec": v / 4096 * slopes,
+            "steps": steps, "warmup": warmup,
+            "workload": "4096 sets, n log-uniform [64,4096], outliers U(0,0.45), angle U(-1.5,1.5)",
+            "plan": "plain kernel <= 128 points, 48 streams, branch-and-bound >= 1536 points, one CUDA graph"}
+
+
+def hough_short(steps: int, warmup: int):
+    """The line-detection workload: 64 binary 2048x2048 edge images, Hough
+    votes into 1024 x 2896 bins, top-32 peaks, 4 px bands, exact LMS of all
+    2048 sets; wall time of the whole (synchronous) call, images in HBM."""
+    import torch
+
+    from paper_1510_01041_gb300 import datagen, lms
+    imgs = torch.from_numpy(datagen.edge_images(64, 1)).cuda()
+    for _ in range(warmup):
+        lms.hough_refine(imgs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        lines = lms.hough_refine(imgs)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    fitted = sum(1 for ln in lines if ln["fit"]["status"] == lms.LMS_OK)
+    return {"value": 64 / dt, "unit": "images/s", "ms_per_step": dt * 1e3, "lines_per_sec": fitted / dt,
+            "steps": steps, "warmup": warmup,
+            "workload": "64 x 2048x2048 edge images, 16 segments, 5% salt; 1024 theta x 2896 rho; top-32, 4 px band"}
+
+
 def node_bound_ops(n: int) -> int:
     """Algorithmic int32 instruction-equivalents of one slope interval's lower
     bound: projections of all points at both interval ends (4n, 4 ops each:
@@ -516,6 +585,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the short batch and Hough lines")
     ap.add_argument("--breakdown", action="store_true", help="per-stage times to stderr")
     ap.add_argument("--workload", choices=["single", "batched", "hough", "table1", "accuracy", "subsample"],
                     default="single",
@@ -601,18 +671,25 @@ def main():
     for v in stats.values():
         v.clear()
     ms, stages = {}, {}
-    lms.profile_read()
-    lms.profile_enable(True)
+    # timed passes without the library's per-launch profiling events
     with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
         launches0 = lms.launch_count()
         ms["learned"] = _timed(arms["learned"], args.steps, args.warmup, flush, stream, barrier)
         launches = lms.launch_count() - launches0
         wall = time.perf_counter() - wall0
-        stages["learned"] = lms.profile_read()
         for k in ("quantile", "plain", "learned2", "plain2"):
             ms[k] = _timed(arms[k], args.steps, args.warmup, flush, stream, barrier)
-            stages[k] = lms.profile_read()
+    # a second pass over the same steps with CUDA events around every launch,
+    # on the stream it runs on: per-kernel times for the stage table and the
+    # roofline (the events add a little time between launches, not inside them)
+    for v in stats.values():
+        v.clear()
+    lms.profile_read()
+    lms.profile_enable(True)
+    for k in ("learned", "quantile", "plain"):
+        _timed(arms[k], args.steps, args.warmup, flush, stream, barrier)
+        stages[k] = lms.profile_read()
     lms.profile_enable(False)
     ms = {k: max_over_ranks(v, dev) for k, v in ms.items()}
     res = {k: lms.decode(v)[args.warmup:] for k, v in outs.items()}
@@ -717,6 +794,9 @@ def main():
                                     sorted(stages["plain"].items(), key=lambda kv: -kv[1][0])},
         "wall_s": wall,
     }
+    if rank == 0 and ws == 1 and not args.no_extra:
+        line["batched"] = batched_short(3, 2)
+        line["hough"] = hough_short(3, 1)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, o = _cpu_baseline(*host[args.warmup])
         r = res["learned"][0]

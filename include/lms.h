@@ -139,19 +139,22 @@ typedef struct {
 
 /*
  * lms_fit_bnb -- exact LMS by branch-and-bound over slope intervals: an
- * upper bound from the exact window width at a few slopes, a lower bound
- * for every slope interval from the hulls of the projections over the
- * interval, intervals with lower bound > upper bound dropped, and the
- * surviving intervals swept exactly.  The result equals lms_fit's bit for
- * bit (ties are never pruned).
- *   seed_slope  device pointer to one float: a predicted slope; the upper
- *               bound is taken at the sampled slopes nearest it.  NULL: at
- *               evenly spaced sampled slopes instead.
+ * upper bound from the exact window width at a few rounds of slopes (each
+ * round zooming in on the narrowest window found so far), a lower bound for
+ * every slope interval from the hulls of the projections over the interval,
+ * intervals with lower bound > upper bound dropped, and the surviving
+ * intervals swept exactly.  The result equals lms_fit's bit for bit (ties
+ * are never pruned).
+ *   seed_slope  device pointer to one float: a predicted slope; half of the
+ *               first round's slopes are sampled slopes near it.  NULL: the
+ *               first round takes evenly spaced quantiles of the sampled
+ *               slopes (seed_mode 0) or evenly spaced angles (seed_mode 1).
  *   stats       host pointer (may be NULL).
- * Other arguments as lms_fit (int16 points, n <= 65536).  The call waits for
- * the stream between bisection levels and returns after the fit is done.
- * The first call on a host thread allocates about 272 KB of page-locked host
- * memory for its reads (kept for that thread until the process exits).
+ * Other arguments as lms_fit (int16 points, n <= 65536).  Every step,
+ * including the interval tree, runs on the device: with stats == NULL the
+ * call is asynchronous on `stream`; with stats it waits for the fit and
+ * fills them (the first such call on a host thread allocates 256 bytes of
+ * page-locked host memory, kept for that thread until the process exits).
  */
 LMS_API int lms_fit_bnb(const void *x, const void *y, int64_t n, int64_t h, const float *seed_slope,
                         const lms_options *opt, lms_result *out, lms_bnb_stats *stats, lms_stream_t stream);
@@ -209,8 +212,9 @@ LMS_API int lms_fit_learned_host(lms_setnet *net, const void *x, const void *y, 
  * lms_batch_plan_create sizes everything from the host offsets once: sets
  * with at most plain_max_n points (0 = 256, at most 256) go to one
  * persistent plain kernel over (set, run of slopes) work items in three
- * size classes; larger sets (up to 32768 points) each get the exact sweep,
- * spread over `streams` internal streams (0 = 8).  It allocates the plan's
+ * size classes; larger sets (up to 32768 points) each get the exact sweep
+ * of every slope or, from 1536 points on, the exact branch-and-bound, spread
+ * over `streams` internal streams (0 = 8).  It allocates the plan's
  * device memory and waits for the device.
  *   offsets_host  B + 1 offsets of the sets in the x/y arrays (host).
  *   h_host        per-set order statistic (NULL: floor(n/2) + 1 each).
@@ -223,6 +227,14 @@ LMS_API int lms_fit_learned_host(lms_setnet *net, const void *x, const void *y, 
 typedef struct lms_batch_plan lms_batch_plan;
 LMS_API int lms_batch_plan_create(const int64_t *offsets_host, int64_t B, const int32_t *h_host,
                                   int32_t plain_max_n, int32_t streams, lms_batch_plan **plan);
+/* The same with the size from which a set is fitted by the exact
+ * branch-and-bound (lms_fit_bnb's method, asynchronous, without statistics)
+ * instead of the sweep of every slope: bnb_min_n 0 = 1536 points (the value
+ * lms_batch_plan_create uses), > 0 = that size (at least 257), < 0 = never.
+ * The branch-and-bound's result equals the sweep's bit for bit. */
+LMS_API int lms_batch_plan_create_ex(const int64_t *offsets_host, int64_t B, const int32_t *h_host,
+                                     int32_t plain_max_n, int32_t streams, int32_t bnb_min_n,
+                                     lms_batch_plan **plan);
 LMS_API int lms_batch_plan_destroy(lms_batch_plan *plan);
 LMS_API size_t lms_batch_plan_bytes(const lms_batch_plan *plan);
 LMS_API int lms_fit_batched(lms_batch_plan *plan, const void *x, const void *y, const int64_t *offsets_dev,

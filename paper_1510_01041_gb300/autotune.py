@@ -1,5 +1,6 @@
 """Autotuner for batched fits: picks the size threshold between the plain
-kernel classes and the sweep, and the number of sweep streams, by timing
+kernel classes and the sweep, the number of sweep streams and the size from
+which sets take the branch-and-bound instead of the sweep, by timing
 CUDA-graph replays of a batch plan on the caller's own sets.  Results are
 cached per (device name, size mix) in autotune_cache.json next to this
 file, or in the file $LMS_AUTOTUNE_CACHE names.
@@ -24,6 +25,7 @@ CACHE = os.environ.get("LMS_AUTOTUNE_CACHE") or os.path.join(os.path.dirname(os.
                                                              "autotune_cache.json")
 PLAIN_MAX = (64, 128, 256)
 STREAMS = (8, 16, 32, 48)
+BNB_MIN = (1024, 1536, 2048, 3072, -1)   # -1: every large set takes the sweep of every slope
 
 
 def _key(offsets, device_name):
@@ -35,7 +37,7 @@ def _key(offsets, device_name):
     hist = np.histogram(np.log2(np.maximum(sizes, 2)), bins=128, range=(1, 17))[0]
     pairs = int(np.sum(sizes * (sizes - 1) // 2))
     h = hashlib.sha1(hist.tobytes() + device_name.encode()).hexdigest()[:16]
-    return f"{device_name}:{sizes.size}:{int(sizes.sum())}:{pairs}:{h}"
+    return f"v2:{device_name}:{sizes.size}:{int(sizes.sum())}:{pairs}:{h}"
 
 
 def _time_plan(plan, x, y, od, reps=2):
@@ -58,16 +60,30 @@ def _time_plan(plan, x, y, od, reps=2):
 
 
 def tune(offsets, x, y, offsets_dev, candidates=None):
-    """Time every candidate (plain_max_n, streams); returns the best config."""
+    """Time candidate plans (plain_max_n, streams, bnb_min_n); returns the
+    best config.  Coordinate search: the plain threshold and stream count at
+    the default branch-and-bound size, then the branch-and-bound size at the
+    best of those (or every given candidate)."""
     import torch
-    cands = candidates or [(p, s) for p in PLAIN_MAX for s in STREAMS]
     results = []
-    for pm, ns in cands:
-        plan = lms.BatchPlan(offsets, plain_max_n=pm, streams=ns)
+
+    def run(pm, ns, bm):
+        plan = lms.BatchPlan(offsets, plain_max_n=pm, streams=ns, bnb_min_n=bm)
         dt, _, _ = _time_plan(plan, x, y, offsets_dev, reps=1)
-        results.append(dict(plain_max_n=pm, streams=ns, seconds=dt))
+        results.append(dict(plain_max_n=pm, streams=ns, bnb_min_n=bm, seconds=dt))
         del plan
         torch.cuda.synchronize()
+
+    if candidates:
+        for c in candidates:
+            run(*c)
+    else:
+        for pm in PLAIN_MAX:
+            for ns in STREAMS:
+                run(pm, ns, 0)
+        b = min(results, key=lambda r: r["seconds"])
+        for bm in BNB_MIN:
+            run(b["plain_max_n"], b["streams"], bm)
     best = min(results, key=lambda r: r["seconds"])
     return best, results
 
@@ -92,4 +108,5 @@ def tuned_plan(offsets, x, y, offsets_dev, use_cache=True):
         except OSError as e:
             import warnings
             warnings.warn(f"autotune cache {CACHE} not written ({e}); set LMS_AUTOTUNE_CACHE to a writable path")
-    return lms.BatchPlan(offsets, plain_max_n=cfg["plain_max_n"], streams=cfg["streams"]), cfg
+    return lms.BatchPlan(offsets, plain_max_n=cfg["plain_max_n"], streams=cfg["streams"],
+                         bnb_min_n=cfg.get("bnb_min_n", 0)), cfg

@@ -189,6 +189,29 @@ int run_fit(const void *x, const void *y, int n, int h, int dtype, const lms_opt
 }
 
 }  // namespace
+
+int fit_bnb_after(const void *x, const void *y, int64_t n, int64_t h, const float *seed_slope, const lms_options *opt,
+                  lms_result *out, lms_bnb_stats *stats, cudaStream_t st, cudaEvent_t pred_ready)
+{
+    lms_options o = opt ? *opt : lms_options{};
+    o.algorithm = LMS_ALGO_BNB;
+    int rc = check_args(x, y, n, h, LMS_I16, &o, out);
+    if (rc) return rc;
+    int dev;
+    if (current_device(dev)) return LMS_ERR_CUDA;
+    Choice c;
+    rc = choose((int)n, (int)h, LMS_I16, &o, dev, c);
+    if (rc) return rc;
+    void *ws = nullptr;
+    rc = workspace(c.bytes, st, &ws);
+    if (rc) return rc;
+    SweepPlan p = c.sweep;
+    sweep_plan_carve(p, ws);
+    cudaGetLastError();
+    return run_bnb(p, (const short *)x, (const short *)y, seed_slope, o.seed_mode, out, stats,
+                   static_cast<unsigned char *>(ws) + c.bnb_off, c.sms, st, pred_ready);
+}
+
 }  // namespace lms
 
 using namespace lms;
@@ -245,24 +268,7 @@ int lms_fit_host(const void *x, const void *y, int64_t n, int64_t h, int32_t dty
 int lms_fit_bnb(const void *x, const void *y, int64_t n, int64_t h, const float *seed_slope,
                 const lms_options *opt, lms_result *out, lms_bnb_stats *stats, lms_stream_t stream)
 {
-    lms_options o = opt ? *opt : lms_options{};
-    o.algorithm = LMS_ALGO_BNB;
-    int rc = check_args(x, y, n, h, LMS_I16, &o, out);
-    if (rc) return rc;
-    int dev;
-    if (current_device(dev)) return LMS_ERR_CUDA;
-    Choice c;
-    rc = choose((int)n, (int)h, LMS_I16, &o, dev, c);
-    if (rc) return rc;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    void *ws = nullptr;
-    rc = workspace(c.bytes, st, &ws);
-    if (rc) return rc;
-    SweepPlan p = c.sweep;
-    sweep_plan_carve(p, ws);
-    cudaGetLastError();
-    return run_bnb(p, (const short *)x, (const short *)y, seed_slope, o.seed_mode, out, stats,
-                   static_cast<unsigned char *>(ws) + c.bnb_off, c.sms, st);
+    return fit_bnb_after(x, y, n, h, seed_slope, opt, out, stats, reinterpret_cast<cudaStream_t>(stream), nullptr);
 }
 
 size_t lms_workspace_size(int64_t n, int32_t dtype, const lms_options *opt)

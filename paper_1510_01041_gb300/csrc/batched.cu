@@ -21,6 +21,7 @@ namespace lms {
 namespace {
 
 constexpr int CHUNK = 64;   // slopes per work item of the plain kernel
+constexpr int BATCH_BNB_MIN_N = 1536;   // default size from which a set takes the branch-and-bound
 
 template <typename K>
 __device__ __forceinline__ void cxk(K &a, K &b)
@@ -248,6 +249,7 @@ struct lms_batch_plan {
     int dev = 0;
     int64_t B = 0;
     int plain_max = 256;
+    int bnb_min = 0;                    // sets of at least this many points take the branch-and-bound
     // plain classes (E = 2, 4, 8)
     struct Cls {
         int E = 0;
@@ -278,6 +280,12 @@ extern "C" {
 int lms_batch_plan_create(const int64_t *offsets_host, int64_t B, const int32_t *h_host, int32_t plain_max_n,
                           int32_t nstreams, lms_batch_plan **out)
 {
+    return lms_batch_plan_create_ex(offsets_host, B, h_host, plain_max_n, nstreams, 0, out);
+}
+
+int lms_batch_plan_create_ex(const int64_t *offsets_host, int64_t B, const int32_t *h_host, int32_t plain_max_n,
+                             int32_t nstreams, int32_t bnb_min_n, lms_batch_plan **out)
+{
     if (!offsets_host || B < 1 || !out) return LMS_ERR_ARG;
     *out = nullptr;
     for (int64_t i = 0; i < B; ++i) {
@@ -290,6 +298,10 @@ int lms_batch_plan_create(const int64_t *offsets_host, int64_t B, const int32_t 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev);
     p->B = B;
     p->plain_max = plain_max_n > 0 ? std::min(plain_max_n, 256) : 256;
+    // sets from this size on take the branch-and-bound (its fixed cost, a few
+    // hundred microseconds of seeds and bounds, pays off once the sweep of every
+    // slope costs more); negative: never
+    p->bnb_min = bnb_min_n > 0 ? std::max(bnb_min_n, 257) : (bnb_min_n < 0 ? 0x7fffffff : BATCH_BNB_MIN_N);
     p->off_host.assign(offsets_host, offsets_host + B + 1);
     p->hval.resize(B);
     for (int64_t i = 0; i < B; ++i) {
@@ -356,7 +368,9 @@ int lms_batch_plan_create(const int64_t *offsets_host, int64_t B, const int32_t 
         load[s] += n * n;
         SweepPlan sp;
         sweep_plan_configure(sp, (int)n, p->hval[p->sweep_sets[k]], sms, 0, 0, true);
-        need[s] = std::max(need[s], sweep_plan_bytes(sp));
+        size_t b = sweep_plan_bytes(sp);
+        if (n >= p->bnb_min) b = a256(b) + bnb_extra_bytes((int)n, sms);
+        need[s] = std::max(need[s], b);
     }
     p->streams.resize(ns);
     p->ev_done.resize(ns);
@@ -442,9 +456,15 @@ int lms_fit_batched(lms_batch_plan *p, const void *xv, const void *yv, const int
         SweepPlan sp;
         sweep_plan_configure(sp, n, p->hval[i], sms, 0, 0, true);
         sweep_plan_carve(sp, p->ws[s]);
-        failed = launch_sweep(sp, x + a, y + a, p->streams[s]) != cudaSuccess ||
-                 launch_argmin(sp.cands, sp.W + sp.G, out + i, LMS_ALGO_SWEEP, sp.meta + 3, p->streams[s]) !=
-                     cudaSuccess;
+        if (n >= p->bnb_min) {
+            // asynchronous without statistics: nothing waits on the host
+            unsigned char *extra = static_cast<unsigned char *>(p->ws[s]) + a256(sweep_plan_bytes(sp));
+            failed = run_bnb(sp, x + a, y + a, nullptr, 0, out + i, nullptr, extra, sms, p->streams[s]) != LMS_OK;
+        } else {
+            failed = launch_sweep(sp, x + a, y + a, p->streams[s]) != cudaSuccess ||
+                     launch_argmin(sp.cands, sp.W + sp.G, out + i, LMS_ALGO_SWEEP, sp.meta + 3, p->streams[s]) !=
+                         cudaSuccess;
+        }
     }
     // join every forked stream back to the caller's, also after a failed
     // launch, so the caller's stream stays ordered after all queued work

@@ -97,7 +97,60 @@ __device__ long long cta_min_window(const long long *top, const long long *bot, 
     return r;
 }
 
-// Upper bounds: exact w at dyadic slopes keys[q] (one CTA per slope).
+// CTA-wide minimum and maximum (every thread returns both).
+__device__ __forceinline__ void cta_min_max(long long &mn, long long &mx)
+{
+    __shared__ long long s_mn[32], s_mx[32];
+    for (int s = 16; s >= 1; s >>= 1) {
+        mn = min(mn, __shfl_xor_sync(FULL, mn, s));
+        mx = max(mx, __shfl_xor_sync(FULL, mx, s));
+    }
+    if ((threadIdx.x & 31) == 0) { s_mn[threadIdx.x >> 5] = mn; s_mx[threadIdx.x >> 5] = mx; }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    mn = s_mn[0];
+    mx = s_mx[0];
+    for (int w = 1; w < nw; ++w) { mn = min(mn, s_mn[w]); mx = max(mx, s_mx[w]); }
+    __syncthreads();
+}
+
+// Right shift that brings a span of values below 2^31: 32-bit sort keys
+// (v - lo) >> sh leave room for one unit of rounding up.
+__device__ __forceinline__ int key_shift(unsigned long long span)
+{
+    const int bits = span ? 64 - __clzll((long long)span) : 0;
+    return bits > 31 ? bits - 31 : 0;
+}
+
+// min over windows a of (top[a + h - 1] - bot[a]) for 32-bit keys, reduced over the CTA.
+__device__ long long cta_min_window32(const unsigned *top, const unsigned *bot, int n, int h)
+{
+    __shared__ long long s_red[32];
+    long long m = I64_MAX;
+    for (int a = threadIdx.x; a + h - 1 < n; a += blockDim.x)
+        m = min(m, (long long)top[a + h - 1] - (long long)bot[a]);
+    for (int s = 16; s >= 1; s >>= 1) m = min(m, __shfl_xor_sync(FULL, m, s));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = (threadIdx.x < (blockDim.x >> 5)) ? s_red[threadIdx.x] : I64_MAX;
+        for (int s = 16; s >= 1; s >>= 1) m = min(m, __shfl_xor_sync(FULL, m, s));
+        if (threadIdx.x == 0) s_red[0] = m;
+    }
+    __syncthreads();
+    const long long r = s_red[0];
+    __syncthreads();
+    return r;
+}
+
+// Upper bounds: the window width w at dyadic slopes keys[q] (one CTA per
+// slope).  In shared memory the projections are sorted as 32-bit keys
+// k = (Z - Zmin) >> sh, sh the smallest shift that brings their span below
+// 2^31; floor is monotone, so the sorted keys are the shifted order
+// statistics, and Z_(a+h-1) - Z_(a) < (k_(a+h-1) - k_(a) + 1) 2^sh.  The
+// result is w exactly when sh = 0 and otherwise an upper bound of w larger
+// by less than 2^sh units of 2^-32 (a few 10^-5 for slopes of order one),
+// which is all an upper bound needs.
 __global__ void __launch_bounds__(1024) k_score_dyadic(const int *__restrict__ xy, int n, int h,
                                                        const int *__restrict__ xcp,
                                                        const long long *__restrict__ keys, int nk,
@@ -114,15 +167,32 @@ __global__ void __launch_bounds__(1024) k_score_dyadic(const int *__restrict__ x
             if (threadIdx.x == 0) out[q] = I64_MAX;
             continue;
         }
-        long long *a = in_smem ? reinterpret_cast<long long *>(smem) : gscratch + (size_t)blockIdx.x * 2 * P;
         const int xc = *xcp;
-        auto z = [&](int k) { return k < n ? zscaled(xy[k], xc, K) : I64_MAX; };
-        const int Ps = P < (int)blockDim.x ? (int)blockDim.x : P;
-        if (!in_smem || !cta_fill_merge_sort_any(a, a + Ps, Ps, z)) {
-            for (int k = threadIdx.x; k < P; k += blockDim.x) a[k] = z(k);
+        if (in_smem) {
+            long long mn = I64_MAX, mx = -I64_MAX;
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                const long long z = zscaled(xy[k], xc, K);
+                mn = min(mn, z);
+                mx = max(mx, z);
+            }
+            cta_min_max(mn, mx);
+            const int sh = key_shift((unsigned long long)(mx - mn));
+            const int Ps = P < (int)blockDim.x ? (int)blockDim.x : P;
+            unsigned *a = reinterpret_cast<unsigned *>(smem);
+            auto key = [&](int k) {
+                return k < n ? (unsigned)((unsigned long long)(zscaled(xy[k], xc, K) - mn) >> sh) : 0xffffffffu;
+            };
+            cta_fill_merge_sort_any(a, a + Ps, Ps, key);
+            const long long wk = cta_min_window32(a, a, n, h);
+            if (threadIdx.x == 0) out[q] = sh ? (wk + 1) << sh : wk;
             __syncthreads();
-            cta_bitonic_i64(a, P);
+            continue;
         }
+        long long *a = gscratch + (size_t)blockIdx.x * 2 * P;
+        auto z = [&](int k) { return k < n ? zscaled(xy[k], xc, K) : I64_MAX; };
+        for (int k = threadIdx.x; k < P; k += blockDim.x) a[k] = z(k);
+        __syncthreads();
+        cta_bitonic_i64(a, P);
         const long long w = cta_min_window(a, a, n, h);
         if (threadIdx.x == 0) out[q] = w;
         __syncthreads();
@@ -130,6 +200,10 @@ __global__ void __launch_bounds__(1024) k_score_dyadic(const int *__restrict__ x
 }
 
 // Lower bounds of slope intervals [K_lo, K_hi] (keys) and the prune flags.
+// In shared memory the hull ends are sorted as 32-bit keys with the shift
+// of k_score_dyadic, rounded outward: lo down (floor), hi up (ceil), so
+// lo_(a+h-1) - hi_(a) >= (L_(a+h-1) - H_(a)) 2^sh and the bound stays a
+// lower bound (exact when sh = 0).
 __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, int n, int h,
                                                   const int *__restrict__ xcp,
                                                   const long long *__restrict__ node_keys,
@@ -150,28 +224,50 @@ __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, in
             if (threadIdx.x == 0) { prune[q] = 0; lb_out[q] = 0; }
             continue;
         }
-        const int Ps = (in_smem && P < (int)blockDim.x) ? (int)blockDim.x : P;
-        long long *lo = in_smem ? reinterpret_cast<long long *>(smem) : gscratch + (size_t)blockIdx.x * 2 * P;
-        long long *hi = lo + Ps;
         const int xc = *xcp;
-        auto zlo = [&](int k) {
-            return k < n ? min(zscaled(xy[k], xc, Klo), zscaled(xy[k], xc, Khi)) : I64_MAX;
-        };
-        auto zhi = [&](int k) {
-            return k < n ? max(zscaled(xy[k], xc, Klo), zscaled(xy[k], xc, Khi)) : I64_MAX;
-        };
-        if (!in_smem || !cta_fill_merge_sort_any(lo, hi + Ps, Ps, zlo) ||
-            !cta_fill_merge_sort_any(hi, hi + Ps, Ps, zhi)) {
+        long long lb;
+        if (in_smem) {
+            long long mn = I64_MAX, mx = -I64_MAX;
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                const long long za = zscaled(xy[k], xc, Klo), zb = zscaled(xy[k], xc, Khi);
+                mn = min(mn, min(za, zb));
+                mx = max(mx, max(za, zb));
+            }
+            cta_min_max(mn, mx);
+            const int sh = key_shift((unsigned long long)(mx - mn));
+            const unsigned long long up = (1ull << sh) - 1ull;
+            const int Ps = P < (int)blockDim.x ? (int)blockDim.x : P;
+            unsigned *lo = reinterpret_cast<unsigned *>(smem);
+            unsigned *hi = lo + Ps;
+            auto klo = [&](int k) {
+                if (k >= n) return 0xffffffffu;
+                const long long za = zscaled(xy[k], xc, Klo), zb = zscaled(xy[k], xc, Khi);
+                return (unsigned)((unsigned long long)(min(za, zb) - mn) >> sh);
+            };
+            auto khi = [&](int k) {
+                if (k >= n) return 0xffffffffu;
+                const long long za = zscaled(xy[k], xc, Klo), zb = zscaled(xy[k], xc, Khi);
+                return (unsigned)(((unsigned long long)(max(za, zb) - mn) + up) >> sh);
+            };
+            cta_fill_merge_sort_any(lo, hi + Ps, Ps, klo);
+            cta_fill_merge_sort_any(hi, hi + Ps, Ps, khi);
+            lb = cta_min_window32(lo, hi, n, h);
+            lb = lb < 0 ? 0 : lb << sh;
+        } else {
+            long long *lo = gscratch + (size_t)blockIdx.x * 2 * P;
+            long long *hi = lo + P;
             for (int k = threadIdx.x; k < P; k += blockDim.x) {
-                lo[k] = zlo(k);
-                hi[k] = zhi(k);
+                const long long za = k < n ? zscaled(xy[k], xc, Klo) : I64_MAX;
+                const long long zb = k < n ? zscaled(xy[k], xc, Khi) : I64_MAX;
+                lo[k] = min(za, zb);
+                hi[k] = max(za, zb);
             }
             __syncthreads();
             cta_bitonic_i64(lo, P);
             cta_bitonic_i64(hi, P);
+            lb = cta_min_window(lo, hi, n, h);
+            if (lb < 0) lb = 0;
         }
-        long long lb = cta_min_window(lo, hi, n, h);
-        if (lb < 0) lb = 0;
         if (threadIdx.x == 0) {
             lb_out[q] = lb;
             prune[q] = lb > *ub ? 1 : 0;
@@ -189,7 +285,13 @@ __global__ void k_min_ub(const long long *__restrict__ w, int nk, long long *__r
 }
 
 constexpr unsigned long long BNB_MIN_RANGE = 64;   // events per swept range, at least
-constexpr double PRED_WINDOW = 0.35;   // radians around a predicted slope angle
+#ifndef LMS_PRED_WINDOW
+#define LMS_PRED_WINDOW 0.35
+#endif
+#ifndef LMS_LEARNED_ROUNDS
+#define LMS_LEARNED_ROUNDS 3
+#endif
+constexpr double PRED_WINDOW = LMS_PRED_WINDOW;   // radians around a predicted slope angle
 
 // Seed slopes.  With a predicted slope: half of them evenly spaced quantiles
 // of the sampled slopes whose angle lies within PRED_WINDOW of the
@@ -319,7 +421,7 @@ int bnb_seeds(int sms) { return std::max(64, std::min(BNB_SEEDS_MAX, sms)); }
 constexpr int BNB_FIRST_NODES = 128;
 // Levels of the interval tree.  The split after the second-to-last level
 // makes every child a single bucket, so the last level leaves no node open.
-constexpr int BNB_LEVELS = 4;
+constexpr int BNB_LEVELS = 3;
 constexpr int TREE_THREADS = 1024;
 
 // Device-side state of one branch-and-bound fit (read back only for the
@@ -417,6 +519,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_first(const unsigned *__r
                                                              unsigned char *__restrict__ keep,
                                                              TreeState *__restrict__ ts)
 {
+    extern __shared__ unsigned s_base[];   // NB + 1 prefix values, for the searches
     __shared__ long long s_warp[32];
     __shared__ unsigned s_tot;
     const int NB = meta[0] + 1;
@@ -436,11 +539,11 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_first(const unsigned *__r
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
         const int b = b_beg + r;
-        if (b < NB) sbase[b] = run;
+        if (b < NB) sbase[b] = s_base[b] = run;
         run += loc[r];
     }
     if (threadIdx.x == blockDim.x - 1) {
-        sbase[NB] = (unsigned)incl;
+        sbase[NB] = s_base[NB] = (unsigned)incl;
         s_tot = (unsigned)incl;
     }
     for (int b = threadIdx.x; b < NB; b += blockDim.x) keep[b] = 0;
@@ -451,7 +554,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_first(const unsigned *__r
     const int k = threadIdx.x + 1;
     long long v = LLONG_MIN;
     if (k <= m0) {
-        int b = lower_bound_u(sbase, 0, NB + 1, E * (unsigned long long)k / (unsigned long long)m0);
+        int b = lower_bound_u(s_base, 0, NB + 1, E * (unsigned long long)k / (unsigned long long)m0);
         if (k == m0) b = NB;
         v = (long long)b - k;
     }
@@ -497,10 +600,16 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_step(int level, int sms, 
                                                             unsigned char *__restrict__ keep,
                                                             TreeState *__restrict__ ts)
 {
+    extern __shared__ unsigned s_base[];   // NB + 1 prefix values, for the searches
     __shared__ long long s_warp[32];
     __shared__ int s_F, s_total;
     const int NB = meta[0] + 1;
     const int nn = ts->count[level & 1];
+    if (nn == 0) {
+        if (threadIdx.x == 0) ts->count[(level + 1) & 1] = 0;
+        return;
+    }
+    for (int b = threadIdx.x; b <= NB; b += blockDim.x) s_base[b] = sbase[b];
     const bool last_split = level >= BNB_LEVELS - 2;
     // survivors that split, dropped nodes, kept single buckets
     int split = 0, dropped = 0;
@@ -546,7 +655,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_step(int level, int sms, 
         if (prune[k] || len <= 1) continue;
         const int parts = min(F, len);
         const int C = nd.y - parts;
-        const unsigned long long s0 = sbase[nd.x], s1 = sbase[nd.y];
+        const unsigned long long s0 = s_base[nd.x], s1 = s_base[nd.y];
         int carry = nd.x;   // u_{q-1} before the chunk (u_0 = b0)
         int mprev = nd.x;   // m'_{q-1}
         for (int q0 = 1; q0 <= parts; q0 += 32) {
@@ -554,7 +663,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_step(int level, int sms, 
             int v = INT_MIN;
             if (q <= parts) {
                 int m = nd.y;
-                if (q < parts) m = upper_bound_u(sbase, nd.x + 1, nd.y, s0 + (s1 - s0) * (unsigned long long)q / parts);
+                if (q < parts) m = upper_bound_u(s_base, nd.x + 1, nd.y, s0 + (s1 - s0) * (unsigned long long)q / parts);
                 v = min(m - q, C);
             }
 #pragma unroll
@@ -794,7 +903,7 @@ size_t bnb_extra_bytes(int n, int sms)
 // Levels left without nodes cost two empty launches.  With stats the call
 // waits for the fit to read them back; without, it returns at once.
 int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pred_dev, int seed_mode, lms_result *out,
-            lms_bnb_stats *stats, void *extra, int sms, cudaStream_t st)
+            lms_bnb_stats *stats, void *extra, int sms, cudaStream_t st, cudaEvent_t pred_ready)
 {
     const int n = p.n, h = p.h;
     unsigned char *cur = static_cast<unsigned char *>(extra);
@@ -830,21 +939,23 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         StageTimer _t(STAGE_SEEDS, st);
         k_x_center<<<1, 1024, 0, st>>>(p.xy, n, xc);
     }
+    if (pred_ready && cudaStreamWaitEvent(st, pred_ready, 0) != cudaSuccess) return LMS_ERR_CUDA;
     {
         StageTimer _t(STAGE_SEEDS, st);
         k_pick_seeds<<<1, 128, 0, st>>>(sorted_sample(p), p.S, pred_dev, seed_mode, KS, seed_keys);
     }
     const int Ps = P < 1024 ? 1024 : P;   // the shared-memory sorts fill whole 1024-thread CTAs
-    // one sorted array plus merge scratch; two sorted arrays plus scratch
-    const size_t one_sort = (n <= SORT_SMEM_N) ? (size_t)2 * Ps * 8 : 0;
-    const size_t two_sorts = (n <= SORT_SMEM_N) ? (size_t)3 * Ps * 8 : 0;
+    // 32-bit keys: one sorted array plus merge scratch; two sorted arrays plus scratch
+    const size_t one_sort = (n <= SORT_SMEM_N) ? (size_t)2 * Ps * 4 : 0;
+    const size_t two_sorts = (n <= SORT_SMEM_N) ? (size_t)3 * Ps * 4 : 0;
     cudaFuncSetAttribute(k_score_dyadic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one_sort);
     cudaFuncSetAttribute(k_node_lb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_sorts);
     {
         StageTimer _t(STAGE_SEEDS, st);
         k_score_dyadic<<<std::min(KS, grid), 1024, one_sort, st>>>(p.xy, n, h, xc, seed_keys, KS, seed_w, gscr);
     }
-    for (int r = 2; r <= BNB_ROUNDS; ++r) {
+    const int rounds = pred_dev ? LMS_LEARNED_ROUNDS : BNB_ROUNDS;
+    for (int r = 2; r <= rounds; ++r) {
         long long *keys_r = seed_keys + (size_t)(r - 1) * KS, *w_r = seed_w + (size_t)(r - 1) * KS;
         {
             StageTimer _t(STAGE_SEEDS, st);
@@ -857,12 +968,16 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     }
     {
         StageTimer _t(STAGE_SEEDS, st);
-        k_min_ub<<<1, 32, 0, st>>>(seed_w, KS * BNB_ROUNDS, ub);
+        k_min_ub<<<1, 32, 0, st>>>(seed_w, KS * rounds, ub);
     }
     // the interval tree, level by level, all on the device
+    const size_t tree_smem = (size_t)(BND_MAX + 1) * sizeof(unsigned);
+    cudaFuncSetAttribute(k_tree_first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tree_smem);
+    cudaFuncSetAttribute(k_tree_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tree_smem);
     {
         StageTimer _t(STAGE_NODE_LB, st);
-        k_tree_first<<<1, TREE_THREADS, 0, st>>>(scount, p.meta, p.bnd, sms, sbase, nodes[0], nkeys[0], keep, ts);
+        k_tree_first<<<1, TREE_THREADS, tree_smem, st>>>(scount, p.meta, p.bnd, sms, sbase, nodes[0], nkeys[0], keep,
+                                                          ts);
     }
     for (int L = 0; L < BNB_LEVELS; ++L) {
         {
@@ -872,8 +987,8 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         }
         {
             StageTimer _t(STAGE_NODE_LB, st);
-            k_tree_step<<<1, TREE_THREADS, 0, st>>>(L, sms, p.meta, p.bnd, sbase, nodes[L & 1], prune,
-                                                    nodes[(L + 1) & 1], nkeys[(L + 1) & 1], offs, keep, ts);
+            k_tree_step<<<1, TREE_THREADS, tree_smem, st>>>(L, sms, p.meta, p.bnd, sbase, nodes[L & 1], prune,
+                                                            nodes[(L + 1) & 1], nkeys[(L + 1) & 1], offs, keep, ts);
         }
     }
     {

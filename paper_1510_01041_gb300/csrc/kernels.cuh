@@ -160,8 +160,13 @@ size_t sweep_f32_extra_bytes(int n, int W);
 
 // ---------------------------------------------------------------- branch and bound
 size_t bnb_extra_bytes(int n, int sms);
+// pred_ready: when not null, an event the step that reads pred_dev waits for
+// (the prediction may be computed on another stream meanwhile).
 int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pred_dev, int seed_mode, lms_result *out,
-            lms_bnb_stats *stats, void *extra, int sms, cudaStream_t st);
+            lms_bnb_stats *stats, void *extra, int sms, cudaStream_t st, cudaEvent_t pred_ready = nullptr);
+// lms_fit_bnb with the event above
+int fit_bnb_after(const void *x, const void *y, int64_t n, int64_t h, const float *seed_slope, const lms_options *opt,
+                  lms_result *out, lms_bnb_stats *stats, cudaStream_t st, cudaEvent_t pred_ready);
 
 // ---------------------------------------------------------------- argmin
 cudaError_t launch_argmin(const Cand *cands, int count, lms_result *out, int algorithm, const int *err,

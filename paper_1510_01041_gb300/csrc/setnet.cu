@@ -306,6 +306,12 @@ __global__ void k_sum_loss(const float *__restrict__ state, int B, float *__rest
 
 using namespace lms;
 
+// {0, n}: the offsets of one set, for the forward pass of a single fit.
+__global__ void k_set_offsets(long long *off, long long n)
+{
+    if (threadIdx.x == 0) { off[0] = 0; off[1] = n; }
+}
+
 struct lms_setnet {
     int dev;
     int max_sets;
@@ -317,6 +323,8 @@ struct lms_setnet {
     long long *off1;                      // device, {0, n} for single fits
     short *hx, *hy;                       // device staging of host-buffer fits (65536 points each)
     lms_result *hres;                     // device result of host-buffer fits
+    cudaStream_t side;                    // the forward pass of a learned fit runs here ...
+    cudaEvent_t ev_fork, ev_join;         // ... beside the branch-and-bound's sampling stage
 };
 
 namespace {
@@ -401,6 +409,9 @@ void lms_setnet_destroy(lms_setnet *net)
     cudaFree(net->state); cudaFree(net->dout); cudaFree(net->pred); cudaFree(net->pool);
     cudaFree(net->loss); cudaFree(net->off1);
     cudaFree(net->hx); cudaFree(net->hy); cudaFree(net->hres);
+    if (net->side) cudaStreamDestroy(net->side);
+    if (net->ev_fork) cudaEventDestroy(net->ev_fork);
+    if (net->ev_join) cudaEventDestroy(net->ev_join);
     delete net;
 }
 
@@ -514,14 +525,29 @@ int lms_fit_learned(lms_setnet *net, const void *x, const void *y, int64_t n, in
 {
     if (!net || !x || !y || !out || n < 2) return LMS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const long long offs[2] = {0, (long long)n};
-    if (cudaMemcpyAsync(net->off1, offs, sizeof(offs), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (!net->side) {
+        if (cudaStreamCreateWithFlags(&net->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return LMS_ERR_CUDA;
+        }
+    }
+    // the forward pass runs on the net's side stream, forked from and joined
+    // back to `stream`: the branch-and-bound samples and sorts pair slopes
+    // meanwhile and waits for the prediction only where it picks its seeds
+    if (cudaEventRecord(net->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(net->side, net->ev_fork, 0) != cudaSuccess)
         return LMS_ERR_CUDA;
+    {
+        StageTimer _t(STAGE_SETNET, net->side);
+        k_set_offsets<<<1, 32, 0, net->side>>>(net->off1, n);
+    }
     int rc = lms_setnet_forward(net, (const int16_t *)x, (const int16_t *)y, (const int64_t *)net->off1, 1,
-                                net->pred, stream);
+                                net->pred, reinterpret_cast<lms_stream_t>(net->side));
     if (rc) return rc;
+    if (cudaEventRecord(net->ev_join, net->side) != cudaSuccess) return LMS_ERR_CUDA;
     // pred[2] is the predicted slope in the original frame
-    return lms_fit_bnb(x, y, n, h, net->pred + 2, opt, out, stats, stream);
+    return fit_bnb_after(x, y, n, h, net->pred + 2, opt, out, stats, st, net->ev_join);
 }
 
 int lms_fit_learned_host(lms_setnet *net, const void *x, const void *y, int64_t n, int64_t h,

@@ -186,7 +186,10 @@ __global__ void __launch_bounds__(1024) k_splitters(const long long *__restrict_
     int P2 = 1;
     while (P2 <= nbnd) P2 <<= 1;
     for (int k = nbnd + threadIdx.x; k < P2; k += blockDim.x) bnd[k] = KEY_INF;
-    if (threadIdx.x == 0) { meta[0] = nbnd; meta[1] = P2; meta[2] = 0; meta[3] = 0; meta[5] = 0; meta[6] = 0; }
+    if (threadIdx.x == 0) {
+        meta[0] = nbnd; meta[1] = P2; meta[2] = 0; meta[3] = 0; meta[5] = 0; meta[6] = 0;
+        meta[7] = 0;   // events covered by the sweep's ranges (start sorts and k_sweep add to it)
+    }
 }
 
 // ---------------------------------------------------------------- count / scatter
@@ -282,7 +285,11 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
 // resolves them 32 at a time, all lanes busy; the rest of the stack is
 // resolved after the last tile.  Counts, list and meta[5] / meta[6] are the
 // same as the combined pass would give (the list order may differ).
-constexpr int CNT_WARPS = CNT_THREADS / 32;
+// The restricted count runs 1024 threads per CTA: its shared arrays (bucket
+// bounds and counters) allow one CTA per SM, and its float tests are short
+// dependent chains, so the extra warps hide their latency.
+constexpr int RC_THREADS = 1024;
+constexpr int CNT_WARPS = RC_THREADS / 32;
 constexpr int CNT_STACK = 64;   // per warp: at most 31 left + 32 pushed
 
 template <class G>
@@ -314,7 +321,7 @@ __device__ __forceinline__ void resolve_pairs(const void *pts, const long long *
 }
 
 template <class G>
-__global__ void __launch_bounds__(CNT_THREADS) k_count_restricted(const void *__restrict__ pts, int n,
+__global__ void __launch_bounds__(RC_THREADS) k_count_restricted(const void *__restrict__ pts, int n,
                                                                   const long long *__restrict__ bnd,
                                                                   unsigned *__restrict__ hist,
                                                                   const unsigned char *__restrict__ keep,
@@ -341,7 +348,7 @@ __global__ void __launch_bounds__(CNT_THREADS) k_count_restricted(const void *__
     const int T = (n + TILE - 1) / TILE;
     const int ntiles = T * (T + 1) / 2;
     const int il = threadIdx.x & (TILE - 1);
-    constexpr int JPT = TILE * TILE / CNT_THREADS;
+    constexpr int JPT = TILE * TILE / RC_THREADS;
     const int jl0 = (threadIdx.x / TILE) * JPT;
     for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
         int bi, bj;
@@ -511,6 +518,35 @@ __device__ __forceinline__ bool ev_less(long long ka, unsigned ea, long long kb,
     return ka < kb || (ka == kb && pair_of(ea) < pair_of(eb));
 }
 
+// Merge of two sorted runs A, B of Hh words each (distinct words; B padded
+// with ~0) into the first m outputs, written as events with the "same slope
+// as the previous event" flag.  Every thread writes 16 consecutive outputs,
+// its start on the merge path found by a binary search on its diagonal.
+__device__ void merge_halves_to_events(const unsigned long long *A, const unsigned long long *B, int Hh, int m,
+                                       unsigned *__restrict__ out)
+{
+    const int d = (int)threadIdx.x * 16;
+    if (d >= m) return;
+    int lo = d > Hh ? d - Hh : 0, hi = d < Hh ? d : Hh;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] < B[d - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    int i = lo, j = d - lo;
+    unsigned long long prev = 0;
+    bool have_prev = false;
+    if (i > 0) { prev = A[i - 1]; have_prev = true; }
+    if (j > 0 && (!have_prev || B[j - 1] > prev)) { prev = B[j - 1]; have_prev = true; }
+    for (int o = d; o < d + 16 && o < m; ++o) {
+        const bool take_a = j >= Hh || (i < Hh && A[i] < B[j]);
+        const unsigned long long v = take_a ? A[i++] : B[j++];
+        const bool cont = have_prev && (prev >> 32) == (v >> 32);
+        out[o] = ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), cont);
+        prev = v;
+        have_prev = true;
+    }
+}
+
 // Sort each bucket by (exact slope key, pair); buckets with more than
 // SEG_CAP events are listed for k_segsort_big.  A bucket holding a single
 // slope only needs its smallest pair moved to the front.
@@ -584,6 +620,17 @@ __global__ void __launch_bounds__(1024) k_segsort(const void *__restrict__ xy, u
             };
             __syncthreads();
             const int Pw = P < (int)blockDim.x ? (int)blockDim.x : P;
+            if (2 * Pw > SEG_CAP * 3 / 2 && Pw == 2 * (int)blockDim.x * 8) {
+                // too large for one merge sort and its scratch: two halves are
+                // merge-sorted one after the other (scratch after both), then
+                // merged by merge path straight into the event array
+                const int Hh = Pw / 2;
+                unsigned long long *A = w, *Bw = w + Hh, *scr = w + 2 * Hh;
+                cta_fill_merge_sort<8>(A, scr, Hh, word);
+                cta_fill_merge_sort<8>(Bw, scr, Hh, [&](int k) { return word(Hh + k); });
+                merge_halves_to_events(A, Bw, Hh, (int)m, ev + off);
+                continue;
+            }
             // merge sort (registers, then merge-path levels) where its scratch
             // copy fits beside the words, else the register-blocked bitonic sort
             const bool sorted = 2 * Pw <= SEG_CAP * 3 / 2 ? cta_fill_merge_sort_any(w, w + Pw, Pw, word)
@@ -744,11 +791,13 @@ __global__ void __launch_bounds__(1024) k_segsort_big(const void *__restrict__ x
 }
 
 // ---------------------------------------------------------------- plan
-constexpr unsigned SNAP_SCAN = 4096;   // events searched for a group start before the bucket end is taken
+constexpr unsigned SNAP_SCAN = 4096;   // events searched for a group start before the bucket start is taken
 
-// First event at or after t that starts a group of equal slopes (t itself if
-// it does), found by one warp inside t's bucket.  A group never spans two
-// buckets, so the bucket's end is always a valid answer; it is taken when no
+// Last event at or before t that starts a group of equal slopes (t itself if
+// it does), found by one warp inside t's bucket: a range then begins with a
+// whole group, which its start sort applies at once (a long group of one
+// slope costs nothing to sweep there).  A group never spans two buckets, so
+// the bucket's first event is always a valid answer; it is taken when no
 // start turns up within SNAP_SCAN events.  Every lane returns the same value.
 __device__ unsigned snap_group_start(const unsigned *__restrict__ ev, const unsigned *__restrict__ base, int NB,
                                      unsigned t, int lane)
@@ -760,17 +809,17 @@ __device__ unsigned snap_group_start(const unsigned *__restrict__ ev, const unsi
         const int mid = (lo + hi) >> 1;
         if (base[mid] <= t) lo = mid; else hi = mid;
     }
-    const unsigned be = base[hi];
-    for (unsigned q = t; q < be && q - t < SNAP_SCAN; q += 32) {
-        const unsigned u = q + lane;
-        const unsigned bal = __ballot_sync(FULL, u < be && !ev_cont(ev[u]));
-        if (bal) return q + __ffs(bal) - 1;
+    const long long bs = base[lo];
+    for (long long top = (long long)t + 1; top > bs && (long long)t + 1 - top < SNAP_SCAN; top -= 32) {
+        const long long u = top - 32 + lane;
+        const unsigned bal = __ballot_sync(FULL, u >= bs && u < top && !ev_cont(ev[u]));
+        if (bal) return (unsigned)(top - 32 + (31 - __clz(bal)));
     }
-    return be;
+    return (unsigned)bs;
 }
 
 // Range r covers the events [s(E r / W), s(E (r + 1) / W)), s = the snap to
-// a group start above: equal event counts up to the group granularity.  One
+// a group start below: equal event counts up to the group granularity.  One
 // warp per range.
 __global__ void k_plan(const unsigned *__restrict__ ev, const unsigned *__restrict__ base,
                        const int *__restrict__ meta, int W, unsigned *__restrict__ range)
@@ -801,7 +850,7 @@ __global__ void k_snap_ranges(const unsigned *__restrict__ ev, const unsigned *_
 
 // The snapped bounds are group starts but need not be monotone: a bound
 // deep inside a group longer than SNAP_SCAN events moves to its bucket's
-// end, one near the group's end to the group's end.  A running maximum over
+// start, one near the group's start to the group's start.  A running maximum over
 // the bounds in order (start_0, end_0, start_1, ...) makes them monotone:
 // every value is still a group start, a raised start only drops events that
 // the previous range already covers, and the ranges become disjoint, so every
@@ -884,22 +933,34 @@ __device__ void cta_bitonic_kv(unsigned long long *a, unsigned short *pay, int P
 }
 
 // Packed sort word of one point at the start slope: (key + 2^32) in bits
-// 63..31, (x + 2^15) in bits 30..15, point index in bits 14..0.  Ascending
-// words order the points by projection, then x ascending, then index: the
-// order just before the slope (a line of that slope lists its points by
-// increasing x).  For int16 points |key| < 2^32 and n <= 32768 here, so
-// the fields never overlap.
+// 63..31, (2^15 - 1 - x) in bits 30..15, point index in bits 14..0.
+// Ascending words order the points by projection, then x descending, then
+// index: the order just after the slope (a line of that slope lists its
+// points by decreasing x), which is the order once the range's first group
+// of events has been applied.  For int16 points |key| < 2^32 and
+// n <= 32768 here, so the fields never overlap.
 __device__ __forceinline__ unsigned long long order_word(long long key, int x, int k)
 {
-    return ((unsigned long long)(key + (1LL << 32)) << 31) | ((unsigned long long)(unsigned)(x + 32768) << 15) |
+    return ((unsigned long long)(key + (1LL << 32)) << 31) | ((unsigned long long)(unsigned)(32767 - x) << 15) |
            (unsigned long long)(unsigned)k;
 }
+
+template <bool XY_SMEM>
+__device__ unsigned group_end(const int *s_xy, const int *__restrict__ g_xy, const unsigned *__restrict__ ev,
+                              unsigned known, unsigned end, int dy0, int dx0, int lane);
 __device__ __forceinline__ long long word_key(unsigned long long w) { return (long long)(w >> 31) - (1LL << 32); }
 __device__ __forceinline__ int word_index(unsigned long long w) { return (int)(w & 0x7fffu); }
 
+// Start of a sweep range: the points sorted in the order just after the
+// range's first slope, every window scored at that slope (with the smallest
+// pair of its group), and the range's start moved past that first group:
+// its events only reverse the blocks of equal projections, which the
+// just-after order already does, and a window's width at the slope does not
+// depend on the order inside a block.  The events of the skipped group count
+// as covered (meta[7]).
 __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy, int n, int h,
                                                      const unsigned *__restrict__ ev,
-                                                     const unsigned *__restrict__ range, int W,
+                                                     unsigned *__restrict__ range, int W,
                                                      int *__restrict__ meta_mut,
                                                      const unsigned *__restrict__ base,
                                                      unsigned short *__restrict__ orders,
@@ -919,7 +980,6 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
     const bool vertical = (E == 0 && w == 0);
     if (w == 0 && threadIdx.x == 0) {
         meta_mut[4] = 0;          // range counter of k_sweep
-        meta_mut[7] = 0;          // events the sweep's ranges cover, summed by k_sweep
         meta_mut[8] = (int)E;     // events to cover (checked by the final reduction)
     }
     if (start >= end && !vertical) {
@@ -939,13 +999,19 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
     }
     __syncthreads();
     const int dy = s_slope[0], dx = s_slope[1];
+    // end of the range's first group of equal slopes (warp 0)
+    __shared__ unsigned s_g1;
+    if (warp == 0) {
+        const unsigned g1 = vertical ? end : group_end<false>(nullptr, xy, ev, start + 1, end, dy, dx, lane);
+        if (lane == 0) s_g1 = g1;
+    }
     auto word = [&](int k) {
         if (k >= n) return ~0ull;
         const int pk = xy[k];
         return order_word(proj(pk, dy, dx), px(pk), k);
     };
     // above 32768 points the index needs 16 bits: the word then holds
-    // (key + 2^32, x + 2^15) and the index travels in a payload array (equal
+    // (key + 2^32, 2^15 - 1 - x) and the index travels in a payload array (equal
     // words are identical points, whose order is immaterial)
     const bool wide = n > 32768;
     unsigned short *pay = wide ? reinterpret_cast<unsigned short *>(gsort + (size_t)W * P) + (size_t)w * P : nullptr;
@@ -953,7 +1019,7 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
         for (int k = threadIdx.x; k < P; k += blockDim.x) {
             if (k < n) {
                 const int pk = xy[k];
-                a[k] = ((unsigned long long)(proj(pk, dy, dx) + (1LL << 32)) << 16) | (unsigned)(px(pk) + 32768);
+                a[k] = ((unsigned long long)(proj(pk, dy, dx) + (1LL << 32)) << 16) | (unsigned)(32767 - px(pk));
             } else {
                 a[k] = ~0ull;
             }
@@ -1013,6 +1079,10 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
             c.i = vertical ? -1 : (int)(mp >> 16);
             c.j = vertical ? -1 : (int)(mp & 0xffffu);
             cands[w] = c;
+            if (!vertical) {
+                range[2 * w] = s_g1;
+                atomicAdd(reinterpret_cast<unsigned *>(meta_mut + 7), s_g1 - start);
+            }
         }
     }
 }
@@ -1027,6 +1097,9 @@ __device__ __forceinline__ int load_xy(const int *s_xy, const int *__restrict__ 
 __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 constexpr int RUN_LANE_MAX = 24;   // runs up to this length are handled by one lane
+#ifndef LMS_SWEEP_XY_SMEM_MAX
+#define LMS_SWEEP_XY_SMEM_MAX 16384     // the sweep keeps the packed points in shared memory up to this n
+#endif
 
 // A range's start order (global, written by k_sweep_init) into the warp's
 // order and position arrays.  When n is a multiple of 8 the order is read as
@@ -1080,8 +1153,11 @@ constexpr bool SWEEP_SERIAL = SWEEP_SERIAL_DEFAULT;   // every batch one event a
 #endif
 // A parallel batch costs about as much as several events applied one at a time:
 // after a batch that advanced fewer than SERIAL_BELOW events, the next
-// SERIAL_CHUNKS batches are applied one event at a time.
+// SERIAL_CHUNKS batches are applied one event at a time; every further such
+// batch in a row doubles that count (up to SERIAL_CHUNKS_MAX), and a batch that
+// advances well resets it, so stretches of chained events try few batches.
 constexpr int SERIAL_BELOW = SWEEP_SERIAL_BELOW, SERIAL_CHUNKS = SWEEP_SERIAL_CHUNKS;
+constexpr int SERIAL_CHUNKS_MAX = 8 * SWEEP_SERIAL_CHUNKS;
 
 // A whole group of one slope dy/dx in one pass over the positions, for
 // groups of about n/2 events or more.  Two points with equal projections at
@@ -1495,6 +1571,7 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
         const unsigned lanemask_lt = lanemask_le >> 1;
         unsigned carried = 0xffffffffu;   // smallest pair of the group open at k
         int serial_left = SERIAL ? 1 << 30 : 0;   // batches still to be applied one event at a time
+        int serial_next = SERIAL_CHUNKS;            // serial batches after the next short parallel one
         unsigned k = start;
         unsigned e_cur = (k + lane < end) ? ev[k + lane] : 0u;
         unsigned e_nxt = (k + 32 + lane < end) ? ev[k + 32 + lane] : 0u;
@@ -1755,7 +1832,12 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
             carried = __shfl_sync(FULL, gmin, advance - 1);
             // chains of events that share points cut batches short; there one
             // event at a time is cheaper than a parallel step
-            if (advance < SERIAL_BELOW) serial_left = SERIAL_CHUNKS;
+            if (advance < SERIAL_BELOW) {
+                serial_left = serial_next;
+                serial_next = min(2 * serial_next, SERIAL_CHUNKS_MAX);
+            } else {
+                serial_next = SERIAL_CHUNKS;
+            }
             // slide the 64-event window by `advance`
             const int src = (lane + advance) & 31;
             const unsigned c1 = __shfl_sync(FULL, e_cur, src);
@@ -1790,7 +1872,7 @@ void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int w
     p.n = n;
     p.h = h;
     p.emax = (long long)n * (n - 1) / 2;
-    p.xy_smem = n <= 16384;
+    p.xy_smem = n <= LMS_SWEEP_XY_SMEM_MAX;
     // sweeping warps per CTA limited by shared memory (order + pos each;
     // order alone when both do not fit, the positions then in global memory)
     const size_t half = ((size_t)n * 2 + 15) / 16 * 16;
@@ -1920,7 +2002,7 @@ static cudaError_t events_count(const SweepPlan &p, const void *pts, const unsig
     if (pre) {
         cudaFuncSetAttribute(k_count_restricted<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
         StageTimer _t(STAGE_COUNT_PAIRS, st);
-        k_count_restricted<G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, p.n, p.bnd, p.hist, keep, pre, npre, p.meta,
+        k_count_restricted<G><<<p.C, RC_THREADS, cnt_smem, st>>>(pts, p.n, p.bnd, p.hist, keep, pre, npre, p.meta,
                                                                   p.ev2);
     } else {
         cudaFuncSetAttribute(k_bucket_pairs<false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);

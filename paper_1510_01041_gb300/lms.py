@@ -437,12 +437,14 @@ def pretrained(path: str = WEIGHTS, seed: int = 1) -> SetNet:
 class BatchPlan:
     """lms_batch_plan for a fixed list of set sizes (CSR offsets)."""
 
-    def __init__(self, offsets, h=None, plain_max_n: int = 0, streams: int = 0):
+    def __init__(self, offsets, h=None, plain_max_n: int = 0, streams: int = 0, bnb_min_n: int = 0):
         L = lib()
         if not getattr(L, "_batch_ready", False):
             vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
             L.lms_batch_plan_create.argtypes = [vp, i64, vp, i32, i32, ctypes.POINTER(ctypes.c_void_p)]
             L.lms_batch_plan_create.restype = ctypes.c_int
+            L.lms_batch_plan_create_ex.argtypes = [vp, i64, vp, i32, i32, i32, ctypes.POINTER(ctypes.c_void_p)]
+            L.lms_batch_plan_create_ex.restype = ctypes.c_int
             L.lms_batch_plan_destroy.argtypes = [vp]
             L.lms_batch_plan_destroy.restype = ctypes.c_int
             L.lms_batch_plan_bytes.argtypes = [vp]
@@ -455,9 +457,9 @@ class BatchPlan:
         self.B = self.offsets.size - 1
         hh = None if h is None else np.ascontiguousarray(h, dtype=np.int32)
         handle = ctypes.c_void_p()
-        rc = L.lms_batch_plan_create(ctypes.c_void_p(self.offsets.ctypes.data), self.B,
-                                     ctypes.c_void_p(hh.ctypes.data) if hh is not None else None,
-                                     int(plain_max_n), int(streams), ctypes.byref(handle))
+        rc = L.lms_batch_plan_create_ex(ctypes.c_void_p(self.offsets.ctypes.data), self.B,
+                                        ctypes.c_void_p(hh.ctypes.data) if hh is not None else None,
+                                        int(plain_max_n), int(streams), int(bnb_min_n), ctypes.byref(handle))
         if rc != LMS_OK:
             raise LmsError(rc, "lms_batch_plan_create")
         self.h = handle

@@ -68,14 +68,19 @@ def csr(sets, idx, device):
     return (torch.from_numpy(xs).to(device), torch.from_numpy(ys).to(device), torch.from_numpy(off).to(device))
 
 
-def angle_error(net, sets, targets, device, batch=64):
+def angle_errors(net, sets, targets, device, batch=64):
+    """Absolute angle errors (radians) of the network's predictions."""
     errs = []
     for s in range(0, len(sets), batch):
         idx = list(range(s, min(len(sets), s + batch)))
         x, y, off = csr(sets, idx, device)
         pred = net.forward(x, y, off).cpu().numpy()
         errs.append(np.abs(pred[:, 0] - targets[idx, 0]))
-    return float(np.mean(np.concatenate(errs)))
+    return np.concatenate(errs)
+
+
+def angle_error(net, sets, targets, device, batch=64):
+    return float(np.mean(angle_errors(net, sets, targets, device, batch)))
 
 
 def main():
@@ -116,12 +121,15 @@ def main():
             hist.append((step, float(loss.item())))
     torch.cuda.synchronize()
     t_train = time.time() - t1
-    err = angle_error(net, val, tval, device)
+    errs = angle_errors(net, val, tval, device)
+    err = float(np.mean(errs))
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     net.save(args.out)
     summary = dict(train_sets=args.sets, val_sets=args.val, n_range=[256, args.n_max], steps=args.steps,
                    batch=args.batch, lr=args.lr, lam=args.lam, seed=args.seed,
                    val_angle_mae_rad_untrained=base_err, val_angle_mae_rad=err,
+                   val_angle_err_rad_median=float(np.median(errs)),
+                   val_angle_err_rad_p90=float(np.percentile(errs, 90)),
                    loss_history=hist, solve_seconds=t_solve, train_seconds=t_train)
     with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
         json.dump(summary, f, indent=1)
