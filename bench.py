@@ -567,10 +567,11 @@ def _roof(stage, stages, units_per_fit, ops_per_unit, fits, peak_tops, mhz_basis
 
 
 # Kernels of the timed paths: the stage name the library's profiler uses,
-# the kernel, and its DRAM traffic per launch from the ncu captures under
-# profiles/ (None when the kernel changed after its capture).
+# the kernel, and its DRAM traffic per launch (dram__bytes_read.sum +
+# dram__bytes_write.sum) from the ncu captures summarised under profiles/;
+# a kernel changed after its capture has no entry.
 KERNEL_OF_STAGE = {"sweep": "k_sweep", "node_bounds": "k_node_lb", "count": "k_count_restricted"}
-DRAM_BYTES = {}
+DRAM_BYTES = {"k_node_lb": 116_992, "k_sweep": 1_958_400, "k_sweep_plain": 194_599_168}
 
 
 def _instances(seeds):

@@ -113,8 +113,8 @@ struct SweepPlan {
     unsigned *base;            // [BND_MAX + 1] bucket starts; base[NB] = E
     int *oversize;             // [BND_MAX] buckets too large for the shared-memory sort
     unsigned *ev;              // [emax] events
-    unsigned *ev2;             // [emax] merge copy for buckets above SEG_CAP (null if emax <= SEG_CAP);
-                               //        before the bucket sorts, the list of kept pairs of a restricted count
+    unsigned *ev2;             // [emax] merge copy for buckets above SEG_CAP; before the bucket sorts,
+                               //        the list of kept pairs of a restricted count
     unsigned *range;           // [2W] range event bounds
     unsigned short *orders;    // [W][n] start orders
     unsigned long long *gsort; // [W][P] global sort scratch when n > SORT_SMEM_N

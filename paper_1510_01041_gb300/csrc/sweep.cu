@@ -196,32 +196,49 @@ __global__ void __launch_bounds__(1024) k_splitters(const long long *__restrict_
 // Float pre-test of a restricted pass: 0 when x_i == x_j (no slope), 1 when
 // the slope lies outside every cover, 2 for a candidate.  The restricted
 // count and the restricted scatter both call it, so they keep the same pairs.
-// Pi: the packed point i (int16 points only).
+// Pi: the packed point i (int16 points only); cov: PRE_MAX covers in shared
+// memory (sorted, disjoint, rounded outward, unused ones at +inf).  For int16
+// points the slope is never divided out: with dx > 0, lo <= dy / dx is
+// tested as lo dx <= dy in float (dx, dy exact, one rounding of relative size
+// 2^-24 per product, far inside the covers' margin of 2^-18 relative): the
+// last cover whose lower end the slope reaches, found by a binary search,
+// must reach past it.
 template <class G>
-__device__ __forceinline__ int pre_test(const void *pts, int Pi, int i, int j, const float2 *s_pre)
+__device__ __forceinline__ int pre_test(const void *pts, int Pi, int i, int j, const float2 *cov)
 {
-    float sl;
-    if constexpr (std::is_same<G, KeyI16>::value) {
-        // dy / dx by the fast division (relative error below 2^-21; exact
-        // small-integer operands)
-        const int Pj = __ldg(static_cast<const int *>(pts) + j);
-        const int dx = px(Pj) - px(Pi);
-        if (dx == 0) return 0;
-        sl = __fdividef((float)(py(Pj) - py(Pi)), (float)dx);
-    } else {
-        if (!G::approx(pts, i, j, sl)) return 0;
-    }
-    // the last cover starting at or below sl must reach it
     int c = 0;
+    if constexpr (std::is_same<G, KeyI16>::value) {
+        const int Pj = __ldg(static_cast<const int *>(pts) + j);
+        int dx = px(Pj) - px(Pi), dy = py(Pj) - py(Pi);
+        if (dx == 0) return 0;
+        if (dx < 0) { dx = -dx; dy = -dy; }
+        const float fx = (float)dx, fy = (float)dy;
 #pragma unroll
-    for (int step = PRE_MAX; step >= 1; step >>= 1)
-        if (s_pre[c + step - 1].x <= sl) c += step;
-    return (c > 0 && sl <= s_pre[c - 1].y) ? 2 : 1;
+        for (int step = PRE_MAX; step >= 1; step >>= 1)
+            if (cov[c + step - 1].x * fx <= fy) c += step;
+        return (c > 0 && fy <= cov[c - 1].y * fx) ? 2 : 1;
+    } else {
+        float sl;
+        if (!G::approx(pts, i, j, sl)) return 0;
+#pragma unroll
+        for (int step = PRE_MAX; step >= 1; step >>= 1)
+            if (cov[c + step - 1].x <= sl) c += step;
+        return (c > 0 && sl <= cov[c - 1].y) ? 2 : 1;
+    }
+}
+
+// The covers of a restricted pass in shared memory: the first npre entries
+// of pre, then +inf (2 PRE_MAX entries, so the search never reads past).
+__device__ __forceinline__ void load_covers(const float2 *__restrict__ pre, int npre, float2 *s_cov)
+{
+    if (threadIdx.x < 2 * PRE_MAX)
+        s_cov[threadIdx.x] = (int)threadIdx.x < npre ? pre[threadIdx.x] : make_float2(INFINITY, INFINITY);
 }
 
 // Both passes walk the same upper-triangle tiles in the same static order,
-// so the scatter's per-CTA bucket cursors match the counts exactly (the
-// restricted count, k_count_restricted, walks them in the same order too).
+// so the scatter's per-CTA bucket cursors match the counts exactly.  (A
+// restricted fit counts with k_count_restricted, which lists its pairs; the
+// scatter then places the list, k_scatter_list, whatever the tiling.)
 template <bool SCATTER, class G>
 __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__restrict__ pts, int n,
                                                               const long long *__restrict__ bnd,
@@ -235,11 +252,10 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
     unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
-    __shared__ float2 s_pre[2 * PRE_MAX];   // covers sorted and disjoint, padded with lower bound +inf
+    __shared__ float2 s_cov[2 * PRE_MAX];
+    if (pre) load_covers(pre, npre, s_cov);
     const int nbnd = meta[0], P2 = meta[1], NB = nbnd + 1;
     for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
-    if (threadIdx.x < 2 * PRE_MAX)
-        s_pre[threadIdx.x] = threadIdx.x < npre ? pre[threadIdx.x] : make_float2(INFINITY, INFINITY);
     unsigned *my_hist = hist + (size_t)blockIdx.x * BND_MAX;
     for (int k = threadIdx.x; k < NB; k += blockDim.x)
         s_cnt[k] = SCATTER ? base[k] + my_hist[k] : 0u;
@@ -261,7 +277,7 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
         for (int jj = 0; jj < JPT; ++jj) {
             const int j = bj * TILE + jl0 + jj;
             if (j <= i || j >= n) continue;
-            if (pre && pre_test<G>(pts, Pi, i, j, s_pre) != 2) continue;
+            if (pre && pre_test<G>(pts, Pi, i, j, s_cov) != 2) continue;
             long long key;
             if (!G::key(pts, i, j, key)) continue;
             const int b = bucket_of(s_bnd, P2, key);
@@ -289,6 +305,10 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
 // bounds and counters) allow one CTA per SM, and its float tests are short
 // dependent chains, so the extra warps hide their latency.
 constexpr int RC_THREADS = 1024;
+#ifndef LMS_RC_TILE
+#define LMS_RC_TILE 128
+#endif
+constexpr int RC_TILE = LMS_RC_TILE;   // pair tile edge of the restricted count
 constexpr int CNT_WARPS = RC_THREADS / 32;
 constexpr int CNT_STACK = 64;   // per warp: at most 31 left + 32 pushed
 
@@ -332,12 +352,11 @@ __global__ void __launch_bounds__(RC_THREADS) k_count_restricted(const void *__r
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
     unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
-    __shared__ float2 s_pre[2 * PRE_MAX];   // covers sorted and disjoint, padded with lower bound +inf
     __shared__ unsigned s_stack[CNT_WARPS][CNT_STACK];
+    __shared__ float2 s_cov[2 * PRE_MAX];
+    load_covers(pre, npre, s_cov);
     const int P2 = meta[1], NB = meta[0] + 1;
     for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
-    if (threadIdx.x < 2 * PRE_MAX)
-        s_pre[threadIdx.x] = threadIdx.x < npre ? pre[threadIdx.x] : make_float2(INFINITY, INFINITY);
     for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -345,25 +364,27 @@ __global__ void __launch_bounds__(RC_THREADS) k_count_restricted(const void *__r
     const unsigned below = (1u << lane) - 1u;
     int top = 0;   // warp-uniform stack height
     unsigned nvalid = 0;
-    const int T = (n + TILE - 1) / TILE;
+    // tiles of RC_TILE x RC_TILE pairs: 16 per thread, so the tile decode and
+    // the row point's load are spread over more tests
+    const int T = (n + RC_TILE - 1) / RC_TILE;
     const int ntiles = T * (T + 1) / 2;
-    const int il = threadIdx.x & (TILE - 1);
-    constexpr int JPT = TILE * TILE / RC_THREADS;
-    const int jl0 = (threadIdx.x / TILE) * JPT;
+    const int il = threadIdx.x & (RC_TILE - 1);
+    constexpr int JPT = RC_TILE * RC_TILE / RC_THREADS;
+    const int jl0 = (threadIdx.x / RC_TILE) * JPT;
     for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
         int bi, bj;
         tile_decode(q, bi, bj);
-        const int i = bi * TILE + il;
+        const int i = bi * RC_TILE + il;
         const bool row = i < n;
         int Pi = 0;
         if constexpr (std::is_same<G, KeyI16>::value)
             if (row) Pi = __ldg(static_cast<const int *>(pts) + i);
 #pragma unroll 4
         for (int jj = 0; jj < JPT; ++jj) {
-            const int j = bj * TILE + jl0 + jj;
+            const int j = bj * RC_TILE + jl0 + jj;
             bool cand = false;
             if (row && j > i && j < n) {
-                const int r = pre_test<G>(pts, Pi, i, j, s_pre);
+                const int r = pre_test<G>(pts, Pi, i, j, s_cov);
                 nvalid += r != 0;
                 cand = r == 2;
             }
@@ -562,119 +583,137 @@ __global__ void __launch_bounds__(1024) k_segsort(const void *__restrict__ xy, u
     __shared__ unsigned s_min[32];
     const int NB = meta[0] + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int b = blockIdx.x; b < NB; b += gridDim.x) {
-        const unsigned off = base[b], m = base[b + 1] - off;
-        if (m == 0) continue;
-        const bool singleton = (b > 0 && b < NB - 1 && bnd[b] == bnd[b - 1] + 1);
-        if (m == 1 || singleton) {
-            // position of the smallest pair (pairs are distinct)
-            unsigned best = 0xffffffffu, bpos = 0;
-            for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-                const unsigned pv = pair_of(ev[off + k]);
-                if (pv < best) { best = pv; bpos = k; }
-            }
-            for (int s = 16; s >= 1; s >>= 1) {
-                const unsigned ob = __shfl_xor_sync(FULL, best, s), op = __shfl_xor_sync(FULL, bpos, s);
-                if (ob < best) { best = ob; bpos = op; }
-            }
-            __syncthreads();
-            if (lane == 0) { s_min[warp] = best; s_key[warp] = bpos; }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned bb = 0xffffffffu, bp = 0;
-                for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
-                    if (s_min[q] < bb) { bb = s_min[q]; bp = (unsigned)s_key[q]; }
-                s_min[0] = bp;
-            }
-            __syncthreads();
-            const unsigned mpos = s_min[0];
-            const unsigned e0 = ev[off], em = ev[off + mpos];
-            __syncthreads();
-            for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-                unsigned e = ev[off + k];
-                if (k == 0) e = em;
-                else if (k == mpos) e = e0;
-                ev[off + k] = ev_pack(ev_i(e), ev_j(e), k > 0);
-            }
-            continue;
+    // The CTA's buckets are b = blockIdx.x + k gridDim.x.  Their sizes are read
+    // all at once, 1024 at a time, and only the non-empty ones are visited:
+    // walking them one by one costs a dependent global read per bucket, which
+    // dominates when few buckets hold events (the branch-and-bound's kept
+    // ones).
+    __shared__ int s_list[1024];
+    __shared__ int s_nl;
+    for (long long c0 = blockIdx.x; c0 < NB; c0 += (long long)gridDim.x * blockDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_nl = 0;
+        __syncthreads();
+        {
+            const long long bb = c0 + (long long)threadIdx.x * gridDim.x;
+            if (bb < NB && base[bb + 1] > base[bb]) s_list[atomicAdd(&s_nl, 1)] = (int)bb;
         }
-        if (m > (unsigned)SEG_CAP) {
-            if (threadIdx.x == 0) {
-                const int slot = atomicAdd(&meta[2], 1);
-                oversize[slot] = b;
-            }
-            continue;
-        }
-        int P = 1;
-        while (P < (int)m) P <<= 1;
-        // An interior bucket holds keys in [bnd[b - 1], bnd[b]); when that span
-        // is below 2^32, (key - bnd[b - 1]) << 32 | pair is one word that
-        // orders events by (key, pair), sorted in registers.
-        if (b > 0 && b < NB - 1 && (unsigned long long)(bnd[b] - bnd[b - 1]) <= 0xffffffffull) {
-            const long long klo = bnd[b - 1];
-            unsigned long long *w = reinterpret_cast<unsigned long long *>(smem);
-            auto word = [&](int k) {
-                if (k >= (int)m) return ~0ull;
-                const unsigned e = ev[off + k];
-                return ((unsigned long long)(event_key<G>(xy, e) - klo) << 32) | pair_of(e);
-            };
-            __syncthreads();
-            const int Pw = P < (int)blockDim.x ? (int)blockDim.x : P;
-            if (2 * Pw > SEG_CAP * 3 / 2 && Pw == 2 * (int)blockDim.x * 8) {
-                // too large for one merge sort and its scratch: two halves are
-                // merge-sorted one after the other (scratch after both), then
-                // merged by merge path straight into the event array
-                const int Hh = Pw / 2;
-                unsigned long long *A = w, *Bw = w + Hh, *scr = w + 2 * Hh;
-                cta_fill_merge_sort<8>(A, scr, Hh, word);
-                cta_fill_merge_sort<8>(Bw, scr, Hh, [&](int k) { return word(Hh + k); });
-                merge_halves_to_events(A, Bw, Hh, (int)m, ev + off);
-                continue;
-            }
-            // merge sort (registers, then merge-path levels) where its scratch
-            // copy fits beside the words, else the register-blocked bitonic sort
-            const bool sorted = 2 * Pw <= SEG_CAP * 3 / 2 ? cta_fill_merge_sort_any(w, w + Pw, Pw, word)
-                                                           : cta_fill_sort_any(w, Pw, word);
-            if (sorted) {
-                for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
-                    const unsigned long long v = w[k];
-                    const bool cont = k > 0 && (w[k - 1] >> 32) == (v >> 32);
-                    ev[off + k] = ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), cont);
+        __syncthreads();
+        const int nl = s_nl;
+        for (int q = 0; q < nl; ++q) {
+            const int b = s_list[q];
+            const unsigned off = base[b], m = base[b + 1] - off;
+            const bool singleton = (b > 0 && b < NB - 1 && bnd[b] == bnd[b - 1] + 1);
+            if (m == 1 || singleton) {
+                // position of the smallest pair (pairs are distinct)
+                unsigned best = 0xffffffffu, bpos = 0;
+                for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+                    const unsigned pv = pair_of(ev[off + k]);
+                    if (pv < best) { best = pv; bpos = k; }
                 }
-                continue;
-            }
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < P; k += blockDim.x) {
-            if (k < (int)m) {
-                const unsigned e = ev[off + k];
-                s_key[k] = event_key<G>(xy, e);
-                s_ev[k] = e;
-            } else {
-                s_key[k] = KEY_INF;
-                s_ev[k] = 0xffffffffu;
-            }
-        }
-        __syncthreads();
-        for (int k = 2; k <= P; k <<= 1) {
-            for (int j = k >> 1; j >= 1; j >>= 1) {
-                for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
-                    const int i = 2 * t - (t & (j - 1));
-                    const int l = i + j;
-                    const bool up = (i & k) == 0;
-                    const long long a = s_key[i], c = s_key[l];
-                    const unsigned ea = s_ev[i], ec = s_ev[l];
-                    if (up ? ev_less(c, ec, a, ea) : ev_less(a, ea, c, ec)) {
-                        s_key[i] = c; s_key[l] = a;
-                        s_ev[i] = ec; s_ev[l] = ea;
-                    }
+                for (int s = 16; s >= 1; s >>= 1) {
+                    const unsigned ob = __shfl_xor_sync(FULL, best, s), op = __shfl_xor_sync(FULL, bpos, s);
+                    if (ob < best) { best = ob; bpos = op; }
                 }
                 __syncthreads();
+                if (lane == 0) { s_min[warp] = best; s_key[warp] = bpos; }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    unsigned bb = 0xffffffffu, bp = 0;
+                    for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+                        if (s_min[q] < bb) { bb = s_min[q]; bp = (unsigned)s_key[q]; }
+                    s_min[0] = bp;
+                }
+                __syncthreads();
+                const unsigned mpos = s_min[0];
+                const unsigned e0 = ev[off], em = ev[off + mpos];
+                __syncthreads();
+                for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+                    unsigned e = ev[off + k];
+                    if (k == 0) e = em;
+                    else if (k == mpos) e = e0;
+                    ev[off + k] = ev_pack(ev_i(e), ev_j(e), k > 0);
+                }
+                continue;
             }
-        }
-        for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
-            const unsigned e = s_ev[k];
-            ev[off + k] = ev_pack(ev_i(e), ev_j(e), k > 0 && s_key[k] == s_key[k - 1]);
+            if (m > (unsigned)SEG_CAP) {
+                if (threadIdx.x == 0) {
+                    const int slot = atomicAdd(&meta[2], 1);
+                    oversize[slot] = b;
+                }
+                continue;
+            }
+            int P = 1;
+            while (P < (int)m) P <<= 1;
+            // An interior bucket holds keys in [bnd[b - 1], bnd[b]); when that span
+            // is below 2^32, (key - bnd[b - 1]) << 32 | pair is one word that
+            // orders events by (key, pair), sorted in registers.
+            if (b > 0 && b < NB - 1 && (unsigned long long)(bnd[b] - bnd[b - 1]) <= 0xffffffffull) {
+                const long long klo = bnd[b - 1];
+                unsigned long long *w = reinterpret_cast<unsigned long long *>(smem);
+                auto word = [&](int k) {
+                    if (k >= (int)m) return ~0ull;
+                    const unsigned e = ev[off + k];
+                    return ((unsigned long long)(event_key<G>(xy, e) - klo) << 32) | pair_of(e);
+                };
+                __syncthreads();
+                const int Pw = P < (int)blockDim.x ? (int)blockDim.x : P;
+                if (2 * Pw > SEG_CAP * 3 / 2 && Pw == 2 * (int)blockDim.x * 8) {
+                    // too large for one merge sort and its scratch: two halves are
+                    // merge-sorted one after the other (scratch after both), then
+                    // merged by merge path straight into the event array
+                    const int Hh = Pw / 2;
+                    unsigned long long *A = w, *Bw = w + Hh, *scr = w + 2 * Hh;
+                    cta_fill_merge_sort<8>(A, scr, Hh, word);
+                    cta_fill_merge_sort<8>(Bw, scr, Hh, [&](int k) { return word(Hh + k); });
+                    merge_halves_to_events(A, Bw, Hh, (int)m, ev + off);
+                    continue;
+                }
+                // merge sort (registers, then merge-path levels) where its scratch
+                // copy fits beside the words, else the register-blocked bitonic sort
+                const bool sorted = 2 * Pw <= SEG_CAP * 3 / 2 ? cta_fill_merge_sort_any(w, w + Pw, Pw, word)
+                                                               : cta_fill_sort_any(w, Pw, word);
+                if (sorted) {
+                    for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
+                        const unsigned long long v = w[k];
+                        const bool cont = k > 0 && (w[k - 1] >> 32) == (v >> 32);
+                        ev[off + k] = ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), cont);
+                    }
+                    continue;
+                }
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < P; k += blockDim.x) {
+                if (k < (int)m) {
+                    const unsigned e = ev[off + k];
+                    s_key[k] = event_key<G>(xy, e);
+                    s_ev[k] = e;
+                } else {
+                    s_key[k] = KEY_INF;
+                    s_ev[k] = 0xffffffffu;
+                }
+            }
+            __syncthreads();
+            for (int k = 2; k <= P; k <<= 1) {
+                for (int j = k >> 1; j >= 1; j >>= 1) {
+                    for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                        const int i = 2 * t - (t & (j - 1));
+                        const int l = i + j;
+                        const bool up = (i & k) == 0;
+                        const long long a = s_key[i], c = s_key[l];
+                        const unsigned ea = s_ev[i], ec = s_ev[l];
+                        if (up ? ev_less(c, ec, a, ea) : ev_less(a, ea, c, ec)) {
+                            s_key[i] = c; s_key[l] = a;
+                            s_ev[i] = ec; s_ev[l] = ea;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
+                const unsigned e = s_ev[k];
+                ev[off + k] = ev_pack(ev_i(e), ev_j(e), k > 0 && s_key[k] == s_key[k - 1]);
+            }
         }
     }
 }
@@ -1940,7 +1979,7 @@ size_t sweep_plan_bytes(const SweepPlan &p)
     b += a256((size_t)(BND_MAX + 1) * 4);
     b += a256((size_t)BND_MAX * 4);
     b += a256((size_t)(emax > 0 ? emax : 1) * 4);
-    b += emax > SEG_CAP ? a256((size_t)emax * 4) : 0;
+    b += a256((size_t)(emax > 0 ? emax : 1) * 4);   // merge copy of large buckets, list of a restricted pass
     b += a256((size_t)2 * W * 4);
     b += a256((size_t)W * n * 2);
     b += (n > SORT_SMEM_N) ? a256((size_t)W * P * (n > 32768 ? 10 : 8)) : 0;
@@ -1964,7 +2003,7 @@ void sweep_plan_carve(SweepPlan &p, void *ws)
     p.base = (unsigned *)take((size_t)(BND_MAX + 1) * 4);
     p.oversize = (int *)take((size_t)BND_MAX * 4);
     p.ev = (unsigned *)take((size_t)(p.emax > 0 ? p.emax : 1) * 4);
-    p.ev2 = p.emax > SEG_CAP ? (unsigned *)take((size_t)p.emax * 4) : nullptr;
+    p.ev2 = (unsigned *)take((size_t)(p.emax > 0 ? p.emax : 1) * 4);
     p.range = (unsigned *)take((size_t)2 * p.W * 4);
     p.orders = (unsigned short *)take((size_t)p.W * p.n * 2);
     p.gsort = (p.n > SORT_SMEM_N) ? (unsigned long long *)take((size_t)p.W * P * (p.n > 32768 ? 10 : 8)) : nullptr;
@@ -2049,7 +2088,7 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
     const int n = p.n;
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
     cudaFuncSetAttribute(k_bucket_pairs<true, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    if (pre && p.ev2) {
+    if (pre) {
         // the restricted count listed the kept pairs: place only those
         unsigned *cursor = p.hist;
         { StageTimer _t(STAGE_SCATTER, st); k_copy_starts<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.base, p.meta, cursor); }
@@ -2065,7 +2104,7 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
     const size_t seg_smem = (size_t)SEG_CAP * 12;
     cudaFuncSetAttribute(k_segsort<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
     { StageTimer _t(STAGE_SEGSORT, st); k_segsort<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, p.base, p.bnd, p.meta, p.oversize); }
-    if (p.ev2) {
+    if (p.emax > SEG_CAP) {
         cudaFuncSetAttribute(k_segsort_big<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
         StageTimer _t(STAGE_SEGSORT_BIG, st);
         k_segsort_big<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, p.ev2, p.base, p.meta, p.oversize);
