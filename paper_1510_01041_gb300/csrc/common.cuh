@@ -354,4 +354,45 @@ __device__ bool cta_fill_sort_any(T *s, int P, F fill)
     }
 }
 
+// A range's start order (global, written by the start sort) into the warp's
+// order and position arrays.  When n is a multiple of 8 the order is read as
+// 16-byte words, four per lane in flight (the slice starts at w n 2 bytes of
+// a 256-byte aligned array, so it is 16-byte aligned), and stored to shared
+// memory as 16-byte words; else one 16-bit entry at a time.
+__device__ __forceinline__ void load_order(const unsigned short *__restrict__ src, int n, unsigned short *order,
+                                           unsigned short *pos, int lane)
+{
+    if ((n & 7) == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *o4 = reinterpret_cast<uint4 *>(order);
+        const int n8 = n >> 3;
+        for (int v0 = 0; v0 < n8; v0 += 4 * 32) {
+            uint4 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int v = v0 + u * 32 + lane;
+                q[u] = v < n8 ? s4[v] : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int v = v0 + u * 32 + lane;
+                if (v >= n8) continue;
+                o4[v] = q[u];
+                const unsigned wds[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    pos[wds[r] & 0xffffu] = (unsigned short)(8 * v + 2 * r);
+                    pos[wds[r] >> 16] = (unsigned short)(8 * v + 2 * r + 1);
+                }
+            }
+        }
+    } else {
+        for (int a = lane; a < n; a += 32) {
+            const unsigned short p = src[a];
+            order[a] = p;
+            pos[p] = (unsigned short)a;
+        }
+    }
+}
+
 }  // namespace lms

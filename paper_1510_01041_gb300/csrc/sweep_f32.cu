@@ -15,6 +15,8 @@
 // differ only by a permutation of points tied at that slope.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "lms.h"
@@ -107,12 +109,13 @@ __global__ void __launch_bounds__(1024) k_pack_f32(const float *__restrict__ x, 
 __global__ void __launch_bounds__(1024) k_sweep_init_f32(const float2 *__restrict__ P, int n, int h,
                                                          const unsigned *__restrict__ ev,
                                                          const unsigned *__restrict__ range, int W,
-                                                         const int *__restrict__ meta,
+                                                         int *__restrict__ meta_mut,
                                                          const unsigned *__restrict__ base,
                                                          unsigned short *__restrict__ orders,
                                                          long long *__restrict__ gkeys, unsigned short *__restrict__ gidx,
                                                          CandF *__restrict__ cands)
 {
+    const int *meta = meta_mut;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_slope;
     __shared__ CandF s_best[32];
@@ -121,45 +124,84 @@ __global__ void __launch_bounds__(1024) k_sweep_init_f32(const float2 *__restric
     const unsigned E = base[meta[0] + 1];
     const unsigned start = range[2 * w], end = range[2 * w + 1];
     const bool vertical = (E == 0 && w == 0);
+    if (w == 0 && threadIdx.x == 0) meta_mut[4] = 0;   // range counter of k_sweep_f32
     if (start >= end && !vertical) {
         if (threadIdx.x == 0) cands[w] = candf_empty();
         return;
     }
     int Pn = 1;
     while (Pn < n) Pn <<= 1;
-    long long *key = (n <= SORT_SMEM_N) ? reinterpret_cast<long long *>(smem) : gkeys + (size_t)w * Pn;
-    unsigned short *idx = (n <= SORT_SMEM_N) ? reinterpret_cast<unsigned short *>(smem + (size_t)Pn * 8)
-                                            : gidx + (size_t)w * Pn;
     if (threadIdx.x == 0) s_slope = vertical ? 0.0 : slope_of(P[ev_i(ev[start])], P[ev_j(ev[start])]);
     __syncthreads();
     const double s0 = s_slope;
-    for (int k = threadIdx.x; k < Pn; k += blockDim.x) {
-        key[k] = k < n ? dkey(zf(P[k], s0)) : 0x7fffffffffffffffLL;
-        idx[k] = (unsigned short)(k < n ? k : 0);
-    }
-    __syncthreads();
-    // bitonic on (key, x, index)
-    for (int kk = 2; kk <= Pn; kk <<= 1) {
-        for (int j = kk >> 1; j >= 1; j >>= 1) {
-            for (int t = threadIdx.x; t < Pn / 2; t += blockDim.x) {
-                const int i = 2 * t - (t & (j - 1));
-                const int l = i + j;
-                const bool up = (i & kk) == 0;
-                const long long a = key[i], b = key[l];
-                const unsigned short ia = idx[i], ib = idx[l];
-                bool gt;
-                if (a != b) gt = a > b;
-                else if (i < n && l < n && P[ia].x != P[ib].x) gt = P[ia].x > P[ib].x;
-                else gt = ia > ib;
-                if (gt == up) { key[i] = b; key[l] = a; idx[i] = ib; idx[l] = ia; }
+    // the order just before s0: (projection, x ascending, index)
+    auto exact_gt = [&](int ia, int ib) {
+        const long long a = dkey(zf(P[ia], s0)), b = dkey(zf(P[ib], s0));
+        if (a != b) return a > b;
+        if (P[ia].x != P[ib].x) return P[ia].x > P[ib].x;
+        return ia > ib;
+    };
+    long long *wd = nullptr;        // shared-memory path: sorted words, index in the low 16 bits
+    long long *key = nullptr;       // global path: keys and indices
+    unsigned short *idx = nullptr;
+    if (n <= SORT_SMEM_N) {
+        // merge sort of words (projection key with its low 16 bits cleared) |
+        // index: the order is exact except inside runs whose keys agree above
+        // those 16 bits (projections within 2^16 ulps of each other), which
+        // odd-even transposition passes with the exact comparison put right
+        const int Ps = Pn < (int)blockDim.x ? (int)blockDim.x : Pn;
+        wd = reinterpret_cast<long long *>(smem);
+        auto word = [&](int k) {
+            return k < n ? ((dkey(zf(P[k], s0)) & ~0xffffLL) | (long long)k) : 0x7fffffffffffffffLL;
+        };
+        cta_fill_merge_sort_any(wd, wd + Ps, Ps, word);
+        for (;;) {
+            int swapped = 0;
+            for (int par = 0; par < 2; ++par) {
+                for (int q = 2 * (int)threadIdx.x + par; q + 1 < n; q += 2 * (int)blockDim.x) {
+                    const long long u = wd[q], v = wd[q + 1];
+                    if ((u >> 16) == (v >> 16) && exact_gt((int)(u & 0xffff), (int)(v & 0xffff))) {
+                        wd[q] = v;
+                        wd[q + 1] = u;
+                        swapped = 1;
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
+            if (!__syncthreads_or(swapped)) break;
+        }
+    } else {
+        key = gkeys + (size_t)w * Pn;
+        idx = gidx + (size_t)w * Pn;
+        for (int k = threadIdx.x; k < Pn; k += blockDim.x) {
+            key[k] = k < n ? dkey(zf(P[k], s0)) : 0x7fffffffffffffffLL;
+            idx[k] = (unsigned short)(k < n ? k : 0);
+        }
+        __syncthreads();
+        // bitonic on (key, x, index)
+        for (int kk = 2; kk <= Pn; kk <<= 1) {
+            for (int j = kk >> 1; j >= 1; j >>= 1) {
+                for (int t = threadIdx.x; t < Pn / 2; t += blockDim.x) {
+                    const int i = 2 * t - (t & (j - 1));
+                    const int l = i + j;
+                    const bool up = (i & kk) == 0;
+                    const long long a = key[i], b = key[l];
+                    const unsigned short ia = idx[i], ib = idx[l];
+                    bool gt;
+                    if (a != b) gt = a > b;
+                    else if (i < n && l < n && P[ia].x != P[ib].x) gt = P[ia].x > P[ib].x;
+                    else gt = ia > ib;
+                    if (gt == up) { key[i] = b; key[l] = a; idx[i] = ib; idx[l] = ia; }
+                }
+                __syncthreads();
+            }
         }
     }
-    for (int k = threadIdx.x; k < n; k += blockDim.x) orders[(size_t)w * n + k] = idx[k];
+    auto ord = [&](int k) { return wd ? (int)(wd[k] & 0xffff) : (int)idx[k]; };
+    for (int k = threadIdx.x; k < n; k += blockDim.x) orders[(size_t)w * n + k] = (unsigned short)ord(k);
     CandF best = candf_empty();
     for (int a = threadIdx.x; a + h - 1 < n; a += blockDim.x) {
-        const double zb = zf(P[idx[a]], s0), zt = zf(P[idx[a + h - 1]], s0);
+        const double zb = zf(P[ord(a)], s0), zt = zf(P[ord(a + h - 1)], s0);
         CandF c;
         c.w = zt - zb; c.t = 0.5 * (zb + zt); c.s = s0; c.valid = 1; c.pad = 0;
         c.i = -1; c.j = -1;
@@ -192,10 +234,11 @@ __global__ void __launch_bounds__(256) k_sweep_f32(const float2 *__restrict__ g_
                                                    const unsigned *__restrict__ ev,
                                                    const unsigned *__restrict__ range, int W,
                                                    const unsigned short *__restrict__ orders,
-                                                   CandF *__restrict__ cands)
+                                                   CandF *__restrict__ cands, int *__restrict__ meta)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    unsigned *next_range = reinterpret_cast<unsigned *>(meta + 4);
     float2 *s_p = reinterpret_cast<float2 *>(smem);
     const size_t off0 = XY_SMEM ? (((size_t)n * 8 + 15) & ~(size_t)15) : 0;
     const size_t half = ((size_t)n * 2 + 15) & ~(size_t)15;
@@ -205,9 +248,8 @@ __global__ void __launch_bounds__(256) k_sweep_f32(const float2 *__restrict__ g_
         for (int k = threadIdx.x; k < n; k += blockDim.x) s_p[k] = g_p[k];
         __syncthreads();
     }
-    const int w = blockIdx.x * nwarp + warp;
-    if (w >= W) return;
-    const unsigned start = range[2 * w], end = range[2 * w + 1];
+    const int g = blockIdx.x * nwarp + warp;   // this sweeping warp
+    if (g >= W) return;                          // candidate slots exist for W warps
     auto PT = [&](int k) { return ldp<XY_SMEM>(s_p, g_p, k); };
     CandF best = candf_empty();
     auto offer = [&](double wd, double t, double sl, int i, int j) {
@@ -215,12 +257,16 @@ __global__ void __launch_bounds__(256) k_sweep_f32(const float2 *__restrict__ g_
         c.w = wd; c.t = t; c.s = sl; c.i = i; c.j = j; c.valid = 1; c.pad = 0;
         if (candf_better(c, best)) best = c;
     };
-    if (start < end) {
-        for (int a = lane; a < n; a += 32) {
-            const unsigned short p = orders[(size_t)w * n + a];
-            order[a] = p;
-            pos[p] = (unsigned short)a;
-        }
+    // ranges are taken in slope order from a shared counter until none is left
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(next_range, 1u);
+        w = __shfl_sync(FULL, w, 0);
+        if (w >= (unsigned)W) break;
+        const unsigned start = range[2 * w], end = range[2 * w + 1];
+        if (start >= end) continue;
+        __syncwarp();
+        load_order(orders + (size_t)w * n, n, order, pos, lane);
         __syncwarp();
         unsigned k = start;
         while (k < end) {
@@ -320,7 +366,7 @@ __global__ void __launch_bounds__(256) k_sweep_f32(const float2 *__restrict__ g_
         }
     }
     best = candf_warp_best(best);
-    if (lane == 0) cands[W + w] = best;
+    if (lane == 0) cands[W + g] = best;
 }
 
 __global__ void __launch_bounds__(1024) k_argmin_f32(const CandF *__restrict__ cands, int count,
@@ -394,7 +440,8 @@ cudaError_t launch_sweep_f32_fit(const SweepPlan &p, const float *x, const float
     if (e != cudaSuccess) return e;
     e = launch_events_finish<KeyF32>(p, P, nullptr, st, true);
     if (e != cudaSuccess) return e;
-    const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)Pn * 10 : 0;
+    const int Ps = Pn < 1024 ? 1024 : Pn;
+    const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)Ps * 16 : 0;   // sort words + merge scratch
     cudaFuncSetAttribute(k_sweep_init_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)init_smem);
     {
         StageTimer _t(STAGE_INIT, st);
@@ -407,19 +454,22 @@ cudaError_t launch_sweep_f32_fit(const SweepPlan &p, const float *x, const float
     int spb = (int)((227 * 1024 - xyb) / per);
     spb = spb < 1 ? 1 : (spb > 8 ? 8 : spb);
     const size_t sw_smem = xyb + per * spb;
-    const int blocks = (p.W + spb - 1) / spb;
+    // persistent: at most one CTA per SM (the shared memory allows no more),
+    // every warp taking ranges from the counter
+    const int blocks = std::min((p.W + spb - 1) / spb, p.C);
+    const int G = std::min(blocks * spb, p.W);
     if (xs) {
         cudaFuncSetAttribute(k_sweep_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
         StageTimer _t(STAGE_SWEEP, st);
-        k_sweep_f32<true><<<blocks, 32 * spb, sw_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.orders, cands);
+        k_sweep_f32<true><<<blocks, 32 * spb, sw_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.orders, cands, p.meta);
     } else {
         cudaFuncSetAttribute(k_sweep_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
         StageTimer _t(STAGE_SWEEP, st);
-        k_sweep_f32<false><<<blocks, 32 * spb, sw_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.orders, cands);
+        k_sweep_f32<false><<<blocks, 32 * spb, sw_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.orders, cands, p.meta);
     }
     {
         StageTimer _t(STAGE_ARGMIN, st);
-        k_argmin_f32<<<1, 1024, 0, st>>>(cands, 2 * p.W, bad, out);
+        k_argmin_f32<<<1, 1024, 0, st>>>(cands, p.W + G, bad, out);
     }
     return cudaGetLastError();
 }
