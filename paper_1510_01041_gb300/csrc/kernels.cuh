@@ -87,6 +87,7 @@ cudaError_t launch_paper(const short *x, const short *y, int n, int h, void *ws,
 
 // ---------------------------------------------------------------- sweep path
 constexpr int SEG_CAP = 16384;   // events a bucket may hold to be sorted in shared memory
+constexpr int SEG_REPAIR_MAX = 64;   // odd-even passes a bucket sort may spend on cells of equal shifted keys
 constexpr int BND_MAX = 16384;   // slope-bucket boundaries (power of two, shared memory)
 constexpr int SORT_SMEM_N = 8192;  // sweep start orders sorted in shared memory up to this n
 

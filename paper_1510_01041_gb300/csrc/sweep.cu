@@ -64,6 +64,47 @@ __device__ __forceinline__ int bucket_of(const long long *bnd, int P2, long long
     return pos;
 }
 
+// Bucket of the pair (i, j), -1 when x_i == x_j.  int16 points: the exact
+// key, searched.  float points: the exact key costs a double division, so
+// the slope is first estimated in float, dy / dx with the differences and
+// the quotient each rounded once (relative error below 2^-21), and widened
+// by 2^-18 relative on both sides (__fdividef is within 2 ulp for divisors
+// in [2^-126, 2^126]; the range checks keep every operand normal); the
+// interval's two ends are mapped to the
+// key space (the double bits of a float are a shift and a re-bias of its
+// own).  When both ends fall in one bucket the exact key does too; otherwise
+// (about one pair in a few hundred), and wherever a float leaves the normal
+// range, the exact key decides.
+template <class G>
+__device__ __forceinline__ int pair_bucket(const void *pts, int i, int j, const long long *s_bnd, int P2)
+{
+    if constexpr (std::is_same<G, KeyF32>::value) {
+        const float2 *P = static_cast<const float2 *>(pts);
+        const float2 a = P[i], c = P[j];
+        if (a.x == c.x) return -1;
+        if (a.y == c.y) return bucket_of(s_bnd, P2, 0);   // slope 0: key 0 exactly
+        float dx = c.x - a.x, dy = c.y - a.y;
+        if (dx < 0.f) { dx = -dx; dy = -dy; }
+        const float q = __fdividef(dy, dx);
+        const float aq = fabsf(q);
+        if (dx >= 0x1p-100f && dx <= 0x1p100f && fabsf(dy) >= 0x1p-100f && aq >= 0x1p-100f && aq <= 0x1p100f) {
+            // float -> key of the same value as a double
+            auto fkey = [](float f) {
+                const unsigned u = __float_as_uint(f);
+                const long long mag = ((long long)(u & 0x7fffffffu) << 29) + (896LL << 52);
+                return (u >> 31) ? ~mag : mag;
+            };
+            const float q0 = q * (1.f - 0x1p-18f), q1 = q * (1.f + 0x1p-18f);
+            const long long klo = fkey(fminf(q0, q1)), khi = fkey(fmaxf(q0, q1));
+            const int b = bucket_of(s_bnd, P2, klo);
+            if (khi < s_bnd[b]) return b;
+        }
+    }
+    long long key;
+    if (!G::key(pts, i, j, key)) return -1;
+    return bucket_of(s_bnd, P2, key);
+}
+
 // Upper-triangle tile decode: tile q -> (bi <= bj).
 __device__ __forceinline__ void tile_decode(int q, int &bi, int &bj)
 {
@@ -278,10 +319,8 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
             const int j = bj * TILE + jl0 + jj;
             if (j <= i || j >= n) continue;
             if (pre && pre_test<G>(pts, Pi, i, j, s_cov) != 2) continue;
-            long long key;
-            if (!G::key(pts, i, j, key)) continue;
-            const int b = bucket_of(s_bnd, P2, key);
-            if (keep && !keep[b]) continue;
+            const int b = pair_bucket<G>(pts, i, j, s_bnd, P2);
+            if (b < 0 || (keep && !keep[b])) continue;
             const unsigned slot = atomicAdd(&s_cnt[b], 1u);
             if (SCATTER) ev[slot] = ev_pack(i, j, false);
         }
@@ -319,9 +358,8 @@ __device__ __forceinline__ void resolve_pairs(const void *pts, const long long *
 {
     bool kept = false;
     if (have) {
-        long long key;
-        if (G::key(pts, (int)(pr >> 16), (int)(pr & 0xffffu), key)) {
-            const int b = bucket_of(s_bnd, P2, key);
+        const int b = pair_bucket<G>(pts, (int)(pr >> 16), (int)(pr & 0xffffu), s_bnd, P2);
+        if (b >= 0) {
             if (!keep || keep[b]) {
                 atomicAdd(&s_cnt[b], 1u);
                 kept = true;
@@ -435,10 +473,8 @@ __global__ void __launch_bounds__(CNT_THREADS) k_scatter_list(const void *__rest
     const unsigned per = (m + gridDim.x - 1) / gridDim.x;
     const unsigned q0 = min(m, blockIdx.x * per), q1 = min(m, q0 + per);
     auto bucket = [&](unsigned pr, int &b) {
-        long long key;
-        if (!G::key(pts, (int)(pr >> 16), (int)(pr & 0xffffu), key)) return false;
-        b = bucket_of(s_bnd, P2, key);
-        return true;
+        b = pair_bucket<G>(pts, (int)(pr >> 16), (int)(pr & 0xffffu), s_bnd, P2);
+        return b >= 0;
     };
     for (unsigned q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
         int b;
@@ -543,25 +579,26 @@ __device__ __forceinline__ bool ev_less(long long ka, unsigned ea, long long kb,
 // with ~0) into the first m outputs, written as events with the "same slope
 // as the previous event" flag.  Every thread writes 16 consecutive outputs,
 // its start on the merge path found by a binary search on its diagonal.
+template <class Less, class Same>
 __device__ void merge_halves_to_events(const unsigned long long *A, const unsigned long long *B, int Hh, int m,
-                                       unsigned *__restrict__ out)
+                                       unsigned *__restrict__ out, Less less, Same same)
 {
     const int d = (int)threadIdx.x * 16;
     if (d >= m) return;
     int lo = d > Hh ? d - Hh : 0, hi = d < Hh ? d : Hh;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (A[mid] < B[d - 1 - mid]) lo = mid + 1; else hi = mid;
+        if (less(A[mid], B[d - 1 - mid])) lo = mid + 1; else hi = mid;
     }
     int i = lo, j = d - lo;
     unsigned long long prev = 0;
     bool have_prev = false;
     if (i > 0) { prev = A[i - 1]; have_prev = true; }
-    if (j > 0 && (!have_prev || B[j - 1] > prev)) { prev = B[j - 1]; have_prev = true; }
+    if (j > 0 && (!have_prev || less(prev, B[j - 1]))) { prev = B[j - 1]; have_prev = true; }
     for (int o = d; o < d + 16 && o < m; ++o) {
-        const bool take_a = j >= Hh || (i < Hh && A[i] < B[j]);
+        const bool take_a = j >= Hh || (i < Hh && less(A[i], B[j]));
         const unsigned long long v = take_a ? A[i++] : B[j++];
-        const bool cont = have_prev && (prev >> 32) == (v >> 32);
+        const bool cont = have_prev && same(prev, v);
         out[o] = ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), cont);
         prev = v;
         have_prev = true;
@@ -645,16 +682,59 @@ __global__ void __launch_bounds__(1024) k_segsort(const void *__restrict__ xy, u
             }
             int P = 1;
             while (P < (int)m) P <<= 1;
-            // An interior bucket holds keys in [bnd[b - 1], bnd[b]); when that span
-            // is below 2^32, (key - bnd[b - 1]) << 32 | pair is one word that
-            // orders events by (key, pair), sorted in registers.
-            if (b > 0 && b < NB - 1 && (unsigned long long)(bnd[b] - bnd[b - 1]) <= 0xffffffffull) {
+            // An interior bucket holds keys in [bnd[b - 1], bnd[b]).  The word
+            // ((key - bnd[b - 1]) >> sh) << 32 | pair, with sh the smallest shift
+            // that brings the span below 2^32, orders events by (key, pair)
+            // except inside a cell of equal shifted keys, where it orders them
+            // by pair alone.  The words are sorted in registers; when sh > 0 the
+            // rare cells of two or more events are then put in (key, pair)
+            // order by odd-even transposition with the exact keys.  (int16 keys
+            // of one bucket span less than 2^32: sh = 0 and no repair.)
+            if (b > 0 && b < NB - 1) {
                 const long long klo = bnd[b - 1];
+                const unsigned long long span = (unsigned long long)(bnd[b] - bnd[b - 1]);
+                const int sh = span > 0xffffffffull ? 32 - __clzll((long long)span) : 0;
                 unsigned long long *w = reinterpret_cast<unsigned long long *>(smem);
                 auto word = [&](int k) {
                     if (k >= (int)m) return ~0ull;
                     const unsigned e = ev[off + k];
-                    return ((unsigned long long)(event_key<G>(xy, e) - klo) << 32) | pair_of(e);
+                    return ((unsigned long long)(event_key<G>(xy, e) - klo) >> sh << 32) | pair_of(e);
+                };
+                auto exact = [&](unsigned long long v) {
+                    return event_key<G>(xy, ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), false));
+                };
+                // (key, pair) order of two words; the padding word ~0 is last
+                auto less = [&](unsigned long long u, unsigned long long v) {
+                    if (sh == 0 || (u >> 32) != (v >> 32) || u == ~0ull || v == ~0ull) return u < v;
+                    const long long ku = exact(u), kv = exact(v);
+                    return ku < kv || (ku == kv && (unsigned)u < (unsigned)v);
+                };
+                auto same = [&](unsigned long long u, unsigned long long v) {
+                    return (u >> 32) == (v >> 32) && (sh == 0 || exact(u) == exact(v));
+                };
+                // false when a cell needs more than SEG_REPAIR_MAX passes (then
+                // the bucket goes to the exact-key bitonic sort below)
+                auto repair = [&](unsigned long long *a, int len) {
+                    if (sh == 0) return true;
+                    int cells = 0;
+                    for (int k = threadIdx.x; k + 1 < len; k += blockDim.x) cells |= (a[k] >> 32) == (a[k + 1] >> 32);
+                    if (!__syncthreads_or(cells)) return true;
+                    for (int pass = 0; pass < SEG_REPAIR_MAX; ++pass) {
+                        int swapped = 0;
+                        for (int par = 0; par < 2; ++par) {
+                            for (int k = 2 * (int)threadIdx.x + par; k + 1 < len; k += 2 * (int)blockDim.x) {
+                                const unsigned long long u = a[k], v = a[k + 1];
+                                if ((u >> 32) == (v >> 32) && less(v, u)) {
+                                    a[k] = v;
+                                    a[k + 1] = u;
+                                    swapped = 1;
+                                }
+                            }
+                            __syncthreads();
+                        }
+                        if (!__syncthreads_or(swapped)) return true;
+                    }
+                    return false;
                 };
                 __syncthreads();
                 const int Pw = P < (int)blockDim.x ? (int)blockDim.x : P;
@@ -666,20 +746,27 @@ __global__ void __launch_bounds__(1024) k_segsort(const void *__restrict__ xy, u
                     unsigned long long *A = w, *Bw = w + Hh, *scr = w + 2 * Hh;
                     cta_fill_merge_sort<8>(A, scr, Hh, word);
                     cta_fill_merge_sort<8>(Bw, scr, Hh, [&](int k) { return word(Hh + k); });
-                    merge_halves_to_events(A, Bw, Hh, (int)m, ev + off);
-                    continue;
-                }
-                // merge sort (registers, then merge-path levels) where its scratch
-                // copy fits beside the words, else the register-blocked bitonic sort
-                const bool sorted = 2 * Pw <= SEG_CAP * 3 / 2 ? cta_fill_merge_sort_any(w, w + Pw, Pw, word)
-                                                               : cta_fill_sort_any(w, Pw, word);
-                if (sorted) {
-                    for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
-                        const unsigned long long v = w[k];
-                        const bool cont = k > 0 && (w[k - 1] >> 32) == (v >> 32);
-                        ev[off + k] = ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), cont);
+                    __syncthreads();
+                    const bool ok = repair(A, Hh);
+                    if (ok && repair(Bw, (int)m - Hh)) {
+                        merge_halves_to_events(A, Bw, Hh, (int)m, ev + off, less, same);
+                        continue;
                     }
-                    continue;
+                } else {
+                    // merge sort (registers, then merge-path levels) where its
+                    // scratch copy fits beside the words, else the register-blocked
+                    // bitonic sort
+                    const bool sorted = 2 * Pw <= SEG_CAP * 3 / 2 ? cta_fill_merge_sort_any(w, w + Pw, Pw, word)
+                                                                   : cta_fill_sort_any(w, Pw, word);
+                    if (sorted) __syncthreads();
+                    if (sorted && repair(w, (int)m)) {
+                        for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
+                            const unsigned long long v = w[k];
+                            const bool cont = k > 0 && same(w[k - 1], v);
+                            ev[off + k] = ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), cont);
+                        }
+                        continue;
+                    }
                 }
             }
             __syncthreads();

@@ -12,7 +12,12 @@
 // put into the order just after the slope.  Each event leaves its own pair
 // in the just-after order and no later event of the slope undoes that, so the
 // order is right once the slope is done, and the windows scored meanwhile
-// differ only by a permutation of points tied at that slope.
+// differ only by a permutation of points tied at that slope.  A window is
+// scored in double only when a float estimate of its width, with a proven
+// error margin, does not already show it wider than the sweeper's best, so
+// nearly every event costs float arithmetic alone (GB300's double rate is a
+// small fraction of its float rate); the result is the same as scoring
+// every window in double.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -90,18 +95,34 @@ __device__ __forceinline__ long long dkey(double v)
     return bits < 0 ? (bits ^ 0x7fffffffffffffffLL) : bits;
 }
 
-// One CTA: pack the coordinates and record whether all of them are finite.
+// A coordinate the sweep's float pre-test accepts: 0 or of magnitude in
+// [2^-40, 2^40].  Then every nonzero difference of two coordinates, every
+// slope and every product the pre-test forms stays a normal float (or
+// overflows to inf, which disables the test for that window).
+__device__ __forceinline__ bool tame(float v)
+{
+    const float a = fabsf(v);
+    return a == 0.f || (a >= 0x1p-40f && a <= 0x1p40f);
+}
+
+// One CTA: pack the coordinates, record whether all of them are finite
+// (bad[0]) and whether all of them are tame (bad[1]).
 __global__ void __launch_bounds__(1024) k_pack_f32(const float *__restrict__ x, const float *__restrict__ y, int n,
                                                    float2 *__restrict__ P, int *__restrict__ bad)
 {
-    int nf = 0;
+    int nf = 0, wild = 0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const float2 v = make_float2(x[k], y[k]);
         nf |= !(isfinite(v.x) && isfinite(v.y));
+        wild |= !(tame(v.x) && tame(v.y));
         P[k] = v;
     }
     nf = __syncthreads_or(nf);
-    if (threadIdx.x == 0) *bad = nf;
+    wild = __syncthreads_or(wild);
+    if (threadIdx.x == 0) {
+        bad[0] = nf;
+        bad[1] = !nf && !wild;
+    }
 }
 
 // Sweeper start: sort by (z at the first slope, x ascending, index), score
@@ -227,14 +248,41 @@ __device__ __forceinline__ float2 ldp(const float2 *s_p, const float2 *__restric
     return XY_SMEM ? s_p[k] : g_p[k];
 }
 
-// One warp per sweeper: lane-parallel swaps with the conflict rule of the
-// int16 sweep; a pair that is not adjacent is repaired by lane 0.
+// Float pre-test of one window end, done before any double arithmetic.  The
+// window has the pair's point A at one end and T at the other; at the
+// pair's slope S its width is (T.y - A.y) - (T.x - A.x) S (a top end) or
+// its negative (a bottom end).  With sf the float slope dy / dx, the float
+// estimate v = fma(-(T.x - A.x), sf, T.y - A.y) is within about
+// 2^-20.5 (|dY| + |dX| |S|) of that width, and the double width the sweep
+// records (projections y - s x in double, then their difference) within
+// 2^-49 (|T.y| + |A.y| + |S| (|T.x| + |A.x|)).  The slack below is at least
+// twice their sum, so v - slack > wb (the lane's best width, rounded up)
+// proves the window wider than the best: it cannot change the best and
+// its double arithmetic (one division, three projections) is skipped.
+// Sound for tame points (every operand a normal float, overflow to inf
+// only ever disabling the test); the caller passes wb = +inf otherwise.
+__device__ __forceinline__ bool f32_wider(float2 A, float2 T, float sf, bool top, float wb)
+{
+    const float dY = T.y - A.y, dX = T.x - A.x;
+    float v = fmaf(-dX, sf, dY);
+    if (!top) v = -v;
+    const float slack = 0x1p-18f * (fabsf(T.y) + fabsf(A.y) + fabsf(sf) * (fabsf(T.x) + fabsf(A.x))) + 0x1p-100f;
+    return v - slack > wb;
+}
+
+// One warp per sweeper, taking slope ranges from a shared counter.  The
+// events of a range are applied 32 at a time, lane-parallel, with the
+// conflict rule of the int16 sweep (an earlier swap next to this one, or at
+// the far end of one of its windows, makes the lane wait for the next
+// batch); a pair that is not adjacent is repaired by the whole warp.  Each
+// swap scores its two windows, the float pre-test first.
 template <bool XY_SMEM>
 __global__ void __launch_bounds__(256) k_sweep_f32(const float2 *__restrict__ g_p, int n, int h,
                                                    const unsigned *__restrict__ ev,
                                                    const unsigned *__restrict__ range, int W,
                                                    const unsigned short *__restrict__ orders,
-                                                   CandF *__restrict__ cands, int *__restrict__ meta)
+                                                   CandF *__restrict__ cands, int *__restrict__ meta,
+                                                   const int *__restrict__ flags)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -250,12 +298,21 @@ __global__ void __launch_bounds__(256) k_sweep_f32(const float2 *__restrict__ g_
     }
     const int g = blockIdx.x * nwarp + warp;   // this sweeping warp
     if (g >= W) return;                          // candidate slots exist for W warps
+    const bool pretest = flags[1] != 0;
+    // the residue test of the conflict check needs h - 1 >= 8 and n <= 3 (h - 1)
+    const int H = h - 1;
+    const bool fold_ok = H >= 8 && n <= 3 * H;
+    const unsigned lanemask_lt = (1u << lane) - 1u;
     auto PT = [&](int k) { return ldp<XY_SMEM>(s_p, g_p, k); };
     CandF best = candf_empty();
+    float wb = INFINITY;   // the best width rounded up (>= 0), +inf while none or without the pre-test
     auto offer = [&](double wd, double t, double sl, int i, int j) {
         CandF c;
         c.w = wd; c.t = t; c.s = sl; c.i = i; c.j = j; c.valid = 1; c.pad = 0;
-        if (candf_better(c, best)) best = c;
+        if (candf_better(c, best)) {
+            best = c;
+            if (pretest) wb = fmaxf(__double2float_ru(wd), 0.f);
+        }
     };
     // ranges are taken in slope order from a shared counter until none is left
     for (;;) {
@@ -269,53 +326,87 @@ __global__ void __launch_bounds__(256) k_sweep_f32(const float2 *__restrict__ g_
         load_order(orders + (size_t)w * n, n, order, pos, lane);
         __syncwarp();
         unsigned k = start;
+        // a window of 64 events: this batch's (e_cur) and the next one's
+        unsigned e_cur = (k + lane < end) ? ev[k + lane] : 0u;
+        unsigned e_nxt = (k + 32 + lane < end) ? ev[k + 32 + lane] : 0u;
         while (k < end) {
             const unsigned navail = min(32u, end - k);
             const bool valid = (unsigned)lane < navail;
-            const unsigned e = valid ? ev[k + lane] : 0u;
-            int a = ev_i(e), b = ev_j(e);
+            int a = ev_i(e_cur), b = ev_j(e_cur);
             float2 Pa = PT(a), Pb = PT(b);
             if (Pa.x > Pb.x) {
                 const int t = a; a = b; b = t;
                 const float2 tp = Pa; Pa = Pb; Pb = tp;
             }
-            const double sl = slope_of(Pa, Pb);
             const int pa = valid ? pos[a] : 0, pb = valid ? pos[b] : 0;
             const bool done = valid && pb < pa;
             const bool simple = valid && !done && pb == pa + 1;
             const bool repair = valid && !done && !simple;
-            // an earlier swap of this batch next to this one, or at the far
-            // end of one of its windows, makes the lane wait for the next batch
-            const unsigned me = simple ? (((unsigned)pa << 1) | 1u) : 0u;
             bool conflict = false;
-            for (int t = 0; t < 31; ++t) {
-                const unsigned o = __shfl_sync(FULL, me, t);
-                if (!simple || t >= lane || !(o & 1u)) continue;
-                const int d = abs(pa - (int)(o >> 1));
-                if (d <= 2 || abs(d - (h - 1)) <= 1) conflict = true;
+            if (fold_ok) {
+                // two simple swaps at p and q conflict only if q - p is within 2
+                // of 0 or of +-H, so p mod H and q mod H are within 2 of each
+                // other, cyclically, and then share a cell of width 4 in one of
+                // three grids (the last one shifted across the wrap); lanes that
+                // share a cell are treated as conflicting (a superset)
+                int f = pa;
+                if (f >= H) f -= H;
+                if (f >= H) f -= H;
+                int f2 = f + 2;
+                const unsigned none = 0x40000000u | (unsigned)lane;
+                const unsigned cA = simple ? (unsigned)(f >> 2) : none;
+                const unsigned cB = simple ? (unsigned)(f2 >> 2) : none;
+                if (f2 >= H) f2 -= H;
+                const unsigned cC = simple ? (unsigned)(f2 >> 2) : none;
+                const unsigned nearm = __match_any_sync(FULL, cA) | __match_any_sync(FULL, cB) |
+                                       __match_any_sync(FULL, cC);
+                const unsigned simm = __ballot_sync(FULL, simple);
+                conflict = simple && (nearm & simm & lanemask_lt) != 0u;
+            } else {
+                const unsigned me = simple ? (((unsigned)pa << 1) | 1u) : 0u;
+                for (int t = 0; t < 31; ++t) {
+                    const unsigned o = __shfl_sync(FULL, me, t);
+                    if (!simple || t >= lane || !(o & 1u)) continue;
+                    const int d = abs(pa - (int)(o >> 1));
+                    if (d <= 2 || abs(d - H) <= 1) conflict = true;
+                }
             }
             const unsigned bad = __ballot_sync(FULL, repair || conflict);
             const int cut = bad ? __ffs(bad) - 1 : (int)navail;
+            int advance;
             if (cut > 0) {
                 const bool go = simple && lane < cut;
-                const double K = zf(Pa, sl);
-                double kt = K, kb = K;
                 const int top = pa + h - 1, bot = pa - h + 2;
-                if (go) {
-                    if (top < n && top > pa + 1) kt = zf(PT(order[top]), sl);
-                    if (bot >= 0 && bot < pa) kb = zf(PT(order[bot]), sl);
-                }
+                const bool rt = go && top < n && top > pa + 1, rb = go && bot >= 0 && bot < pa;
+                const int it = rt ? order[top] : 0, ib = rb ? order[bot] : 0;
                 __syncwarp();
                 if (go) {
                     order[pa] = (unsigned short)b;
                     order[pa + 1] = (unsigned short)a;
                     pos[b] = (unsigned short)pa;
                     pos[a] = (unsigned short)(pa + 1);
-                    if (top < n) offer(kt - K, 0.5 * (K + kt), sl, min(a, b), max(a, b));
-                    if (bot >= 0) offer(K - kb, 0.5 * (kb + K), sl, min(a, b), max(a, b));
                 }
                 __syncwarp();
-                k += cut;
+                if (go) {
+                    const float2 Tt = PT(it), Tb = PT(ib);
+                    const float sf = __fdividef(Pb.y - Pa.y, Pb.x - Pa.x);
+                    const bool wt = top < n && !(rt && f32_wider(Pa, Tt, sf, true, wb));
+                    const bool wbm = bot >= 0 && !(rb && f32_wider(Pa, Tb, sf, false, wb));
+                    if (wt || wbm) {
+                        const double sl = slope_of(Pa, Pb);
+                        const double K = zf(Pa, sl);
+                        const int i = min(a, b), j = max(a, b);
+                        if (wt) {
+                            const double kt = rt ? zf(Tt, sl) : K;
+                            offer(kt - K, 0.5 * (K + kt), sl, i, j);
+                        }
+                        if (wbm) {
+                            const double kb = rb ? zf(Tb, sl) : K;
+                            offer(K - kb, 0.5 * (kb + K), sl, i, j);
+                        }
+                    }
+                }
+                advance = cut;
             } else {
                 // lane 0's pair is not adjacent: every point between its two
                 // points meets them at this slope (the order is sorted just
@@ -324,8 +415,8 @@ __global__ void __launch_bounds__(256) k_sweep_f32(const float2 *__restrict__ g_
                 // every window with an end in the block is scored.  A block in
                 // strictly ascending x (the usual case) is reversed by the warp.
                 const int lo = __shfl_sync(FULL, pa, 0), hi = __shfl_sync(FULL, pb, 0);
-                const double rsl = __shfl_sync(FULL, sl, 0);
                 const int ra = __shfl_sync(FULL, a, 0), rb = __shfl_sync(FULL, b, 0);
+                const double rsl = slope_of(PT(ra), PT(rb));
                 bool asc = true;
                 for (int u = lo + lane; u < hi; u += 32) asc = asc && PT(order[u]).x < PT(order[u + 1]).x;
                 if (__all_sync(FULL, asc)) {
@@ -361,8 +452,17 @@ __global__ void __launch_bounds__(256) k_sweep_f32(const float2 *__restrict__ g_
                     }
                 }
                 __syncwarp();
-                k += 1;
+                advance = 1;
             }
+            // slide the 64-event window by `advance`
+            const int src = (lane + advance) & 31;
+            const unsigned c1 = __shfl_sync(FULL, e_cur, src);
+            const unsigned c2 = __shfl_sync(FULL, e_nxt, src);
+            const bool from_cur = lane + advance < 32;
+            k += advance;
+            e_cur = from_cur ? c1 : c2;
+            const unsigned q = k + 32 + lane;
+            e_nxt = from_cur ? c2 : ((q < end) ? ev[q] : 0u);
         }
     }
     best = candf_warp_best(best);
@@ -461,11 +561,13 @@ cudaError_t launch_sweep_f32_fit(const SweepPlan &p, const float *x, const float
     if (xs) {
         cudaFuncSetAttribute(k_sweep_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
         StageTimer _t(STAGE_SWEEP, st);
-        k_sweep_f32<true><<<blocks, 32 * spb, sw_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.orders, cands, p.meta);
+        k_sweep_f32<true><<<blocks, 32 * spb, sw_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.orders, cands, p.meta,
+                                                             bad);
     } else {
         cudaFuncSetAttribute(k_sweep_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw_smem);
         StageTimer _t(STAGE_SWEEP, st);
-        k_sweep_f32<false><<<blocks, 32 * spb, sw_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.orders, cands, p.meta);
+        k_sweep_f32<false><<<blocks, 32 * spb, sw_smem, st>>>(P, n, p.h, p.ev, p.range, p.W, p.orders, cands, p.meta,
+                                                              bad);
     }
     {
         StageTimer _t(STAGE_ARGMIN, st);
