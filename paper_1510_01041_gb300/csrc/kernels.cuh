@@ -121,7 +121,17 @@ struct SweepPlan {
     unsigned long long *gsort; // [W][P] global sort scratch when n > SORT_SMEM_N
     Cand *cands;               // [W + G] range-start + sweeping-warp candidates
     unsigned short *gpos;      // [G][n] positions of the sweeping warps when !pos_smem (else null)
+    // A restricted pass with resplit set sorts its kept events in buckets of
+    // their own: splitters from a sample of the listed pairs (about
+    // RESPLIT_PER events a bucket) instead of the buckets of all pairs, of
+    // which the kept ones can be far above SEG_CAP.
+    bool resplit;
+    long long *bnd2;           // [BND_MAX] boundaries of the kept events' buckets
+    unsigned *base2;           // [BND_MAX + 1] their starts
+    int *meta2;                // [16] their nbnd, P2 and oversize count (layout of meta)
 };
+constexpr int RESPLIT_PER = 4096;    // kept events per bucket of a resplit pass
+constexpr int RESPLIT_S = 32768;     // sampled listed pairs of a resplit pass (at most S)
 
 size_t sweep_plan_bytes(const SweepPlan &p);
 // concurrent: the fit shares the GPU with other fits (batch plans)

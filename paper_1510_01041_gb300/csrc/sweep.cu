@@ -180,11 +180,18 @@ __global__ void k_merge_runs(const long long *__restrict__ src, long long *__res
 // or more quantile positions is a heavy slope and gets the singleton bucket
 // [v, v + 1).  Boundaries are strictly increasing; the array is padded with
 // KEY_INF to the power of two P2 > nbnd.
+// bcount (optional): the number of keys the buckets will hold; then B is
+// lowered to about *bcount / bper buckets.
 __global__ void __launch_bounds__(1024) k_splitters(const long long *__restrict__ sorted, int S, int B,
-                                                    long long *__restrict__ bnd, int *__restrict__ meta)
+                                                    long long *__restrict__ bnd, int *__restrict__ meta,
+                                                    const int *__restrict__ bcount = nullptr, int bper = 1)
 {
     __shared__ int s_m;
     __shared__ int s_scan[1024];
+    if (bcount) {
+        const long long want = ((long long)max(*bcount, 0) + bper - 1) / bper;
+        B = (int)min((long long)B, max(want, 1LL));
+    }
     if (threadIdx.x == 0) {
         int lo = 0, hi = S;
         while (lo < hi) { int m = (lo + hi) >> 1; if (sorted[m] < KEY_INF) lo = m + 1; else hi = m; }
@@ -460,7 +467,8 @@ __global__ void __launch_bounds__(CNT_THREADS) k_scatter_list(const void *__rest
                                                               const int *__restrict__ meta,
                                                               const unsigned *__restrict__ list,
                                                               unsigned *__restrict__ cursor,
-                                                              unsigned *__restrict__ ev)
+                                                              unsigned *__restrict__ ev,
+                                                              const int *__restrict__ mlist)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
@@ -469,7 +477,7 @@ __global__ void __launch_bounds__(CNT_THREADS) k_scatter_list(const void *__rest
     for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
     for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0u;
     __syncthreads();
-    const unsigned m = (unsigned)meta[6];
+    const unsigned m = (unsigned)*mlist;
     const unsigned per = (m + gridDim.x - 1) / gridDim.x;
     const unsigned q0 = min(m, blockIdx.x * per), q1 = min(m, q0 + per);
     auto bucket = [&](unsigned pr, int &b) {
@@ -489,6 +497,50 @@ __global__ void __launch_bounds__(CNT_THREADS) k_scatter_list(const void *__rest
         int b;
         if (bucket(pr, b)) ev[atomicAdd(&s_cnt[b], 1u)] = ev_pack((int)(pr >> 16), (int)(pr & 0xffffu), false);
     }
+}
+
+// Resplit of a restricted pass: S keys of evenly spaced entries of the
+// list of kept pairs (the list is in tile order, unrelated to the slopes).
+template <class G>
+__global__ void k_list_sample(const void *__restrict__ pts, const unsigned *__restrict__ list,
+                              const int *__restrict__ mlist, int S, long long *__restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const unsigned m = (unsigned)max(*mlist, 0);
+    long long k = KEY_INF;
+    if (m > 0) {
+        const unsigned pr = list[(unsigned)(((unsigned long long)s * m) / (unsigned)S)];
+        if (!G::key(pts, (int)(pr >> 16), (int)(pr & 0xffffu), k)) k = KEY_INF;
+    }
+    out[s] = k;
+}
+
+// Resplit: bucket totals of the listed pairs (total zeroed by the caller).
+template <class G>
+__global__ void __launch_bounds__(CNT_THREADS) k_list_hist(const void *__restrict__ pts,
+                                                           const long long *__restrict__ bnd,
+                                                           const int *__restrict__ meta,
+                                                           const unsigned *__restrict__ list,
+                                                           const int *__restrict__ mlist,
+                                                           unsigned *__restrict__ total)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long *s_bnd = reinterpret_cast<long long *>(smem);
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
+    const int P2 = meta[1], NB = meta[0] + 1;
+    for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
+    for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0u;
+    __syncthreads();
+    const unsigned m = (unsigned)max(*mlist, 0);
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+        const unsigned pr = list[q];
+        const int b = pair_bucket<G>(pts, (int)(pr >> 16), (int)(pr & 0xffffu), s_bnd, P2);
+        if (b >= 0) atomicAdd(&s_cnt[b], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NB; k += blockDim.x)
+        if (s_cnt[k]) atomicAdd(&total[k], s_cnt[k]);
 }
 
 __global__ void k_copy_starts(const unsigned *__restrict__ base, const int *__restrict__ meta,
@@ -1493,7 +1545,7 @@ __device__ void group_claims(unsigned short *order, unsigned short *pos, const i
 template <bool XY_SMEM>
 __device__ __forceinline__ void serial_event(unsigned short *order, unsigned short *pos, const int *s_xy,
                                              const int *__restrict__ g_xy, int n, int h, unsigned e, unsigned gmin,
-                                             int lane, Cand &best, int *err)
+                                             bool single, int lane, Cand &best, int *err)
 {
     auto XY = [&](int k) { return load_xy<XY_SMEM>(s_xy, g_xy, k); };
     int a = ev_i(e), b = ev_j(e);
@@ -1509,12 +1561,13 @@ __device__ __forceinline__ void serial_event(unsigned short *order, unsigned sho
     const long long K = proj(Pa, dy, dx);
     const int top0 = pa + h - 1, bot0 = pb - h + 1;
     const bool rd_t = top0 < n && top0 > pb, rd_b = bot0 >= 0 && bot0 < pa;
-    const int i_lo = pa > 0 ? order[pa - 1] : 0;
-    const int i_hi = pb < n - 1 ? order[pb + 1] : 0;
+    // single: the pair is alone at its slope, so no neighbour is on its line
+    const int i_lo = (!single && pa > 0) ? order[pa - 1] : 0;
+    const int i_hi = (!single && pb < n - 1) ? order[pb + 1] : 0;
     const int i_t = rd_t ? order[top0] : 0;
     const int i_b = rd_b ? order[bot0] : 0;
-    const bool lo_eq = pa > 0 && proj(XY(i_lo), dy, dx) == K;
-    const bool hi_eq = pb < n - 1 && proj(XY(i_hi), dy, dx) == K;
+    const bool lo_eq = !single && pa > 0 && proj(XY(i_lo), dy, dx) == K;
+    const bool hi_eq = !single && pb < n - 1 && proj(XY(i_hi), dy, dx) == K;
     Cand c;
     c.dy = dy; c.dx = dx; c.i = (int)(gmin >> 16); c.j = (int)(gmin & 0xffffu);
     auto offer = [&](long long wd, long long t) {
@@ -1695,8 +1748,10 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
                     cnt = 31 - __clz(smask);
                 for (int i = 0; i < cnt; ++i) {
                     const unsigned ei = __shfl_sync(FULL, e, i);
+                    const unsigned en = i < 31 ? __shfl_sync(FULL, e, i + 1) : __shfl_sync(FULL, e_nxt, 0);
                     if (!ev_cont(ei)) carried = ((unsigned)ev_i(ei) << 16) | (unsigned)ev_j(ei);
-                    serial_event<XY_SMEM>(order, pos, s_xy, g_xy, n, h, ei, carried, lane, best, err);
+                    serial_event<XY_SMEM>(order, pos, s_xy, g_xy, n, h, ei, carried, !ev_cont(ei) && !ev_cont(en),
+                                          lane, best, err);
                 }
                 const int src = (lane + cnt) & 31;
                 const unsigned c1 = __shfl_sync(FULL, e_cur, src);
@@ -1730,12 +1785,20 @@ __global__ void __launch_bounds__(256) k_sweep(const int *__restrict__ g_xy, int
             // read at once
             const int top0 = pa + h - 1, bot0 = pb - h + 1;
             const bool rd_t = live && top0 < n && top0 > pb, rd_b = live && bot0 >= 0 && bot0 < pa;
-            const int i_lo = (live && pa > 0) ? order[pa - 1] : 0;
-            const int i_hi = (live && pb < n - 1) ? order[pb + 1] : 0;
+            // A pair alone at its slope has no third point on its line (that
+            // point would pair with both at the same slope), so its outer
+            // neighbours need no test.  The next event of the last lane is the
+            // first of the next batch; past the range end (a group start)
+            // events read as 0, a start.
+            const unsigned e_dn = __shfl_down_sync(FULL, e, 1), e_n0 = __shfl_sync(FULL, e_nxt, 0);
+            const bool single = is_start && !ev_cont(lane == 31 ? e_n0 : e_dn);
+            const bool nb = live && !single;
+            const int i_lo = (nb && pa > 0) ? order[pa - 1] : 0;
+            const int i_hi = (nb && pb < n - 1) ? order[pb + 1] : 0;
             const int i_t = rd_t ? order[top0] : 0;
             const int i_b = rd_b ? order[bot0] : 0;
-            const bool lo_eq = live && pa > 0 && proj(XY(i_lo), dy, dx) == K;
-            const bool hi_eq = live && pb < n - 1 && proj(XY(i_hi), dy, dx) == K;
+            const bool lo_eq = nb && pa > 0 && proj(XY(i_lo), dy, dx) == K;
+            const bool hi_eq = nb && pb < n - 1 && proj(XY(i_hi), dy, dx) == K;
             long long kt = rd_t ? proj(XY(i_t), dy, dx) : K;
             long long kb = rd_b ? proj(XY(i_b), dy, dx) : K;
             int lo = pa, hi = pb;
@@ -2009,6 +2072,9 @@ void sweep_plan_configure(SweepPlan &p, int n, int h, int sms, int want_w, int w
     if (B > p.S / 8) B = p.S / 8;
     p.B = (int)B;
     p.C = sms;
+    // the kept events of a restricted pass above n = 8192 fill buckets of
+    // all pairs far beyond SEG_CAP; below, the resplit costs more than it saves
+    p.resplit = n > SORT_SMEM_N;
 }
 
 size_t sweep_plan_bytes(const SweepPlan &p)
@@ -2032,6 +2098,7 @@ size_t sweep_plan_bytes(const SweepPlan &p)
     b += (n > SORT_SMEM_N) ? a256((size_t)W * P * (n > 32768 ? 10 : 8)) : 0;
     b += a256((size_t)(2 * W + 8) * sizeof(Cand));
     b += p.pos_smem ? 0 : a256((size_t)p.G * n * 2);
+    b += a256((size_t)BND_MAX * 8) + a256((size_t)(BND_MAX + 1) * 4) + a256(64);   // resplit buckets
     return b;
 }
 
@@ -2056,6 +2123,9 @@ void sweep_plan_carve(SweepPlan &p, void *ws)
     p.gsort = (p.n > SORT_SMEM_N) ? (unsigned long long *)take((size_t)p.W * P * (p.n > 32768 ? 10 : 8)) : nullptr;
     p.cands = (Cand *)take((size_t)(2 * p.W + 8) * sizeof(Cand));
     p.gpos = p.pos_smem ? nullptr : (unsigned short *)take((size_t)p.G * p.n * 2);
+    p.bnd2 = (long long *)take((size_t)BND_MAX * 8);
+    p.base2 = (unsigned *)take((size_t)(BND_MAX + 1) * 4);
+    p.meta2 = (int *)take(64);
 }
 
 const long long *sorted_sample(const SweepPlan &p)
@@ -2135,14 +2205,39 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
     const int n = p.n;
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
     cudaFuncSetAttribute(k_bucket_pairs<true, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
+    // buckets of the bucket sorts: those of the count, or of a resplit
+    const long long *sbnd = p.bnd;
+    const unsigned *sbase = p.base;
+    int *smeta = p.meta;
     if (pre) {
         // the restricted count listed the kept pairs: place only those
         unsigned *cursor = p.hist;
-        { StageTimer _t(STAGE_SCATTER, st); k_copy_starts<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.base, p.meta, cursor); }
         const size_t bsm = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
+        if (p.resplit) {
+            const int S2 = std::min(p.S, RESPLIT_S);
+            { StageTimer _t(STAGE_SAMPLE, st); k_list_sample<G><<<(S2 + 255) / 256, 256, 0, st>>>(pts, p.ev2, p.meta + 6, S2, p.skeys); }
+            { StageTimer _t(STAGE_SAMPLE_SORT, st); k_sort_chunks<<<S2 / SORT_CHUNK, SORT_CHUNK / 2, 0, st>>>(p.skeys); }
+            long long *src = p.skeys, *dst = p.skeys2;
+            for (int width = SORT_CHUNK; width < S2; width <<= 1) {
+                { StageTimer _t(STAGE_SAMPLE_SORT, st); k_merge_runs<<<(S2 + 255) / 256, 256, 0, st>>>(src, dst, S2, width); }
+                long long *t = src; src = dst; dst = t;
+            }
+            {
+                StageTimer _t(STAGE_SPLITTERS, st);
+                k_splitters<<<1, 1024, 0, st>>>(src, S2, BND_MAX / 2, p.bnd2, p.meta2, p.meta + 6, RESPLIT_PER);
+            }
+            if (cudaMemsetAsync(p.base2, 0, (size_t)(BND_MAX + 1) * 4, st) != cudaSuccess) return cudaGetLastError();
+            cudaFuncSetAttribute(k_list_hist<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+            { StageTimer _t(STAGE_COUNT_PAIRS, st); k_list_hist<G><<<p.C, CNT_THREADS, bsm, st>>>(pts, p.bnd2, p.meta2, p.ev2, p.meta + 6, p.base2); }
+            { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base2, p.meta2); }
+            sbnd = p.bnd2;
+            sbase = p.base2;
+            smeta = p.meta2;
+        }
+        { StageTimer _t(STAGE_SCATTER, st); k_copy_starts<<<(BND_MAX + 255) / 256, 256, 0, st>>>(sbase, smeta, cursor); }
         cudaFuncSetAttribute(k_scatter_list<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
         StageTimer _t(STAGE_SCATTER, st);
-        k_scatter_list<G><<<p.C, CNT_THREADS, bsm, st>>>(pts, p.bnd, p.meta, p.ev2, cursor, p.ev);
+        k_scatter_list<G><<<p.C, CNT_THREADS, bsm, st>>>(pts, sbnd, smeta, p.ev2, cursor, p.ev, p.meta + 6);
     } else {
         StageTimer _t(STAGE_SCATTER, st);
         k_bucket_pairs<true, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep,
@@ -2150,11 +2245,11 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
     }
     const size_t seg_smem = (size_t)SEG_CAP * 12;
     cudaFuncSetAttribute(k_segsort<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
-    { StageTimer _t(STAGE_SEGSORT, st); k_segsort<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, p.base, p.bnd, p.meta, p.oversize); }
+    { StageTimer _t(STAGE_SEGSORT, st); k_segsort<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, sbase, sbnd, smeta, p.oversize); }
     if (p.emax > SEG_CAP) {
         cudaFuncSetAttribute(k_segsort_big<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
         StageTimer _t(STAGE_SEGSORT_BIG, st);
-        k_segsort_big<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, p.ev2, p.base, p.meta, p.oversize);
+        k_segsort_big<G><<<p.C, 1024, seg_smem, st>>>(pts, p.ev, p.ev2, sbase, smeta, p.oversize);
     }
     {
         StageTimer _t(STAGE_PLAN, st);
