@@ -56,45 +56,9 @@ __global__ void k_x_center(const int *__restrict__ xy, int n, int *__restrict__ 
     if (threadIdx.x == 0) *xc = (int)(((long long)s_lo + s_hi) / 2);
 }
 
-__device__ void cta_bitonic_i64(long long *a, int P)
-{
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j >= 1; j >>= 1) {
-            for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
-                const int i = 2 * t - (t & (j - 1));
-                const int l = i + j;
-                const bool up = (i & k) == 0;
-                const long long x0 = a[i], x1 = a[l];
-                if ((x0 > x1) == up) { a[i] = x1; a[l] = x0; }
-            }
-            __syncthreads();
-        }
-    }
-}
-
 __device__ __forceinline__ long long zscaled(int p, int xc, long long K)
 {
     return ((long long)py(p) << 32) - (long long)(px(p) - xc) * K;
-}
-
-// min over windows of (hiarr[a + h - 1] - loarr[a]) with a reduction over the CTA.
-__device__ long long cta_min_window(const long long *top, const long long *bot, int n, int h)
-{
-    __shared__ long long s_red[32];
-    long long m = I64_MAX;
-    for (int a = threadIdx.x; a + h - 1 < n; a += blockDim.x) m = min(m, top[a + h - 1] - bot[a]);
-    for (int s = 16; s >= 1; s >>= 1) m = min(m, __shfl_xor_sync(FULL, m, s));
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        m = (threadIdx.x < (blockDim.x >> 5)) ? s_red[threadIdx.x] : I64_MAX;
-        for (int s = 16; s >= 1; s >>= 1) m = min(m, __shfl_xor_sync(FULL, m, s));
-        if (threadIdx.x == 0) s_red[0] = m;
-    }
-    __syncthreads();
-    const long long r = s_red[0];
-    __syncthreads();
-    return r;
 }
 
 // CTA-wide minimum and maximum (every thread returns both).
@@ -143,6 +107,57 @@ __device__ long long cta_min_window32(const unsigned *top, const unsigned *bot, 
     return r;
 }
 
+// Point sets up to BNB_SMEM_N are sorted whole in shared memory (32-bit
+// keys: the words plus merge scratch, 128 KB, or two arrays plus scratch,
+// 192 KB, at the limit).  Larger sets are sorted in chunks of BNB_SMEM_N
+// keys in shared memory, merged in global scratch.
+constexpr int BNB_SMEM_N = 16384;
+
+// Merge of the sorted runs a[0, len) and b[0, len) into out[0, 2 len), all
+// in global memory: every thread writes an equal share of the outputs, its
+// start on the merge path found by a binary search on its diagonal (the
+// split with a[i - 1] <= b[d - i]; equal keys are interchangeable).
+__device__ void cta_merge_global_u32(const unsigned *a, const unsigned *b, int len, unsigned *out)
+{
+    const int total = 2 * len;
+    const int per = (total + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int d = (int)threadIdx.x * per;
+    if (d >= total) return;
+    int lo = d > len ? d - len : 0, hi = d < len ? d : len;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (a[m] <= b[d - 1 - m]) lo = m + 1; else hi = m;
+    }
+    int i = lo, j = d - lo;
+    for (int o = d; o < d + per && o < total; ++o) {
+        const bool take_a = j >= len || (i < len && a[i] <= b[j]);
+        out[o] = take_a ? a[i++] : b[j++];
+    }
+}
+
+// Ascending sort of the P keys key(0 .. P - 1) (P a power of two above
+// BNB_SMEM_N) into global memory: chunks of BNB_SMEM_N keys are merge-sorted
+// in shared memory (s: 2 BNB_SMEM_N words) and written to A, then runs are
+// merged pairwise between A and B.  Returns the buffer holding the result.
+// Every thread of the CTA calls it.
+template <class F>
+__device__ unsigned *cta_sort_chunked_u32(unsigned *s, unsigned *A, unsigned *B, int P, F key)
+{
+    constexpr int Q = BNB_SMEM_N;
+    for (int c = 0; c < P; c += Q) {
+        cta_fill_merge_sort<Q / 1024>(s, s + Q, Q, [&](int k) { return key(c + k); });
+        for (int k = threadIdx.x; k < Q; k += blockDim.x) A[c + k] = s[k];
+        __syncthreads();
+    }
+    unsigned *src = A, *dst = B;
+    for (int len = Q; len < P; len <<= 1) {
+        for (int r = 0; r < P; r += 2 * len) cta_merge_global_u32(src + r, src + r + len, len, dst + r);
+        __syncthreads();
+        unsigned *t = src; src = dst; dst = t;
+    }
+    return src;
+}
+
 // Upper bounds: the window width w at dyadic slopes keys[q] (one CTA per
 // slope).  In shared memory the projections are sorted as 32-bit keys
 // k = (Z - Zmin) >> sh, sh the smallest shift that brings their span below
@@ -160,7 +175,7 @@ __global__ void __launch_bounds__(1024) k_score_dyadic(const int *__restrict__ x
     extern __shared__ __align__(16) unsigned char smem[];
     int P = 1;
     while (P < n) P <<= 1;
-    const bool in_smem = n <= SORT_SMEM_N;
+    const bool in_smem = n <= BNB_SMEM_N;
     for (int q = blockIdx.x; q < nk; q += gridDim.x) {
         const long long K = keys[q];
         if (K >= K_GUARD || K <= -K_GUARD) {
@@ -168,33 +183,27 @@ __global__ void __launch_bounds__(1024) k_score_dyadic(const int *__restrict__ x
             continue;
         }
         const int xc = *xcp;
-        if (in_smem) {
-            long long mn = I64_MAX, mx = -I64_MAX;
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                const long long z = zscaled(xy[k], xc, K);
-                mn = min(mn, z);
-                mx = max(mx, z);
-            }
-            cta_min_max(mn, mx);
-            const int sh = key_shift((unsigned long long)(mx - mn));
-            const int Ps = P < (int)blockDim.x ? (int)blockDim.x : P;
-            unsigned *a = reinterpret_cast<unsigned *>(smem);
-            auto key = [&](int k) {
-                return k < n ? (unsigned)((unsigned long long)(zscaled(xy[k], xc, K) - mn) >> sh) : 0xffffffffu;
-            };
-            cta_fill_merge_sort_any(a, a + Ps, Ps, key);
-            const long long wk = cta_min_window32(a, a, n, h);
-            if (threadIdx.x == 0) out[q] = sh ? (wk + 1) << sh : wk;
-            __syncthreads();
-            continue;
+        long long mn = I64_MAX, mx = -I64_MAX;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const long long z = zscaled(xy[k], xc, K);
+            mn = min(mn, z);
+            mx = max(mx, z);
         }
-        long long *a = gscratch + (size_t)blockIdx.x * 2 * P;
-        auto z = [&](int k) { return k < n ? zscaled(xy[k], xc, K) : I64_MAX; };
-        for (int k = threadIdx.x; k < P; k += blockDim.x) a[k] = z(k);
-        __syncthreads();
-        cta_bitonic_i64(a, P);
-        const long long w = cta_min_window(a, a, n, h);
-        if (threadIdx.x == 0) out[q] = w;
+        cta_min_max(mn, mx);
+        const int sh = key_shift((unsigned long long)(mx - mn));
+        unsigned *a = reinterpret_cast<unsigned *>(smem);
+        auto key = [&](int k) {
+            return k < n ? (unsigned)((unsigned long long)(zscaled(xy[k], xc, K) - mn) >> sh) : 0xffffffffu;
+        };
+        if (in_smem) {
+            const int Ps = P < (int)blockDim.x ? (int)blockDim.x : P;
+            cta_fill_merge_sort_any(a, a + Ps, Ps, key);
+        } else {
+            unsigned *g = reinterpret_cast<unsigned *>(gscratch + (size_t)blockIdx.x * 2 * P);
+            a = cta_sort_chunked_u32(a, g, g + P, P, key);
+        }
+        const long long wk = cta_min_window32(a, a, n, h);
+        if (threadIdx.x == 0) out[q] = sh ? (wk + 1) << sh : wk;
         __syncthreads();
     }
 }
@@ -216,7 +225,7 @@ __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, in
     extern __shared__ __align__(16) unsigned char smem[];
     int P = 1;
     while (P < n) P <<= 1;
-    const bool in_smem = n <= SORT_SMEM_N;
+    const bool in_smem = n <= BNB_SMEM_N;
     const int nnodes = *nnodes_dev;
     for (int q = blockIdx.x; q < nnodes; q += gridDim.x) {
         const long long Klo = node_keys[2 * q], Khi = node_keys[2 * q + 1];
@@ -225,49 +234,39 @@ __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, in
             continue;
         }
         const int xc = *xcp;
-        long long lb;
+        long long mn = I64_MAX, mx = -I64_MAX;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const long long za = zscaled(xy[k], xc, Klo), zb = zscaled(xy[k], xc, Khi);
+            mn = min(mn, min(za, zb));
+            mx = max(mx, max(za, zb));
+        }
+        cta_min_max(mn, mx);
+        const int sh = key_shift((unsigned long long)(mx - mn));
+        const unsigned long long up = (1ull << sh) - 1ull;
+        auto klo = [&](int k) {
+            if (k >= n) return 0xffffffffu;
+            const long long za = zscaled(xy[k], xc, Klo), zb = zscaled(xy[k], xc, Khi);
+            return (unsigned)((unsigned long long)(min(za, zb) - mn) >> sh);
+        };
+        auto khi = [&](int k) {
+            if (k >= n) return 0xffffffffu;
+            const long long za = zscaled(xy[k], xc, Klo), zb = zscaled(xy[k], xc, Khi);
+            return (unsigned)(((unsigned long long)(max(za, zb) - mn) + up) >> sh);
+        };
+        unsigned *lo = reinterpret_cast<unsigned *>(smem), *hi;
         if (in_smem) {
-            long long mn = I64_MAX, mx = -I64_MAX;
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                const long long za = zscaled(xy[k], xc, Klo), zb = zscaled(xy[k], xc, Khi);
-                mn = min(mn, min(za, zb));
-                mx = max(mx, max(za, zb));
-            }
-            cta_min_max(mn, mx);
-            const int sh = key_shift((unsigned long long)(mx - mn));
-            const unsigned long long up = (1ull << sh) - 1ull;
             const int Ps = P < (int)blockDim.x ? (int)blockDim.x : P;
-            unsigned *lo = reinterpret_cast<unsigned *>(smem);
-            unsigned *hi = lo + Ps;
-            auto klo = [&](int k) {
-                if (k >= n) return 0xffffffffu;
-                const long long za = zscaled(xy[k], xc, Klo), zb = zscaled(xy[k], xc, Khi);
-                return (unsigned)((unsigned long long)(min(za, zb) - mn) >> sh);
-            };
-            auto khi = [&](int k) {
-                if (k >= n) return 0xffffffffu;
-                const long long za = zscaled(xy[k], xc, Klo), zb = zscaled(xy[k], xc, Khi);
-                return (unsigned)(((unsigned long long)(max(za, zb) - mn) + up) >> sh);
-            };
+            hi = lo + Ps;
             cta_fill_merge_sort_any(lo, hi + Ps, Ps, klo);
             cta_fill_merge_sort_any(hi, hi + Ps, Ps, khi);
-            lb = cta_min_window32(lo, hi, n, h);
-            lb = lb < 0 ? 0 : lb << sh;
         } else {
-            long long *lo = gscratch + (size_t)blockIdx.x * 2 * P;
-            long long *hi = lo + P;
-            for (int k = threadIdx.x; k < P; k += blockDim.x) {
-                const long long za = k < n ? zscaled(xy[k], xc, Klo) : I64_MAX;
-                const long long zb = k < n ? zscaled(xy[k], xc, Khi) : I64_MAX;
-                lo[k] = min(za, zb);
-                hi[k] = max(za, zb);
-            }
-            __syncthreads();
-            cta_bitonic_i64(lo, P);
-            cta_bitonic_i64(hi, P);
-            lb = cta_min_window(lo, hi, n, h);
-            if (lb < 0) lb = 0;
+            unsigned *g = reinterpret_cast<unsigned *>(gscratch + (size_t)blockIdx.x * 2 * P);
+            unsigned *s = lo;
+            lo = cta_sort_chunked_u32(s, g, g + P, P, klo);
+            hi = cta_sort_chunked_u32(s, g + 2 * P, g + 3 * P, P, khi);
         }
+        long long lb = cta_min_window32(lo, hi, n, h);
+        lb = lb < 0 ? 0 : lb << sh;
         if (threadIdx.x == 0) {
             lb_out[q] = lb;
             prune[q] = lb > *ub ? 1 : 0;
@@ -892,7 +891,7 @@ size_t bnb_extra_bytes(int n, int sms)
     b += a256((size_t)(BND_MAX + 1) * 4);            // their prefix
     b += a256((size_t)(BND_MAX + 1) * 2 * 4);        // runs of kept buckets
     b += a256((size_t)PRE_MAX * sizeof(float2));     // slope pre-filter of the restricted pair passes
-    b += (n > SORT_SMEM_N) ? a256((size_t)grid * 2 * P * 8) : 0;
+    b += (n > BNB_SMEM_N) ? a256((size_t)grid * 2 * P * 8) : 0;   // chunked sorts: four key arrays per CTA
     return b;
 }
 
@@ -930,7 +929,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     float2 *pre = (float2 *)take((size_t)PRE_MAX * sizeof(float2));
     int P = 1;
     while (P < n) P <<= 1;
-    long long *gscr = (n > SORT_SMEM_N) ? (long long *)take((size_t)2 * sms * 2 * P * 8) : nullptr;
+    long long *gscr = (n > BNB_SMEM_N) ? (long long *)take((size_t)2 * sms * 2 * P * 8) : nullptr;
     const int grid = 2 * sms;
 
     if (launch_sweep_sample(p, x, y, st) != cudaSuccess) return LMS_ERR_CUDA;
@@ -946,8 +945,8 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     }
     const int Ps = P < 1024 ? 1024 : P;   // the shared-memory sorts fill whole 1024-thread CTAs
     // 32-bit keys: one sorted array plus merge scratch; two sorted arrays plus scratch
-    const size_t one_sort = (n <= SORT_SMEM_N) ? (size_t)2 * Ps * 4 : 0;
-    const size_t two_sorts = (n <= SORT_SMEM_N) ? (size_t)3 * Ps * 4 : 0;
+    const size_t one_sort = (n <= BNB_SMEM_N) ? (size_t)2 * Ps * 4 : (size_t)2 * BNB_SMEM_N * 4;
+    const size_t two_sorts = (n <= BNB_SMEM_N) ? (size_t)3 * Ps * 4 : (size_t)2 * BNB_SMEM_N * 4;
     cudaFuncSetAttribute(k_score_dyadic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one_sort);
     cudaFuncSetAttribute(k_node_lb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_sorts);
     {

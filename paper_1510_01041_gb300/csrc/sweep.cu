@@ -40,7 +40,7 @@ namespace {
 constexpr long long KEY_INF = 0x7fffffffffffffffLL;
 constexpr int TILE = 64;          // pair tile edge of the count / scatter passes
 constexpr int CNT_THREADS = 512;  // threads of a count / scatter CTA
-constexpr int SORT_CHUNK = 1024;  // sample keys sorted per shared-memory chunk
+constexpr int SORT_CHUNK = 1024;  // smallest sample (one CTA of the chunk sort)
 #ifndef SWEEP_RANGE_FACTOR
 #define SWEEP_RANGE_FACTOR 4
 #endif
@@ -136,43 +136,53 @@ __global__ void k_sample(const void *__restrict__ pts, int n, long long npairs, 
     out[k] = G::key(pts, i, j, key) ? key : KEY_INF;
 }
 
-// Bitonic sort of one chunk of SORT_CHUNK keys in shared memory.
-__global__ void __launch_bounds__(SORT_CHUNK / 2) k_sort_chunks(long long *__restrict__ keys)
+// The sample (S keys, a power of two) is sorted in chunks of up to
+// SAMPLE_CH keys, one CTA each, by the shared-memory merge sort, then the
+// chunks are merged in one pass by ranking.
+constexpr int SAMPLE_CH = 8192;
+
+__global__ void __launch_bounds__(1024) k_sort_chunks(long long *__restrict__ keys, int S)
 {
-    __shared__ long long s[SORT_CHUNK];
-    long long *g = keys + (size_t)blockIdx.x * SORT_CHUNK;
-    for (int k = threadIdx.x; k < SORT_CHUNK; k += blockDim.x) s[k] = g[k];
-    __syncthreads();
-    for (int k = 2; k <= SORT_CHUNK; k <<= 1) {
-        for (int j = k >> 1; j >= 1; j >>= 1) {
-            const int t = threadIdx.x;
-            const int i = 2 * t - (t & (j - 1));
-            const int l = i + j;
-            const bool up = (i & k) == 0;
-            const long long a = s[i], b = s[l];
-            if ((a > b) == up) { s[i] = b; s[l] = a; }
-            __syncthreads();
-        }
-    }
-    for (int k = threadIdx.x; k < SORT_CHUNK; k += blockDim.x) g[k] = s[k];
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long *s = reinterpret_cast<long long *>(smem);
+    const int P = S < SAMPLE_CH ? S : SAMPLE_CH;
+    long long *g = keys + (size_t)blockIdx.x * P;
+    cta_fill_merge_sort_any(s, s + P, P, [&](int k) { return g[k]; });
+    for (int k = threadIdx.x; k < P; k += blockDim.x) g[k] = s[k];
 }
 
-// Stable merge of neighbouring sorted runs of length `width` by ranking.
-__global__ void k_merge_runs(const long long *__restrict__ src, long long *__restrict__ dst, int S, int width)
+// Merge of the S / SAMPLE_CH sorted chunks (at most 16) by ranking: the key
+// at position p of chunk c goes to p plus the number of keys <= it in the
+// chunks before c and < it in the chunks after (a stable order, every
+// position taken once).  The binary searches over the chunks are
+// independent and run together.
+__global__ void __launch_bounds__(256) k_merge_chunks(const long long *__restrict__ src, long long *__restrict__ dst,
+                                                      int S)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= S) return;
-    const int run = k / width, p = k - run * width;
-    const int pair_base = (run & ~1) * width;
+    const int nch = S / SAMPLE_CH, c = k / SAMPLE_CH;
     const long long v = src[k];
-    const long long *other = src + (size_t)(run ^ 1) * width;
-    int lo = 0, hi = width;
-    if ((run & 1) == 0) {          // left run: count right elements < v
-        while (lo < hi) { int m = (lo + hi) >> 1; if (other[m] < v) lo = m + 1; else hi = m; }
-    } else {                       // right run: count left elements <= v
-        while (lo < hi) { int m = (lo + hi) >> 1; if (other[m] <= v) lo = m + 1; else hi = m; }
+    int r = k - c * SAMPLE_CH;
+#pragma unroll
+    for (int c2 = 0; c2 < 16; ++c2) {
+        if (c2 >= nch || c2 == c) continue;
+        const long long *o = src + (size_t)c2 * SAMPLE_CH;
+        int pos = 0;
+        if (c2 < c) {
+#pragma unroll
+            for (int step = SAMPLE_CH / 2; step >= 1; step >>= 1)
+                if (o[pos + step - 1] <= v) pos += step;
+            pos += o[pos] <= v;   // the loop leaves the last key untested
+        } else {
+#pragma unroll
+            for (int step = SAMPLE_CH / 2; step >= 1; step >>= 1)
+                if (o[pos + step - 1] < v) pos += step;
+            pos += o[pos] < v;
+        }
+        r += pos;
     }
-    dst[pair_base + p + lo] = v;
+    dst[r] = v;
 }
 
 // ---------------------------------------------------------------- splitters
@@ -2130,9 +2140,20 @@ void sweep_plan_carve(SweepPlan &p, void *ws)
 
 const long long *sorted_sample(const SweepPlan &p)
 {
-    int rounds = 0;
-    for (int width = SORT_CHUNK; width < p.S; width <<= 1) ++rounds;
-    return (rounds & 1) ? p.skeys2 : p.skeys;
+    return p.S > SAMPLE_CH ? p.skeys2 : p.skeys;
+}
+
+// Sorts S sampled keys (a power of two, SORT_CHUNK .. 16 SAMPLE_CH) held in
+// keys, scratch beside; returns the array that holds the sorted keys.
+static long long *sort_sample(long long *keys, long long *scratch, int S, cudaStream_t st)
+{
+    const int P = std::min(S, SAMPLE_CH);
+    const size_t smem = (size_t)2 * P * 8;
+    cudaFuncSetAttribute(k_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    { StageTimer _t(STAGE_SAMPLE_SORT, st); k_sort_chunks<<<S / P, 1024, smem, st>>>(keys, S); }
+    if (S <= SAMPLE_CH) return keys;
+    { StageTimer _t(STAGE_SAMPLE_SORT, st); k_merge_chunks<<<(S + 255) / 256, 256, 0, st>>>(keys, scratch, S); }
+    return scratch;
 }
 
 template <class G>
@@ -2140,12 +2161,7 @@ static cudaError_t events_sample(const SweepPlan &p, const void *pts, cudaStream
 {
     const int n = p.n;
     { StageTimer _t(STAGE_SAMPLE, st); k_sample<G><<<(p.S + 255) / 256, 256, 0, st>>>(pts, n, p.emax, p.S, p.skeys); }
-    { StageTimer _t(STAGE_SAMPLE_SORT, st); k_sort_chunks<<<p.S / SORT_CHUNK, SORT_CHUNK / 2, 0, st>>>(p.skeys); }
-    long long *src = p.skeys, *dst = p.skeys2;
-    for (int width = SORT_CHUNK; width < p.S; width <<= 1) {
-        { StageTimer _t(STAGE_SAMPLE_SORT, st); k_merge_runs<<<(p.S + 255) / 256, 256, 0, st>>>(src, dst, p.S, width); }
-        long long *t = src; src = dst; dst = t;
-    }
+    const long long *src = sort_sample(p.skeys, p.skeys2, p.S, st);
     { StageTimer _t(STAGE_SPLITTERS, st); k_splitters<<<1, 1024, 0, st>>>(src, p.S, p.B, p.bnd, p.meta); }
     return cudaGetLastError();
 }
@@ -2216,12 +2232,7 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
         if (p.resplit) {
             const int S2 = std::min(p.S, RESPLIT_S);
             { StageTimer _t(STAGE_SAMPLE, st); k_list_sample<G><<<(S2 + 255) / 256, 256, 0, st>>>(pts, p.ev2, p.meta + 6, S2, p.skeys); }
-            { StageTimer _t(STAGE_SAMPLE_SORT, st); k_sort_chunks<<<S2 / SORT_CHUNK, SORT_CHUNK / 2, 0, st>>>(p.skeys); }
-            long long *src = p.skeys, *dst = p.skeys2;
-            for (int width = SORT_CHUNK; width < S2; width <<= 1) {
-                { StageTimer _t(STAGE_SAMPLE_SORT, st); k_merge_runs<<<(S2 + 255) / 256, 256, 0, st>>>(src, dst, S2, width); }
-                long long *t = src; src = dst; dst = t;
-            }
+            const long long *src = sort_sample(p.skeys, p.skeys2, S2, st);
             {
                 StageTimer _t(STAGE_SPLITTERS, st);
                 k_splitters<<<1, 1024, 0, st>>>(src, S2, BND_MAX / 2, p.bnd2, p.meta2, p.meta + 6, RESPLIT_PER);
