@@ -219,10 +219,49 @@ __device__ __forceinline__ int merge_slot(int p)
     return p ^ ((p / R) & (R - 1));
 }
 
+// Ascending bitonic sort of the 32 IPT words a warp holds, IPT per lane in
+// v (lane l holds positions l IPT .. l IPT + IPT - 1).  For the pair at
+// positions i < i ^ j of merge size k the smaller value goes to i when
+// i & k == 0; with positions counted inside the warp every run of the last
+// merge (k = 32 IPT) is ascending.  Partners within a lane are compared in
+// registers, partners in other lanes are exchanged by shuffles.
+template <int IPT, class T>
+__device__ __forceinline__ void warp_sort_blocked(T (&v)[IPT])
+{
+    const int lane = threadIdx.x & 31;
+    const int base = lane * IPT;
+#pragma unroll
+    for (int k = 2; k <= 32 * IPT; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j >= IPT; j >>= 1) {
+            const int m = j / IPT;
+            const bool lower = (lane & m) == 0;
+#pragma unroll
+            for (int r = 0; r < IPT; ++r) {
+                const T o = __shfl_xor_sync(FULL, v[r], m);
+                const bool up = ((base + r) & k) == 0;
+                v[r] = (lower == up) ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
+            }
+        }
+#pragma unroll
+        for (int j = (k >> 1) < IPT ? (k >> 1) : IPT / 2; j >= 1; j >>= 1) {
+#pragma unroll
+            for (int r = 0; r < IPT; ++r) {
+                const int q = r ^ j;
+                if (q > r) {
+                    const bool up = ((base + r) & k) == 0;
+                    const T a = v[r], b = v[q];
+                    if ((a > b) == up) { v[r] = b; v[q] = a; }
+                }
+            }
+        }
+    }
+}
+
 // Ascending merge sort of P = IPT * blockDim.x words held IPT per thread in
 // v (thread t holds positions t IPT ..), result in s (plain order); s2 is
-// scratch of P words.  Each thread sorts its IPT words in registers
-// (bitonic network), then runs of width w = IPT, 2 IPT, .. are merged
+// scratch of P words.  Each warp sorts its 32 IPT words in registers
+// (warp_sort_blocked), then runs of width w = 32 IPT, 64 IPT, .. are merged
 // pairwise: thread t produces the IPT outputs starting at t IPT of its
 // merged run, finding its start on the merge path by a binary search (the
 // diagonal split with A[i - 1] <= B[d - i], ties taken from the left run)
@@ -233,34 +272,20 @@ template <int IPT, class T>
 __device__ __forceinline__ void cta_merge_sort(T (&v)[IPT], T *s, T *s2, int P)
 {
     static_assert(sizeof(T) == 4 || sizeof(T) == 8, "merge_slot assumes 4- or 8-byte words");
-#pragma unroll
-    for (int k = 2; k <= IPT; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j >= 1; j >>= 1) {
-#pragma unroll
-            for (int r = 0; r < IPT; ++r) {
-                const int q = r ^ j;
-                if (q > r) {
-                    const bool up = (r & k) == 0;
-                    const T a = v[r], b = v[q];
-                    if ((a > b) == up) { v[r] = b; v[q] = a; }
-                }
-            }
-        }
-    }
+    warp_sort_blocked<IPT>(v);
     const int t = threadIdx.x;
     const int o = t * IPT;
     // the number of merge levels decides where the first write goes so that
     // the last one lands in s
     int levels = 0;
-    for (int w = IPT; w < P; w <<= 1) ++levels;
+    for (int w = 32 * IPT; w < P; w <<= 1) ++levels;
     const bool swz = P % (128 / (int)sizeof(T)) == 0;   // whole rows: the slots are a permutation
     auto slot = [&](int p) { return swz ? merge_slot<T>(p) : p; };
     T *src = (levels & 1) ? s2 : s, *dst = (levels & 1) ? s : s2;
 #pragma unroll
     for (int r = 0; r < IPT; ++r) src[levels ? slot(o + r) : o + r] = v[r];
     __syncthreads();
-    for (int w = IPT; w < P; w <<= 1) {
+    for (int w = 32 * IPT; w < P; w <<= 1) {
         const bool last = 2 * w >= P;
         const int base = o & ~(2 * w - 1);       // start of this thread's merged run
         const int d = o - base;                   // output offset inside it
