@@ -40,20 +40,66 @@ namespace {
 constexpr long long I64_MAX = 0x7fffffffffffffffLL;
 constexpr long long K_GUARD = 1LL << 46;
 
-__global__ void k_x_center(const int *__restrict__ xy, int n, int *__restrict__ xc)
+// Set constants of the bounds, into xs[0 .. 2]: the midrange of x (the
+// common shift of the projections), dh, a lower bound of the x-span of any
+// h points (h points take at least ceil(h / m) distinct integer x, m the
+// largest number of points sharing one x, so they span at least that less
+// one), and the y range.  The x histogram is kept in shared memory, one half
+// of the int16 range at a time.
+__global__ void __launch_bounds__(1024) k_x_center(const int *__restrict__ xy, int n, int h, int *__restrict__ xs)
 {
-    __shared__ int s_lo, s_hi;
-    if (threadIdx.x == 0) { s_lo = 0x7fffffff; s_hi = -0x7fffffff; }
+    extern __shared__ unsigned s_h[];   // 32768 counters
+    __shared__ int s_lo, s_hi, s_ylo, s_yhi;
+    __shared__ unsigned s_m;
+    if (threadIdx.x == 0) { s_lo = s_ylo = 0x7fffffff; s_hi = s_yhi = -0x7fffffff; s_m = 0u; }
     __syncthreads();
-    int lo = 0x7fffffff, hi = -0x7fffffff;
+    int lo = 0x7fffffff, hi = -0x7fffffff, ylo = 0x7fffffff, yhi = -0x7fffffff;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         lo = min(lo, px(xy[k]));
         hi = max(hi, px(xy[k]));
+        ylo = min(ylo, py(xy[k]));
+        yhi = max(yhi, py(xy[k]));
     }
     atomicMin(&s_lo, lo);
     atomicMax(&s_hi, hi);
+    atomicMin(&s_ylo, ylo);
+    atomicMax(&s_yhi, yhi);
+    unsigned m = 0;
+    for (int half = 0; half < 2; ++half) {
+        for (int k = threadIdx.x; k < 32768; k += blockDim.x) s_h[k] = 0u;
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int x = px(xy[k]) + 32768;
+            if ((x >> 15) == half) atomicAdd(&s_h[x & 32767], 1u);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < 32768; k += blockDim.x) m = max(m, s_h[k]);
+        __syncthreads();
+    }
+    atomicMax(&s_m, m);
     __syncthreads();
-    if (threadIdx.x == 0) *xc = (int)(((long long)s_lo + s_hi) / 2);
+    if (threadIdx.x == 0) {
+        xs[0] = (int)(((long long)s_lo + s_hi) / 2);
+        const unsigned mm = s_m ? s_m : 1u;
+        xs[1] = (int)(((unsigned)h + mm - 1u) / mm) - 1;
+        xs[2] = s_yhi - s_ylo;
+    }
+}
+
+// Lower bound of w over slope keys [Klo, Khi] lying wholly on one side of 0
+// (steep or unbounded intervals, where the projections at the ends are not
+// available): any h points span at least dh in x and at most yr in y, so
+// their window at slope s is at least |s| dh - yr; in units of 2^-32,
+// |K| dh - yr 2^32 with K the end nearer 0.  0 when the interval contains 0.
+__device__ __forceinline__ long long steep_lb(long long Klo, long long Khi, int dh, int yr)
+{
+    long long K;
+    if (Khi <= 0 && Khi > -I64_MAX) K = -Khi;
+    else if (Klo >= 0 && Klo < I64_MAX) K = Klo;
+    else return 0;
+    const __int128 v = (__int128)K * dh - ((__int128)yr << 32);
+    if (v <= 0) return 0;
+    return v > (__int128)I64_MAX ? I64_MAX : (long long)v;
 }
 
 __device__ __forceinline__ long long zscaled(int p, int xc, long long K)
@@ -113,51 +159,6 @@ __device__ long long cta_min_window32(const unsigned *top, const unsigned *bot, 
 // keys in shared memory, merged in global scratch.
 constexpr int BNB_SMEM_N = 16384;
 
-// Merge of the sorted runs a[0, len) and b[0, len) into out[0, 2 len), all
-// in global memory: every thread writes an equal share of the outputs, its
-// start on the merge path found by a binary search on its diagonal (the
-// split with a[i - 1] <= b[d - i]; equal keys are interchangeable).
-__device__ void cta_merge_global_u32(const unsigned *a, const unsigned *b, int len, unsigned *out)
-{
-    const int total = 2 * len;
-    const int per = (total + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int d = (int)threadIdx.x * per;
-    if (d >= total) return;
-    int lo = d > len ? d - len : 0, hi = d < len ? d : len;
-    while (lo < hi) {
-        const int m = (lo + hi) >> 1;
-        if (a[m] <= b[d - 1 - m]) lo = m + 1; else hi = m;
-    }
-    int i = lo, j = d - lo;
-    for (int o = d; o < d + per && o < total; ++o) {
-        const bool take_a = j >= len || (i < len && a[i] <= b[j]);
-        out[o] = take_a ? a[i++] : b[j++];
-    }
-}
-
-// Ascending sort of the P keys key(0 .. P - 1) (P a power of two above
-// BNB_SMEM_N) into global memory: chunks of BNB_SMEM_N keys are merge-sorted
-// in shared memory (s: 2 BNB_SMEM_N words) and written to A, then runs are
-// merged pairwise between A and B.  Returns the buffer holding the result.
-// Every thread of the CTA calls it.
-template <class F>
-__device__ unsigned *cta_sort_chunked_u32(unsigned *s, unsigned *A, unsigned *B, int P, F key)
-{
-    constexpr int Q = BNB_SMEM_N;
-    for (int c = 0; c < P; c += Q) {
-        cta_fill_merge_sort<Q / 1024>(s, s + Q, Q, [&](int k) { return key(c + k); });
-        for (int k = threadIdx.x; k < Q; k += blockDim.x) A[c + k] = s[k];
-        __syncthreads();
-    }
-    unsigned *src = A, *dst = B;
-    for (int len = Q; len < P; len <<= 1) {
-        for (int r = 0; r < P; r += 2 * len) cta_merge_global_u32(src + r, src + r + len, len, dst + r);
-        __syncthreads();
-        unsigned *t = src; src = dst; dst = t;
-    }
-    return src;
-}
-
 // Upper bounds: the window width w at dyadic slopes keys[q] (one CTA per
 // slope).  In shared memory the projections are sorted as 32-bit keys
 // k = (Z - Zmin) >> sh, sh the smallest shift that brings their span below
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(1024) k_score_dyadic(const int *__restrict__ x
             cta_fill_merge_sort_any(a, a + Ps, Ps, key);
         } else {
             unsigned *g = reinterpret_cast<unsigned *>(gscratch + (size_t)blockIdx.x * 2 * P);
-            a = cta_sort_chunked_u32(a, g, g + P, P, key);
+            a = cta_sort_chunked<BNB_SMEM_N>(a, g, g + P, P, key);
         }
         const long long wk = cta_min_window32(a, a, n, h);
         if (threadIdx.x == 0) out[q] = sh ? (wk + 1) << sh : wk;
@@ -230,7 +231,11 @@ __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, in
     for (int q = blockIdx.x; q < nnodes; q += gridDim.x) {
         const long long Klo = node_keys[2 * q], Khi = node_keys[2 * q + 1];
         if (Klo <= -K_GUARD || Khi >= K_GUARD || Klo >= K_GUARD || Khi <= -K_GUARD) {
-            if (threadIdx.x == 0) { prune[q] = 0; lb_out[q] = 0; }
+            if (threadIdx.x == 0) {
+                const long long lb = steep_lb(Klo, Khi, xcp[1], xcp[2]);
+                lb_out[q] = lb;
+                prune[q] = lb > *ub ? 1 : 0;
+            }
             continue;
         }
         const int xc = *xcp;
@@ -262,8 +267,8 @@ __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, in
         } else {
             unsigned *g = reinterpret_cast<unsigned *>(gscratch + (size_t)blockIdx.x * 2 * P);
             unsigned *s = lo;
-            lo = cta_sort_chunked_u32(s, g, g + P, P, klo);
-            hi = cta_sort_chunked_u32(s, g + 2 * P, g + 3 * P, P, khi);
+            lo = cta_sort_chunked<BNB_SMEM_N>(s, g, g + P, P, klo);
+            hi = cta_sort_chunked<BNB_SMEM_N>(s, g + 2 * P, g + 3 * P, P, khi);
         }
         long long lb = cta_min_window32(lo, hi, n, h);
         lb = lb < 0 ? 0 : lb << sh;
@@ -433,6 +438,7 @@ struct TreeState {
     unsigned swept;          // events in the kept buckets
     int covers;              // slope covers handed to the restricted pair pass
     int nruns;               // runs of consecutive kept buckets
+    int refine;              // sub-intervals of the refinement level
 };
 
 // Page-locked host buffer for the statistics of a fit, one per host thread
@@ -686,18 +692,192 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_step(int level, int sms, 
     if (threadIdx.x == 0) ts->count[(level + 1) & 1] = s_total;
 }
 
-// Slope covers of the runs of kept buckets for the restricted pair pass:
-// bucket b holds keys [bnd[b - 1], bnd[b]), a key being floor(slope 2^32);
-// each run's cover is widened by more than the float slope error (2^-21
-// relative) and rounded outward to floats.  At most PRE_MAX covers: the
-// runs are grouped at the PRE_MAX - 1 widest gaps between neighbouring
-// covers (the same grouping as merging the closest neighbours one at a
-// time); covers that touch after rounding are merged.  The unused entries
-// are +inf, which no slope reaches.
+// ------------------------------------------------------------ sub-bucket refinement
+// The last tree level ends at single buckets, and a bucket's lower bound is
+// weaker than the bound of a narrower interval by about the spread of the
+// projections over the bucket's slope range, which near the optimum (where
+// pair slopes crowd) is what keeps most surviving buckets.  So every kept
+// interior bucket is cut into F_b sub-intervals of equal key width, each
+// bounded once more; the buckets are then replaced by their sub-intervals
+// (new boundaries, a keep flag per sub-interval) for the restricted pass
+// and the sweep.  F = max(2, SMs / kept) (one wave of bounds), at most
+// REFINE_MAX and within the room left under BND_MAX boundaries, and no
+// refinement when more than twice the SM count of buckets survive; F_b =
+// min(F, the bucket's key width).  Both kernels below derive the same
+// F_b and sub-node offsets from the same inputs.
+constexpr int REFINE_MAX = 64;
+// No refinement when the kept buckets hold fewer events than this (by the
+// sampled pairs): a level of bounds costs about as much as sweeping them.
+constexpr long long REFINE_MIN_EVENTS = 1 << 16;
+
+struct RefinePlan {
+    int F;      // sub-intervals per kept bucket (0: no refinement)
+    int total;  // sub-nodes
+};
+
+// Per thread: PER consecutive buckets; fb[r] = F_b (0 when the bucket is not cut).
+// scount: sampled pairs per bucket (S sampled of emax pairs).
+template <int PER>
+__device__ RefinePlan refine_plan(const int *__restrict__ meta, const long long *__restrict__ bnd,
+                                  const unsigned char *__restrict__ keep, const unsigned *__restrict__ scount,
+                                  int S, long long emax, int sms, int (&fb)[PER], int &off, long long *s_warp)
+{
+    __shared__ int s_F;
+    __shared__ long long s_tot;
+    const int NB = meta[0] + 1, nbnd = meta[0];
+    const int b_beg = threadIdx.x * PER;
+    int cut = 0;
+    long long smp = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int b = b_beg + r;
+        const bool ok = b > 0 && b < NB - 1 && keep[b] && bnd[b] - bnd[b - 1] >= 2;
+        fb[r] = ok ? 1 : 0;
+        cut += ok;
+        smp += ok ? scount[b] : 0;
+    }
+    const long long nk = block_scan<false>(cut, s_warp);
+    const long long nsmp = block_scan<false>(smp, s_warp);
+    if (threadIdx.x == blockDim.x - 1) {
+        int F = 0;
+        const double est = (double)nsmp * (double)emax / (double)S;   // events in the buckets to cut
+        if (nk > 0 && nk <= 2LL * sms && est >= (double)REFINE_MIN_EVENTS) {
+            const long long room = (long long)(BND_MAX - 1 - nbnd);
+            long long f = max(2LL, (long long)sms / nk);
+            f = min(f, 1 + room / nk);
+            f = min(f, (long long)REFINE_MAX);
+            F = f >= 2 ? (int)f : 0;
+        }
+        s_F = F;
+    }
+    __syncthreads();
+    const int F = s_F;
+    long long sum = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int b = b_beg + r;
+        if (fb[r] && F) fb[r] = (int)min((long long)F, bnd[b] - bnd[b - 1]);
+        else fb[r] = 0;
+        sum += fb[r];
+    }
+    const long long inc = block_scan<false>(sum, s_warp);
+    off = (int)(inc - sum);
+    if (threadIdx.x == blockDim.x - 1) s_tot = inc;
+    __syncthreads();
+    RefinePlan rp;
+    rp.F = F;
+    rp.total = (int)s_tot;
+    __syncthreads();
+    return rp;
+}
+
+// Key interval of sub-interval i of the F_b cuts of [lo, hi).
+__device__ __forceinline__ long long sub_key(long long lo, long long hi, int i, int Fb)
+{
+    return lo + (hi - lo) * i / Fb;
+}
+
+__global__ void __launch_bounds__(TREE_THREADS) k_refine_nodes(const int *__restrict__ meta,
+                                                               const long long *__restrict__ bnd,
+                                                               const unsigned char *__restrict__ keep,
+                                                               const unsigned *__restrict__ scount, int S,
+                                                               long long emax, int sms,
+                                                               long long *__restrict__ nkeys,
+                                                               TreeState *__restrict__ ts)
+{
+    __shared__ long long s_warp[32];
+    constexpr int PER = BND_MAX / TREE_THREADS;
+    int fb[PER], off;
+    const RefinePlan rp = refine_plan<PER>(meta, bnd, keep, scount, S, emax, sms, fb, off, s_warp);
+    const int b_beg = threadIdx.x * PER;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        if (!fb[r]) continue;
+        const int b = b_beg + r;
+        const long long lo = bnd[b - 1], hi = bnd[b];
+        for (int i = 0; i < fb[r]; ++i) {
+            nkeys[2 * (off + i)] = sub_key(lo, hi, i, fb[r]);
+            nkeys[2 * (off + i) + 1] = sub_key(lo, hi, i + 1, fb[r]);
+        }
+        off += fb[r];
+    }
+    if (threadIdx.x == 0) ts->refine = rp.total;
+}
+
+// Replace the buckets by their sub-intervals: boundaries and keep flags into
+// the scratch arrays, then copied over bnd (padded with I64_MAX to the new
+// power of two) and keep, and the new counts into meta.
+__global__ void __launch_bounds__(TREE_THREADS) k_refine_apply(int *__restrict__ meta, long long *__restrict__ bnd,
+                                                               unsigned char *__restrict__ keep,
+                                                               const unsigned char *__restrict__ prune,
+                                                               const unsigned *__restrict__ scount, int S,
+                                                               long long emax, int sms,
+                                                               long long *__restrict__ bnd_tmp,
+                                                               unsigned char *__restrict__ keep_tmp,
+                                                               TreeState *__restrict__ ts)
+{
+    __shared__ long long s_warp[32];
+    __shared__ int s_nb;
+    constexpr int PER = BND_MAX / TREE_THREADS;
+    int fb[PER], off;
+    const RefinePlan rp = refine_plan<PER>(meta, bnd, keep, scount, S, emax, sms, fb, off, s_warp);
+    if (rp.total == 0) return;
+    const int NB = meta[0] + 1;
+    const int b_beg = threadIdx.x * PER;
+    // new buckets per old bucket: F_b when cut, else 1
+    long long cnt = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) cnt += (b_beg + r < NB) ? (fb[r] ? fb[r] : 1) : 0;
+    const long long inc = block_scan<false>(cnt, s_warp);
+    if (threadIdx.x == blockDim.x - 1) s_nb = (int)inc;
+    int o = (int)(inc - cnt);
+    int pr = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int b = b_beg + r;
+        if (b >= NB) break;
+        if (fb[r]) {
+            const long long lo = bnd[b - 1], hi = bnd[b];
+            for (int i = 0; i < fb[r]; ++i) {
+                const bool drop = prune[off + i] != 0;
+                pr += drop;
+                keep_tmp[o + i] = drop ? 0 : 1;
+                bnd_tmp[o + i] = i + 1 < fb[r] ? sub_key(lo, hi, i + 1, fb[r]) : hi;
+            }
+            off += fb[r];
+            o += fb[r];
+        } else {
+            keep_tmp[o] = keep[b];
+            if (b < NB - 1) bnd_tmp[o] = bnd[b];
+            ++o;
+        }
+    }
+    const long long pruned = block_scan<false>(pr, s_warp);
+    const int NB2 = s_nb, nbnd2 = NB2 - 1;
+    int P2 = 1;
+    while (P2 <= nbnd2) P2 <<= 1;
+    for (int k = threadIdx.x; k < P2; k += blockDim.x) bnd[k] = k < nbnd2 ? bnd_tmp[k] : I64_MAX;
+    for (int k = threadIdx.x; k < NB2; k += blockDim.x) keep[k] = keep_tmp[k];
+    if (threadIdx.x == blockDim.x - 1) {
+        ts->evaluated += rp.total;
+        ts->pruned += (int)pruned;
+        ts->levels += 1;
+        meta[0] = nbnd2;
+        meta[1] = P2;
+    }
+}
+
+// Covers of the runs of kept buckets for the restricted pair pass: bucket
+// b holds keys [bnd[b - 1], bnd[b]), a key being floor(slope 2^32).  At most
+// PRE_MAX covers: the runs are grouped at the PRE_MAX - 1 widest gaps
+// between neighbouring runs (the same grouping as merging the closest
+// neighbours one at a time; gaps measured in slope); each cover is the key
+// range from its first run's start to its last run's end.  Unused entries
+// are empty ranges.
 __global__ void __launch_bounds__(TREE_THREADS) k_tree_covers(const int *__restrict__ meta,
                                                               const long long *__restrict__ bnd,
                                                               const unsigned char *__restrict__ keep,
-                                                              int *__restrict__ runs, float2 *__restrict__ pre,
+                                                              int *__restrict__ runs, long long *__restrict__ cov,
                                                               TreeState *__restrict__ ts)
 {
     __shared__ long long s_warp[32];
@@ -782,23 +962,25 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_covers(const int *__restr
         for (int t = 0; t < nsep; ++t) sep[t] = s_sep[t];
         for (int a = 1; a < nsep; ++a)
             for (int b = a; b > 0 && sep[b - 1] > sep[b]; --b) { const int tt = sep[b]; sep[b] = sep[b - 1]; sep[b - 1] = tt; }
-        float2 out[PRE_MAX];
+        // cover: the key range from the first bucket of its first run to the
+        // end of its last run (-inf / +inf at the outer buckets)
         int nc = 0;
         if (R == 0) {
-            out[nc++] = make_float2(-INFINITY, INFINITY);   // nothing kept: test every pair
+            cov[0] = -I64_MAX;   // nothing kept: every pair
+            cov[1] = I64_MAX;
+            nc = 1;
         } else {
             int first = 0;
             for (int t = 0; t <= nsep; ++t) {
                 const int last = t < nsep ? sep[t] - 1 : R - 1;
-                float2 f;
-                f.x = nextafterf((float)lo_of(first), -INFINITY);
-                f.y = nextafterf((float)hi_of(last), INFINITY);
-                if (nc > 0 && f.x <= out[nc - 1].y) out[nc - 1].y = fmaxf(out[nc - 1].y, f.y);
-                else out[nc++] = f;
+                const int b0 = runs[2 * first], e1 = runs[2 * last + 1];
+                cov[2 * nc] = b0 == 0 ? -I64_MAX : bnd[b0 - 1];
+                cov[2 * nc + 1] = e1 >= NB ? I64_MAX : bnd[e1 - 1];
+                ++nc;
                 first = last + 1;
             }
         }
-        for (int c = 0; c < PRE_MAX; ++c) pre[c] = c < nc ? out[c] : make_float2(INFINITY, INFINITY);
+        for (int c = nc; c < PRE_MAX; ++c) cov[2 * c] = cov[2 * c + 1] = I64_MAX;   // empty
         ts->covers = nc;
     }
 }
@@ -890,7 +1072,8 @@ size_t bnb_extra_bytes(int n, int sms)
     b += a256((size_t)BND_MAX * 4);                  // sampled pairs per bucket
     b += a256((size_t)(BND_MAX + 1) * 4);            // their prefix
     b += a256((size_t)(BND_MAX + 1) * 2 * 4);        // runs of kept buckets
-    b += a256((size_t)PRE_MAX * sizeof(float2));     // slope pre-filter of the restricted pair passes
+    b += a256((size_t)PRE_MAX * 2 * 8);              // key ranges of the kept covers
+    b += band_scratch_bytes(n);                      // restricted count: sorted words per cover
     b += (n > BNB_SMEM_N) ? a256((size_t)grid * 2 * P * 8) : 0;   // chunked sorts: four key arrays per CTA
     return b;
 }
@@ -926,7 +1109,8 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     unsigned *scount = (unsigned *)take((size_t)BND_MAX * 4);
     unsigned *sbase = (unsigned *)take((size_t)(BND_MAX + 1) * 4);
     int *runs = (int *)take((size_t)(BND_MAX + 1) * 2 * 4);
-    float2 *pre = (float2 *)take((size_t)PRE_MAX * sizeof(float2));
+    long long *cov = (long long *)take((size_t)PRE_MAX * 2 * 8);
+    void *band_scr = take(band_scratch_bytes(n));
     int P = 1;
     while (P < n) P <<= 1;
     long long *gscr = (n > BNB_SMEM_N) ? (long long *)take((size_t)2 * sms * 2 * P * 8) : nullptr;
@@ -936,7 +1120,8 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     if (launch_sample_counts(p, scount, st) != cudaSuccess) return LMS_ERR_CUDA;
     {
         StageTimer _t(STAGE_SEEDS, st);
-        k_x_center<<<1, 1024, 0, st>>>(p.xy, n, xc);
+        cudaFuncSetAttribute(k_x_center, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768 * 4);
+        k_x_center<<<1, 1024, 32768 * 4, st>>>(p.xy, n, h, xc);
     }
     if (pred_ready && cudaStreamWaitEvent(st, pred_ready, 0) != cudaSuccess) return LMS_ERR_CUDA;
     {
@@ -991,16 +1176,25 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         }
     }
     {
+        // kept buckets cut into sub-intervals and bounded once more (lbv and
+        // offs, no longer needed, hold the new boundaries and flags meanwhile)
         StageTimer _t(STAGE_NODE_LB, st);
-        k_tree_covers<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, runs, pre, ts);
+        k_refine_nodes<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, scount, p.S, p.emax, sms, nkeys[0], ts);
+        k_node_lb<<<sms, 1024, two_sorts, st>>>(p.xy, n, h, xc, nkeys[0], &ts->refine, ub, prune, lbv, gscr);
+        k_refine_apply<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, prune, scount, p.S, p.emax, sms, lbv,
+                                                   reinterpret_cast<unsigned char *>(offs), ts);
+    }
+    {
+        StageTimer _t(STAGE_NODE_LB, st);
+        k_tree_covers<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, runs, cov, ts);
     }
     // exact events of the kept buckets only: p.base becomes their starts
-    if (launch_sweep_count(p, keep, pre, PRE_MAX, st) != cudaSuccess) return LMS_ERR_CUDA;
+    if (launch_sweep_count(p, keep, cov, band_scr, stats != nullptr, st) != cudaSuccess) return LMS_ERR_CUDA;
     {
         StageTimer _t(STAGE_PLAN, st);
         k_tree_ranges<<<1, TREE_THREADS, 0, st>>>(p.meta, p.base, runs, p.W, p.G, p.range, ts);
     }
-    if (launch_sweep_finish(p, keep, st, false, pre, PRE_MAX) != cudaSuccess) return LMS_ERR_CUDA;
+    if (launch_sweep_finish(p, keep, st, false, true) != cudaSuccess) return LMS_ERR_CUDA;
     if (launch_argmin(p.cands, p.W + p.G, out, LMS_ALGO_BNB, p.meta + 3, st) != cudaSuccess) return LMS_ERR_CUDA;
     if (cudaGetLastError() != cudaSuccess) return LMS_ERR_CUDA;
     if (stats) {

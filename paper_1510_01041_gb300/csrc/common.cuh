@@ -347,6 +347,51 @@ __device__ bool cta_fill_merge_sort_any(T *s, T *s2, int P, F fill)
     }
 }
 
+// Merge of the sorted runs a[0, len) and b[0, len) into out[0, 2 len), all
+// in global memory: every thread writes an equal share of the outputs, its
+// start on the merge path found by a binary search on its diagonal (the
+// split with a[i - 1] <= b[d - i]; equal words are interchangeable).
+template <class T>
+__device__ void cta_merge_global(const T *a, const T *b, int len, T *out)
+{
+    const int total = 2 * len;
+    const int per = (total + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int d = (int)threadIdx.x * per;
+    if (d >= total) return;
+    int lo = d > len ? d - len : 0, hi = d < len ? d : len;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (a[m] <= b[d - 1 - m]) lo = m + 1; else hi = m;
+    }
+    int i = lo, j = d - lo;
+    for (int o = d; o < d + per && o < total; ++o) {
+        const bool take_a = j >= len || (i < len && a[i] <= b[j]);
+        out[o] = take_a ? a[i++] : b[j++];
+    }
+}
+
+// Ascending sort of the P words key(0 .. P - 1) (P a power of two, a
+// multiple of Q) into global memory: chunks of Q words (Q = IPT blockDim.x
+// with IPT in 1 .. 16) are merge-sorted in shared memory (s: 2 Q words)
+// and written to A, then runs are merged pairwise between A and B.
+// Returns the buffer holding the result.  Every thread of the CTA calls it.
+template <int Q, class T, class F>
+__device__ T *cta_sort_chunked(T *s, T *A, T *B, int P, F key)
+{
+    for (int c = 0; c < P; c += Q) {
+        cta_fill_merge_sort_any(s, s + Q, Q, [&](int k) { return key(c + k); });
+        for (int k = threadIdx.x; k < Q; k += blockDim.x) A[c + k] = s[k];
+        __syncthreads();
+    }
+    T *src = A, *dst = B;
+    for (int len = Q; len < P; len <<= 1) {
+        for (int r = 0; r < P; r += 2 * len) cta_merge_global(src + r, src + r + len, len, dst + r);
+        __syncthreads();
+        T *t = src; src = dst; dst = t;
+    }
+    return src;
+}
+
 // Fills P = IPT * blockDim.x words with fill(position), sorts them and
 // leaves the ascending result in s.
 template <int IPT, class T, class F>

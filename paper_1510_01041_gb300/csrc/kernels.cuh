@@ -144,23 +144,26 @@ cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short
 // plan = false: the caller has written the range bounds (any event offsets
 // inside runs of kept buckets); they are moved to group starts on the device
 cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan,
-                                const float2 *pre = nullptr, int npre = 0);
+                                bool listed = false);
 const long long *sorted_sample(const SweepPlan &p);
 // generic halves of the event pipeline (sample .. bucket starts; scatter .. plan)
 template <class G> cudaError_t launch_events_prepare(const SweepPlan &p, const void *pts, cudaStream_t st);
 template <class G>
 cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsigned char *keep, cudaStream_t st,
-                                 bool plan, const float2 *pre = nullptr, int npre = 0);
-// Restriction of the pair passes to kept buckets: a pair is examined
-// further only if its float slope lies in one of the npre intervals pre
-// (outward-rounded covers of the kept slope ranges) and its bucket is kept.
+                                 bool plan, bool listed = false);
+// A restricted pass (the branch-and-bound's) lists the pairs whose exact
+// slope key lies in a kept bucket; the kept buckets form at most PRE_MAX
+// covers, given as key ranges [cov[2c], cov[2c + 1]) (unused covers empty).
 constexpr int PRE_MAX = 8;
-// the sample half of the prepare step (pack, sample, sort, splitters) and
-// the count half (count, prefix, scan) restricted as above; pairs with
-// distinct x are counted into meta[5]
+// the sample half of the prepare step (pack, sample, sort, splitters), and
+// the restricted count (the kept pairs listed into ev2 and counted per
+// bucket, then prefix and scan)
 cudaError_t launch_sweep_sample(const SweepPlan &p, const short *x, const short *y, cudaStream_t st);
-cudaError_t launch_sweep_count(const SweepPlan &p, const unsigned char *keep, const float2 *pre, int npre,
-                               cudaStream_t st);
+// scratch: band_scratch_bytes(n); distinct_x: also count the pairs with
+// distinct x into meta[5]
+size_t band_scratch_bytes(int n);
+cudaError_t launch_sweep_count(const SweepPlan &p, const unsigned char *keep, const long long *cov, void *scratch,
+                               bool distinct_x, cudaStream_t st);
 // per-bucket counts of the valid sampled pairs into counts[0 .. NB)
 cudaError_t launch_sample_counts(const SweepPlan &p, unsigned *counts, cudaStream_t st);
 // float32 points: event pipeline on the double slope key, double-precision

@@ -251,52 +251,10 @@ __global__ void __launch_bounds__(1024) k_splitters(const long long *__restrict_
 }
 
 // ---------------------------------------------------------------- count / scatter
-// Float pre-test of a restricted pass: 0 when x_i == x_j (no slope), 1 when
-// the slope lies outside every cover, 2 for a candidate.  The restricted
-// count and the restricted scatter both call it, so they keep the same pairs.
-// Pi: the packed point i (int16 points only); cov: PRE_MAX covers in shared
-// memory (sorted, disjoint, rounded outward, unused ones at +inf).  For int16
-// points the slope is never divided out: with dx > 0, lo <= dy / dx is
-// tested as lo dx <= dy in float (dx, dy exact, one rounding of relative size
-// 2^-24 per product, far inside the covers' margin of 2^-18 relative): the
-// last cover whose lower end the slope reaches, found by a binary search,
-// must reach past it.
-template <class G>
-__device__ __forceinline__ int pre_test(const void *pts, int Pi, int i, int j, const float2 *cov)
-{
-    int c = 0;
-    if constexpr (std::is_same<G, KeyI16>::value) {
-        const int Pj = __ldg(static_cast<const int *>(pts) + j);
-        int dx = px(Pj) - px(Pi), dy = py(Pj) - py(Pi);
-        if (dx == 0) return 0;
-        if (dx < 0) { dx = -dx; dy = -dy; }
-        const float fx = (float)dx, fy = (float)dy;
-#pragma unroll
-        for (int step = PRE_MAX; step >= 1; step >>= 1)
-            if (cov[c + step - 1].x * fx <= fy) c += step;
-        return (c > 0 && fy <= cov[c - 1].y * fx) ? 2 : 1;
-    } else {
-        float sl;
-        if (!G::approx(pts, i, j, sl)) return 0;
-#pragma unroll
-        for (int step = PRE_MAX; step >= 1; step >>= 1)
-            if (cov[c + step - 1].x <= sl) c += step;
-        return (c > 0 && sl <= cov[c - 1].y) ? 2 : 1;
-    }
-}
-
-// The covers of a restricted pass in shared memory: the first npre entries
-// of pre, then +inf (2 PRE_MAX entries, so the search never reads past).
-__device__ __forceinline__ void load_covers(const float2 *__restrict__ pre, int npre, float2 *s_cov)
-{
-    if (threadIdx.x < 2 * PRE_MAX)
-        s_cov[threadIdx.x] = (int)threadIdx.x < npre ? pre[threadIdx.x] : make_float2(INFINITY, INFINITY);
-}
-
 // Both passes walk the same upper-triangle tiles in the same static order,
 // so the scatter's per-CTA bucket cursors match the counts exactly.  (A
-// restricted fit counts with k_count_restricted, which lists its pairs; the
-// scatter then places the list, k_scatter_list, whatever the tiling.)
+// restricted fit lists its pairs with the band scan below; the scatter then
+// places the list, k_scatter_list, whatever the order.)
 template <bool SCATTER, class G>
 __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__restrict__ pts, int n,
                                                               const long long *__restrict__ bnd,
@@ -304,14 +262,11 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
                                                               unsigned *__restrict__ hist,
                                                               const unsigned *__restrict__ base,
                                                               unsigned *__restrict__ ev,
-                                                              const unsigned char *__restrict__ keep,
-                                                              const float2 *__restrict__ pre, int npre)
+                                                              const unsigned char *__restrict__ keep)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
     unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
-    __shared__ float2 s_cov[2 * PRE_MAX];
-    if (pre) load_covers(pre, npre, s_cov);
     const int nbnd = meta[0], P2 = meta[1], NB = nbnd + 1;
     for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
     unsigned *my_hist = hist + (size_t)blockIdx.x * BND_MAX;
@@ -328,14 +283,10 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
         tile_decode(q, bi, bj);
         const int i = bi * TILE + il;
         if (i >= n) continue;
-        // int16 points: this thread's fixed point, loaded once per tile
-        int Pi = 0;
-        if constexpr (std::is_same<G, KeyI16>::value) Pi = __ldg(static_cast<const int *>(pts) + i);
 #pragma unroll 4
         for (int jj = 0; jj < JPT; ++jj) {
             const int j = bj * TILE + jl0 + jj;
             if (j <= i || j >= n) continue;
-            if (pre && pre_test<G>(pts, Pi, i, j, s_cov) != 2) continue;
             const int b = pair_bucket<G>(pts, i, j, s_bnd, P2);
             if (b < 0 || (keep && !keep[b])) continue;
             const unsigned slot = atomicAdd(&s_cnt[b], 1u);
@@ -348,122 +299,262 @@ __global__ void __launch_bounds__(CNT_THREADS) k_bucket_pairs(const void *__rest
     }
 }
 
-// ---------------------------------------------------------------- restricted count
-// The count pass of a restricted fit (covers given, kept pairs listed).  The
-// float pre-test passes about one pair in a hundred, so resolving a pair
-// where it is tested would run the costly steps (exact key, bucket search,
-// keep test, count, list) with one or two lanes of a warp live.  Instead
-// every warp pushes the pairs that pass onto a stack in shared memory and
-// resolves them 32 at a time, all lanes busy; the rest of the stack is
-// resolved after the last tile.  Counts, list and meta[5] / meta[6] are the
-// same as the combined pass would give (the list order may differ).
-// The restricted count runs 1024 threads per CTA: its shared arrays (bucket
-// bounds and counters) allow one CTA per SM, and its float tests are short
-// dependent chains, so the extra warps hide their latency.
-constexpr int RC_THREADS = 1024;
-#ifndef LMS_RC_TILE
-#define LMS_RC_TILE 128
-#endif
-constexpr int RC_TILE = LMS_RC_TILE;   // pair tile edge of the restricted count
-constexpr int CNT_WARPS = RC_THREADS / 32;
-constexpr int CNT_STACK = 64;   // per warp: at most 31 left + 32 pushed
+// ---------------------------------------------------------------- restricted count (band scan)
+// The pairs of a restricted pass are those whose exact slope key lies in a
+// kept bucket; the kept buckets form at most PRE_MAX covers, cover c the key
+// range [Klo_c, Khi_c).  A pair (a, b) with x_a < x_b and slope s has
+//     Z_b - Z_a = (x_b - x_a) (s 2^32 - Klo),   Z = y 2^32 - x Klo,
+// so a pair with key in [Klo, Khi) has 0 <= Z_b - Z_a < (x_b - x_a)(Khi - Klo)
+// <= X (Khi - Klo), X the span of x.  With the points sorted by Z, every such
+// pair lies within a band of D = X (Khi - Klo) of each other: scanning from
+// every point forward over the points whose Z exceeds its own by at most D
+// meets every pair of the cover exactly once (from the earlier of the two),
+// so the pass lists the kept pairs in O(n log n + band pairs) instead of
+// testing all n (n - 1) / 2.  Each pair met is resolved exactly (slope key,
+// its cover, its bucket, the keep flag); a pair counts only in the scan of
+// the cover its key lies in, so no pair is listed twice.  Covers whose keys
+// reach |K| >= 2^46 (slopes steeper than 2^14, where Z would overflow) or are
+// unbounded are scanned with an unbounded band: every pair, resolved the
+// same way.
 
-template <class G>
-__device__ __forceinline__ void resolve_pairs(const void *pts, const long long *s_bnd, int P2, unsigned *s_cnt,
-                                              const unsigned char *keep, unsigned pr, bool have, int *meta_mut,
-                                              unsigned *list)
+// Per cover, one CTA: the sorted words ((Z - Zmin) >> sh) << 16 | index,
+// sh the smallest shift that keeps the span below 2^47, into words[c n ..],
+// and the band in those units, (D >> sh) + 1 (truncation moves a difference
+// by less than one unit), or -1 for an unused cover, into band[c].
+// gscr: 2 P words per cover when n > 8192 (chunked sort), else unused.
+__global__ void __launch_bounds__(1024) k_band_sort(const int *__restrict__ xy, int n,
+                                                    const long long *__restrict__ cov,
+                                                    unsigned long long *__restrict__ words,
+                                                    long long *__restrict__ band,
+                                                    unsigned long long *__restrict__ gscr)
 {
-    bool kept = false;
-    if (have) {
-        const int b = pair_bucket<G>(pts, (int)(pr >> 16), (int)(pr & 0xffffu), s_bnd, P2);
-        if (b >= 0) {
-            if (!keep || keep[b]) {
-                atomicAdd(&s_cnt[b], 1u);
-                kept = true;
-            }
-        }
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_mn[32], s_mx[32];
+    __shared__ int s_xl[32], s_xh[32];
+    const int c = blockIdx.x;
+    const long long Klo = cov[2 * c], Khi = cov[2 * c + 1];
+    if (Klo >= Khi) {
+        if (threadIdx.x == 0) band[c] = -1;
+        return;
     }
-    if (list) {
-        const unsigned m = __ballot_sync(FULL, kept);
-        if (m) {
-            const int lane = threadIdx.x & 31;
-            unsigned at = 0;
-            if (lane == 0) at = atomicAdd(reinterpret_cast<unsigned *>(meta_mut + 6), (unsigned)__popc(m));
-            at = __shfl_sync(FULL, at, 0) + __popc(m & ((1u << lane) - 1u));
-            if (kept) list[at] = pr;
-        }
+    const long long G = 1LL << 46;
+    const bool bounded = Klo > -G && Khi < G;
+    const long long K = bounded ? Klo : 0;
+    long long mn = LLONG_MAX, mx = LLONG_MIN;
+    int xl = INT_MAX, xh = INT_MIN;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int p = xy[k];
+        const long long z = ((long long)py(p) << 32) - (long long)px(p) * K;
+        mn = min(mn, z);
+        mx = max(mx, z);
+        xl = min(xl, px(p));
+        xh = max(xh, px(p));
+    }
+    for (int s = 16; s >= 1; s >>= 1) {
+        mn = min(mn, __shfl_xor_sync(FULL, mn, s));
+        mx = max(mx, __shfl_xor_sync(FULL, mx, s));
+        xl = min(xl, __shfl_xor_sync(FULL, xl, s));
+        xh = max(xh, __shfl_xor_sync(FULL, xh, s));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_xl[warp] = xl; s_xh[warp] = xh; }
+    __syncthreads();
+    mn = s_mn[0]; mx = s_mx[0]; xl = s_xl[0]; xh = s_xh[0];
+    for (int w = 1; w < nw; ++w) {
+        mn = min(mn, s_mn[w]); mx = max(mx, s_mx[w]);
+        xl = min(xl, s_xl[w]); xh = max(xh, s_xh[w]);
+    }
+    const unsigned long long span = (unsigned long long)(mx - mn);
+    const int bits = span ? 64 - __clzll((long long)span) : 0;
+    const int sh = bits > 47 ? bits - 47 : 0;
+    int P = 1;
+    while (P < n) P <<= 1;
+    auto word = [&](int k) -> unsigned long long {
+        if (k >= n) return ~0ull;
+        const int p = xy[k];
+        const long long z = ((long long)py(p) << 32) - (long long)px(p) * K;
+        return (((unsigned long long)(z - mn) >> sh) << 16) | (unsigned long long)k;
+    };
+    unsigned long long *s = reinterpret_cast<unsigned long long *>(smem);
+    const unsigned long long *sorted = s;
+    if (P <= 8192) {
+        const int Ps = P < (int)blockDim.x ? (int)blockDim.x : P;
+        cta_fill_merge_sort_any(s, s + Ps, Ps, word);
+    } else {
+        unsigned long long *A = gscr + (size_t)c * 2 * P;
+        sorted = cta_sort_chunked<8192>(s, A, A + P, P, word);
+    }
+    for (int k = threadIdx.x; k < n; k += blockDim.x) words[(size_t)c * n + k] = sorted[k];
+    if (threadIdx.x == 0) {
+        // X (Khi - Klo) < 2^16 2^47: no overflow
+        band[c] = bounded ? (((long long)(xh - xl) * (Khi - Klo)) >> sh) + 1 : LLONG_MAX;
     }
 }
 
-template <class G>
-__global__ void __launch_bounds__(RC_THREADS) k_count_restricted(const void *__restrict__ pts, int n,
-                                                                  const long long *__restrict__ bnd,
-                                                                  unsigned *__restrict__ hist,
-                                                                  const unsigned char *__restrict__ keep,
-                                                                  const float2 *__restrict__ pre, int npre,
-                                                                  int *__restrict__ meta,
-                                                                  unsigned *__restrict__ list)
+// Restricted count by the band scan: item (c, p) is position p of cover c's
+// sorted words; its thread walks forward while the truncated Z stays within
+// the band and pushes every pair met onto its warp's stack, which is
+// resolved 32 pairs at a time with all lanes busy (the exact key, bucket
+// search, keep test, count and list are the costly part).  Counts go to this
+// CTA's row of hist, the kept pairs to list (meta[6] counts them).
+constexpr int BAND_THREADS = 1024;
+constexpr int BAND_WARPS = BAND_THREADS / 32;
+constexpr int BAND_STACK = 64;   // per warp: at most 31 left + 32 pushed
+
+__global__ void __launch_bounds__(BAND_THREADS) k_band_pairs(const int *__restrict__ xy, int n,
+                                                             const long long *__restrict__ bnd,
+                                                             unsigned *__restrict__ hist,
+                                                             const unsigned char *__restrict__ keep,
+                                                             const long long *__restrict__ cov,
+                                                             const unsigned long long *__restrict__ words,
+                                                             const long long *__restrict__ band,
+                                                             int *__restrict__ meta, unsigned *__restrict__ list)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     long long *s_bnd = reinterpret_cast<long long *>(smem);
     unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
-    __shared__ unsigned s_stack[CNT_WARPS][CNT_STACK];
-    __shared__ float2 s_cov[2 * PRE_MAX];
-    load_covers(pre, npre, s_cov);
+    __shared__ unsigned long long s_stack[BAND_WARPS][BAND_STACK];
+    __shared__ long long s_cov[2 * PRE_MAX], s_band[PRE_MAX];
+    __shared__ float s_flo[PRE_MAX], s_fhi[PRE_MAX];
+    if (threadIdx.x < 2 * PRE_MAX) s_cov[threadIdx.x] = cov[threadIdx.x];
+    if (threadIdx.x < PRE_MAX) {
+        // float slope bounds of the cover, widened by 2^-18 relative (a pair's
+        // float test below errs by about 2^-23): used only by unbounded bands
+        const int c = threadIdx.x;
+        s_band[c] = band[c];
+        const long long lo = cov[2 * c], hi = cov[2 * c + 1];
+        const double dlo = (double)lo * 0x1p-32, dhi = (double)hi * 0x1p-32;
+        s_flo[c] = lo <= -(1LL << 62) ? -INFINITY : __double2float_rd(dlo - (fabs(dlo) * 0x1p-18 + 0x1p-30));
+        s_fhi[c] = hi >= (1LL << 62) ? INFINITY : __double2float_ru(dhi + (fabs(dhi) * 0x1p-18 + 0x1p-30));
+    }
     const int P2 = meta[1], NB = meta[0] + 1;
     for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
     for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    unsigned *stk = s_stack[threadIdx.x >> 5];
+    unsigned long long *stk = s_stack[threadIdx.x >> 5];
     const unsigned below = (1u << lane) - 1u;
     int top = 0;   // warp-uniform stack height
-    unsigned nvalid = 0;
-    // tiles of RC_TILE x RC_TILE pairs: 16 per thread, so the tile decode and
-    // the row point's load are spread over more tests
-    const int T = (n + RC_TILE - 1) / RC_TILE;
-    const int ntiles = T * (T + 1) / 2;
-    const int il = threadIdx.x & (RC_TILE - 1);
-    constexpr int JPT = RC_TILE * RC_TILE / RC_THREADS;
-    const int jl0 = (threadIdx.x / RC_TILE) * JPT;
-    for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
-        int bi, bj;
-        tile_decode(q, bi, bj);
-        const int i = bi * RC_TILE + il;
-        const bool row = i < n;
-        int Pi = 0;
-        if constexpr (std::is_same<G, KeyI16>::value)
-            if (row) Pi = __ldg(static_cast<const int *>(pts) + i);
-#pragma unroll 4
-        for (int jj = 0; jj < JPT; ++jj) {
-            const int j = bj * RC_TILE + jl0 + jj;
+    // exact resolution of one stacked pair per lane
+    auto resolve = [&](unsigned long long e, bool have) {
+        bool kept = false;
+        unsigned pr = 0;
+        if (have) {
+            const int c = (int)(e >> 32);
+            pr = (unsigned)e;
+            long long key;
+            if (KeyI16::key(xy, (int)(pr >> 16), (int)(pr & 0xffffu), key) && key >= s_cov[2 * c] &&
+                key < s_cov[2 * c + 1]) {
+                const int b = bucket_of(s_bnd, P2, key);
+                if (!keep || keep[b]) {
+                    atomicAdd(&s_cnt[b], 1u);
+                    kept = true;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(FULL, kept);
+        if (m) {
+            unsigned at = 0;
+            if (lane == 0) at = atomicAdd(reinterpret_cast<unsigned *>(meta + 6), (unsigned)__popc(m));
+            at = __shfl_sync(FULL, at, 0) + __popc(m & below);
+            if (kept) list[at] = pr;
+        }
+    };
+    const long long items = (long long)PRE_MAX * n;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // whole warps take consecutive items, so the loop below stays warp-uniform
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < items; base += stride) {
+        const long long it = base + lane;
+        const int c = (int)(min(it, items - 1) / n);
+        const int p = (int)(min(it, items - 1) - (long long)c * n);
+        const long long B = s_band[c];
+        bool act = it < items && B >= 0;
+        if (!__any_sync(FULL, act)) continue;
+        const unsigned long long *w = words + (size_t)c * n;
+        const unsigned long long wp = act ? w[p] : 0ull;
+        const long long kp = (long long)(wp >> 16);
+        const unsigned ip = (unsigned)(wp & 0xffffu);
+        const bool unb = B == LLONG_MAX;   // every later point: pre-test the slope in float
+        const int Pp = xy[ip];
+        const float flo = s_flo[c], fhi = s_fhi[c];
+        int q = p + 1;
+        for (;;) {
             bool cand = false;
-            if (row && j > i && j < n) {
-                const int r = pre_test<G>(pts, Pi, i, j, s_cov);
-                nvalid += r != 0;
-                cand = r == 2;
+            unsigned long long e = 0;
+            if (act) {
+                if (q < n) {
+                    const unsigned long long wq = w[q];
+                    if ((long long)(wq >> 16) - kp <= B) {
+                        const unsigned iq = (unsigned)(wq & 0xffffu);
+                        const unsigned a = min(ip, iq), b = max(ip, iq);
+                        e = ((unsigned long long)c << 32) | (a << 16) | b;
+                        cand = true;
+                        if (unb) {
+                            const int Pq = xy[iq];
+                            int dx = px(Pq) - px(Pp), dy = py(Pq) - py(Pp);
+                            if (dx < 0) { dx = -dx; dy = -dy; }
+                            cand = dx != 0 && flo * (float)dx <= (float)dy && (float)dy <= fhi * (float)dx;
+                        }
+                        ++q;
+                    } else {
+                        act = false;
+                    }
+                } else {
+                    act = false;
+                }
             }
             const unsigned m = __ballot_sync(FULL, cand);
             if (m) {
-                if (cand) stk[top + __popc(m & below)] = ((unsigned)i << 16) | (unsigned)j;
+                if (cand) stk[top + __popc(m & below)] = e;
                 top += __popc(m);
                 if (top >= 32) {
                     __syncwarp();
                     top -= 32;
-                    const unsigned pr = stk[top + lane];
+                    const unsigned long long se = stk[top + lane];
                     __syncwarp();
-                    resolve_pairs<G>(pts, s_bnd, P2, s_cnt, keep, pr, true, meta, list);
+                    resolve(se, true);
                 }
             }
+            if (!__any_sync(FULL, act)) break;
         }
     }
     __syncwarp();
-    if (top > 0) resolve_pairs<G>(pts, s_bnd, P2, s_cnt, keep, lane < top ? stk[lane] : 0u, lane < top, meta, list);
-    for (int m = 16; m >= 1; m >>= 1) nvalid += __shfl_xor_sync(FULL, nvalid, m);
-    if (lane == 0 && nvalid) atomicAdd(reinterpret_cast<unsigned *>(meta + 5), nvalid);
+    if (top > 0) resolve(lane < top ? stk[lane] : 0ull, lane < top);
     __syncthreads();
     unsigned *my_hist = hist + (size_t)blockIdx.x * BND_MAX;
     for (int k = threadIdx.x; k < NB; k += blockDim.x) my_hist[k] = s_cnt[k];
+}
+
+// Pairs with distinct x (the candidate slopes of the whole set) into
+// meta[5]: all pairs less those within groups of equal x, counted by a
+// histogram of x in shared memory, one half of the int16 range at a time.
+__global__ void __launch_bounds__(1024) k_distinct_x_pairs(const int *__restrict__ xy, int n, int *__restrict__ meta)
+{
+    extern __shared__ unsigned s_h[];   // 32768 counters
+    unsigned long long same = 0;
+    for (int half = 0; half < 2; ++half) {
+        for (int k = threadIdx.x; k < 32768; k += blockDim.x) s_h[k] = 0u;
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int x = px(xy[k]) + 32768;
+            if ((x >> 15) == half) atomicAdd(&s_h[x & 32767], 1u);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < 32768; k += blockDim.x) {
+            const unsigned long long v = s_h[k];
+            same += v * (v - (v > 0)) / 2;
+        }
+        __syncthreads();
+    }
+    for (int s = 16; s >= 1; s >>= 1) same += __shfl_xor_sync(FULL, same, s);
+    __shared__ unsigned long long s_same[32];
+    if ((threadIdx.x & 31) == 0) s_same[threadIdx.x >> 5] = same;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_same[w];
+        meta[5] = (int)((unsigned long long)n * (unsigned long long)(n - 1) / 2 - t);
+    }
 }
 
 // The listed pairs to their buckets (the order inside a bucket is left to
@@ -2167,20 +2258,14 @@ static cudaError_t events_sample(const SweepPlan &p, const void *pts, cudaStream
 }
 
 template <class G>
-static cudaError_t events_count(const SweepPlan &p, const void *pts, const unsigned char *keep, const float2 *pre,
-                                int npre, cudaStream_t st)
+static cudaError_t events_count(const SweepPlan &p, const void *pts, cudaStream_t st)
 {
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
-    if (pre) {
-        cudaFuncSetAttribute(k_count_restricted<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-        StageTimer _t(STAGE_COUNT_PAIRS, st);
-        k_count_restricted<G><<<p.C, RC_THREADS, cnt_smem, st>>>(pts, p.n, p.bnd, p.hist, keep, pre, npre, p.meta,
-                                                                  p.ev2);
-    } else {
+    {
         cudaFuncSetAttribute(k_bucket_pairs<false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
         StageTimer _t(STAGE_COUNT_PAIRS, st);
         k_bucket_pairs<false, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, p.n, p.bnd, p.meta, p.hist, nullptr, nullptr,
-                                                                    keep, nullptr, 0);
+                                                                    nullptr);
     }
     { StageTimer _t(STAGE_PREFIX, st); k_bucket_prefix<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.hist, p.C, p.meta, p.base); }
     { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta); }
@@ -2192,7 +2277,7 @@ cudaError_t launch_events_prepare(const SweepPlan &p, const void *pts, cudaStrea
 {
     cudaError_t e = events_sample<G>(p, pts, st);
     if (e != cudaSuccess) return e;
-    return events_count<G>(p, pts, nullptr, nullptr, 0, st);
+    return events_count<G>(p, pts, st);
 }
 
 cudaError_t launch_sweep_sample(const SweepPlan &p, const short *x, const short *y, cudaStream_t st)
@@ -2201,10 +2286,45 @@ cudaError_t launch_sweep_sample(const SweepPlan &p, const short *x, const short 
     return events_sample<KeyI16>(p, p.xy, st);
 }
 
-cudaError_t launch_sweep_count(const SweepPlan &p, const unsigned char *keep, const float2 *pre, int npre,
-                               cudaStream_t st)
+size_t band_scratch_bytes(int n)
 {
-    return events_count<KeyI16>(p, p.xy, keep, pre, npre, st);
+    int P = 1;
+    while (P < n) P <<= 1;
+    size_t b = a256((size_t)PRE_MAX * n * 8) + a256((size_t)PRE_MAX * 8);
+    if (P > 8192) b += a256((size_t)PRE_MAX * 2 * P * 8);
+    return b;
+}
+
+cudaError_t launch_sweep_count(const SweepPlan &p, const unsigned char *keep, const long long *cov, void *scratch,
+                               bool distinct_x, cudaStream_t st)
+{
+    const int n = p.n;
+    int P = 1;
+    while (P < n) P <<= 1;
+    unsigned char *q = static_cast<unsigned char *>(scratch);
+    unsigned long long *words = reinterpret_cast<unsigned long long *>(q);
+    q += a256((size_t)PRE_MAX * n * 8);
+    long long *band = reinterpret_cast<long long *>(q);
+    q += a256((size_t)PRE_MAX * 8);
+    unsigned long long *gscr = P > 8192 ? reinterpret_cast<unsigned long long *>(q) : nullptr;
+    const int Ps = P > 8192 ? 8192 : (P < 1024 ? 1024 : P);
+    const size_t sort_smem = (size_t)2 * Ps * 8;
+    cudaFuncSetAttribute(k_band_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
+    { StageTimer _t(STAGE_COUNT_PAIRS, st); k_band_sort<<<PRE_MAX, 1024, sort_smem, st>>>(p.xy, n, cov, words, band, gscr); }
+    const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
+    cudaFuncSetAttribute(k_band_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
+    {
+        StageTimer _t(STAGE_COUNT_PAIRS, st);
+        k_band_pairs<<<p.C, BAND_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.hist, keep, cov, words, band, p.meta, p.ev2);
+    }
+    if (distinct_x) {
+        cudaFuncSetAttribute(k_distinct_x_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768 * 4);
+        StageTimer _t(STAGE_OTHER, st);
+        k_distinct_x_pairs<<<1, 1024, 32768 * 4, st>>>(p.xy, n, p.meta);
+    }
+    { StageTimer _t(STAGE_PREFIX, st); k_bucket_prefix<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.hist, p.C, p.meta, p.base); }
+    { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta); }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sample_counts(const SweepPlan &p, unsigned *counts, cudaStream_t st)
@@ -2216,7 +2336,7 @@ cudaError_t launch_sample_counts(const SweepPlan &p, unsigned *counts, cudaStrea
 
 template <class G>
 cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsigned char *keep, cudaStream_t st,
-                                 bool plan, const float2 *pre, int npre)
+                                 bool plan, bool listed)
 {
     const int n = p.n;
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
@@ -2225,7 +2345,7 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
     const long long *sbnd = p.bnd;
     const unsigned *sbase = p.base;
     int *smeta = p.meta;
-    if (pre) {
+    if (listed) {
         // the restricted count listed the kept pairs: place only those
         unsigned *cursor = p.hist;
         const size_t bsm = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
@@ -2251,8 +2371,7 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
         k_scatter_list<G><<<p.C, CNT_THREADS, bsm, st>>>(pts, sbnd, smeta, p.ev2, cursor, p.ev, p.meta + 6);
     } else {
         StageTimer _t(STAGE_SCATTER, st);
-        k_bucket_pairs<true, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep,
-                                                                   pre, npre);
+        k_bucket_pairs<true, G><<<p.C, CNT_THREADS, cnt_smem, st>>>(pts, n, p.bnd, p.meta, p.hist, p.base, p.ev, keep);
     }
     const size_t seg_smem = (size_t)SEG_CAP * 12;
     cudaFuncSetAttribute(k_segsort<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem);
@@ -2276,7 +2395,7 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
 
 template cudaError_t launch_events_prepare<KeyF32>(const SweepPlan &, const void *, cudaStream_t);
 template cudaError_t launch_events_finish<KeyF32>(const SweepPlan &, const void *, const unsigned char *, cudaStream_t,
-                                                  bool, const float2 *, int);
+                                                  bool, bool);
 
 cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short *y, cudaStream_t st)
 {
@@ -2285,10 +2404,10 @@ cudaError_t launch_sweep_prepare(const SweepPlan &p, const short *x, const short
 }
 
 cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, cudaStream_t st, bool plan,
-                                const float2 *pre, int npre)
+                                bool listed)
 {
     const int n = p.n;
-    cudaError_t e = launch_events_finish<KeyI16>(p, p.xy, keep, st, plan, pre, npre);
+    cudaError_t e = launch_events_finish<KeyI16>(p, p.xy, keep, st, plan, listed);
     if (e != cudaSuccess) return e;
     int P = 1;
     while (P < n) P <<= 1;
