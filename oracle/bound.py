@@ -30,3 +30,19 @@ def lower_bound(xs, ys, h, a: Fraction, b: Fraction) -> Fraction:
 def width_at(xs, ys, h, s: Fraction) -> Fraction:
     z = sorted(Fraction(y) - s * x for x, y in zip(xs, ys))
     return min(z[k + h - 1] - z[k] for k in range(len(z) - h + 1))
+
+
+def span_lower_bound(xs, h) -> int:
+    """dh: at most m points share one integer x (m the largest multiplicity),
+    so any h points take at least ceil(h / m) distinct x values and span at
+    least ceil(h / m) - 1 in x."""
+    m = max(xs.count(v) for v in set(xs))
+    return -(-h // m) - 1
+
+
+def steep_lower_bound(xs, ys, h, s_abs_min: Fraction) -> Fraction:
+    """Lower bound of w(s) for every slope with |s| >= s_abs_min: the h points
+    of any window span at least dh in x and at most the y range in y, so their
+    projections y - s x spread over at least |s| dh - (max y - min y)."""
+    v = s_abs_min * span_lower_bound(list(xs), h) - (max(ys) - min(ys))
+    return max(Fraction(0), Fraction(v))
