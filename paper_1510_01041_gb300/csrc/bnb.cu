@@ -297,14 +297,35 @@ constexpr unsigned long long BNB_MIN_RANGE = 64;   // events per swept range, at
 #endif
 constexpr double PRED_WINDOW = LMS_PRED_WINDOW;   // radians around a predicted slope angle
 
+// First index in [0, n) of the sorted array a with a[index] >= key (le =
+// false) or a[index] > key (le = true), by a 32-way search: each round every
+// lane tests one of 32 evenly spaced splits, so n = 65536 takes four rounds of
+// one load per lane instead of sixteen dependent loads.  All lanes of the
+// warp call it and get the result.
+__device__ __forceinline__ int warp_search(const long long *__restrict__ a, int n, long long key, bool le)
+{
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n;   // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) / 32;
+        const int at = lo + (lane + 1) * step - 1;
+        const bool below = at < hi && (le ? a[at] <= key : a[at] < key);
+        const int c = __popc(__ballot_sync(FULL, below));
+        lo += c * step;
+        hi = min(hi, lo + step);
+    }
+    const bool below = lo + lane < hi && (le ? a[lo + lane] <= key : a[lo + lane] < key);
+    return lo + __popc(__ballot_sync(FULL, below));
+}
+
 // Seed slopes.  With a predicted slope: half of them evenly spaced quantiles
 // of the sampled slopes whose angle lies within PRED_WINDOW of the
 // prediction (the prediction picks the region, the sample finds where pairs
 // concentrate in it), half quantiles of all samples.  Without: evenly spaced
 // quantiles of all valid samples (mode 0) or the keys of evenly spaced
-// angles in (-pi/2, pi/2) (mode 1).
-__global__ void k_pick_seeds(const long long *__restrict__ sorted, int S, const float *__restrict__ pred,
-                             int mode, int KS, long long *__restrict__ out)
+// angles in (-pi/2, pi/2) (mode 1).  meta[10]: the valid samples.
+__global__ void k_pick_seeds(const long long *__restrict__ sorted, const int *__restrict__ meta,
+                             const float *__restrict__ pred, int mode, int KS, long long *__restrict__ out)
 {
     if (!pred && mode == 1) {
         for (int q = threadIdx.x; q < KS; q += blockDim.x) {
@@ -318,13 +339,11 @@ __global__ void k_pick_seeds(const long long *__restrict__ sorted, int S, const 
         }
         return;
     }
-    __shared__ int s_m, s_lo, s_hi;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = S;
-        while (lo < hi) { int m = (lo + hi) >> 1; if (sorted[m] < I64_MAX) lo = m + 1; else hi = m; }
-        s_m = lo;
-        int a = 0, b = s_m;
-        if (pred && s_m > 0) {
+    __shared__ int s_lo, s_hi;
+    const int m = meta[10];
+    if (threadIdx.x < 32) {
+        int a = 0, b = m;
+        if (pred && m > 0) {
             // the window of slope angles within PRED_WINDOW radians of the prediction
             const double sp = (double)*pred;
             const double ang = (sp == sp) ? atan(sp) : 0.0;
@@ -335,24 +354,17 @@ __global__ void k_pick_seeds(const long long *__restrict__ sorted, int S, const 
                 return (long long)(v * 4294967296.0);
             };
             const double half_pi = 1.5707963267948966;
-            const long long klo = key_of(fmax(ang - PRED_WINDOW, -half_pi + 1e-6));
-            const long long khi = key_of(fmin(ang + PRED_WINDOW, half_pi - 1e-6));
-            int x0 = 0, x1 = s_m;
-            while (x0 < x1) { int m = (x0 + x1) >> 1; if (sorted[m] < klo) x0 = m + 1; else x1 = m; }
-            a = x0;
-            x1 = s_m;
-            while (x0 < x1) { int m = (x0 + x1) >> 1; if (sorted[m] <= khi) x0 = m + 1; else x1 = m; }
-            b = x0;
+            a = warp_search(sorted, m, key_of(fmax(ang - PRED_WINDOW, -half_pi + 1e-6)), false);
+            b = warp_search(sorted, m, key_of(fmin(ang + PRED_WINDOW, half_pi - 1e-6)), true);
             if (b <= a) {                      // no sample in the window: the nearest ones
-                a = max(0, min(a, s_m - 1));
+                a = max(0, min(a, m - 1));
                 b = a + 1;
             }
         }
-        s_lo = a;
-        s_hi = b;
+        if (threadIdx.x == 0) { s_lo = a; s_hi = b; }
     }
     __syncthreads();
-    const int m = s_m, a = s_lo, b = s_hi;
+    const int a = s_lo, b = s_hi;
     // with a prediction the first half of the seeds samples the window and
     // the second half all samples, so a wrong prediction costs nothing
     const int KW = pred ? KS / 2 : KS;
@@ -368,47 +380,62 @@ __global__ void k_pick_seeds(const long long *__restrict__ sorted, int S, const 
     }
 }
 
-// Zoom round of the upper bound: around the best seed of the previous round
-// (smallest width, ties to the smaller index), KS sample ranks evenly
-// spaced over [r* - span, r* + span], r* the rank of that seed's key in the
+// Zoom round of the upper bound: KS sample ranks evenly spaced over
+// [r* - span, r* + span] around the best seed of the previous round
+// (smallest width, ties to the smaller index), r* the rank of its key in the
 // sorted sample and span the previous round's spacing of sample ranks
-// (round 2: m / KS, m the valid samples; round 3: 2 span_2 / KS).  The
-// upper bound only needs some real slope with a narrow window; narrowing the
+// (round 2: m / KS, m the valid samples; round 3: 2 span_2 / KS).  The upper
+// bound only needs some real slope with a narrow window; narrowing the
 // search where the previous round found the narrowest windows brings it
 // close to the optimum, and the tighter the bound the fewer slope intervals
 // survive.  A round whose previous round found nothing repeats its keys.
-__global__ void k_zoom_seeds(const long long *__restrict__ sorted, int S, const long long *__restrict__ prev_keys,
-                             const long long *__restrict__ prev_w, int KS, int round, long long *__restrict__ out)
+__global__ void __launch_bounds__(256) k_zoom_seeds(const long long *__restrict__ sorted,
+                                                    const int *__restrict__ meta,
+                                                    const long long *__restrict__ prev_keys,
+                                                    const long long *__restrict__ prev_w, int KS, int round,
+                                                    long long *__restrict__ out)
 {
-    __shared__ int s_lo, s_hi, s_ok;
+    __shared__ long long s_w[8];
+    __shared__ int s_q[8], s_q1, s_r1;
+    const int m = meta[10];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = threadIdx.x;
+    // the best seed: (width, index) minimum over the block
+    long long v = q < KS ? prev_w[q] : I64_MAX;
+    int idx = v < I64_MAX ? q : -1;
+    for (int d = 16; d >= 1; d >>= 1) {
+        const long long ov = __shfl_xor_sync(FULL, v, d);
+        const int oi = __shfl_xor_sync(FULL, idx, d);
+        if (oi >= 0 && (idx < 0 || ov < v || (ov == v && oi < idx))) { v = ov; idx = oi; }
+    }
+    if (lane == 0) { s_w[warp] = v; s_q[warp] = idx; }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        int m0 = 0, m1 = S;
-        while (m0 < m1) { const int md = (m0 + m1) >> 1; if (sorted[md] < I64_MAX) m0 = md + 1; else m1 = md; }
-        const int m = m0;
-        int q = -1;
-        long long bw = I64_MAX;
-        for (int k = 0; k < KS; ++k)
-            if (prev_w[k] < bw) { bw = prev_w[k]; q = k; }
-        s_ok = (q >= 0 && m > 0) ? 1 : 0;
-        if (s_ok) {
-            const long long key = prev_keys[q];
-            int a = 0, b = m;
-            while (a < b) { const int md = (a + b) >> 1; if (sorted[md] < key) a = md + 1; else b = md; }
-            const int r = min(a, m - 1);
-            int span = max(1, m / KS);
-            for (int k = 2; k < round; ++k) span = max(1, (2 * span + 1) / KS);
-            s_lo = max(0, r - span);
-            s_hi = min(m, r + span + 1);
-        }
+        long long bv = I64_MAX;
+        int bi = -1;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
+            if (s_q[k] >= 0 && (bi < 0 || s_w[k] < bv || (s_w[k] == bv && s_q[k] < bi))) { bv = s_w[k]; bi = s_q[k]; }
+        s_q1 = bi;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < KS; q += blockDim.x) {
-        if (!s_ok) {
-            out[q] = prev_keys[q];
-            continue;
-        }
-        const long long len = s_hi - s_lo;
-        out[q] = sorted[s_lo + (int)(((2LL * q + 1) * len) / (2LL * KS))];
+    const int q1 = s_q1;
+    if (q1 < 0 || m == 0) {
+        if (q < KS) out[q] = prev_keys[q];
+        return;
+    }
+    // its rank in the sample
+    if (warp == 0) {
+        const int r = warp_search(sorted, m, prev_keys[q1], false);
+        if (lane == 0) s_r1 = min(r, m - 1);
+    }
+    __syncthreads();
+    int span = max(1, m / KS);
+    for (int k = 2; k < round; ++k) span = max(1, (2 * span + 1) / KS);
+    const int r1 = s_r1;
+    if (q < KS) {
+        const int lo = max(0, r1 - span), hi = min(m, r1 + span + 1);
+        const long long len = hi - lo;
+        out[q] = sorted[lo + (int)(((2LL * q + 1) * len) / (2LL * KS))];
     }
 }
 
@@ -929,7 +956,10 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_covers(const int *__restr
     };
     // separators: the PRE_MAX - 1 widest gaps (gap r lies between runs r - 1 and r)
     const int nsep = min(R - 1, PRE_MAX - 1);
-    for (int t = 0; t < nsep; ++t) {
+    // with at most PRE_MAX runs every run is a cover of its own
+    if (R <= PRE_MAX)
+        for (int t = threadIdx.x; t < nsep; t += blockDim.x) s_sep[t] = t + 1;
+    for (int t = 0; t < (R <= PRE_MAX ? 0 : nsep); ++t) {
         double bv = -1.0;
         int bi = 0x7fffffff;
         for (int r = 1 + threadIdx.x; r < R; r += blockDim.x) {
@@ -956,6 +986,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_covers(const int *__restr
         }
         __syncthreads();
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         // separators in increasing order
         int sep[PRE_MAX];
@@ -1003,28 +1034,34 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_ranges(const int *__restr
                                                               TreeState *__restrict__ ts)
 {
     __shared__ long long s_warp[32];
-    __shared__ unsigned long long s_target;
+    __shared__ long long s_cnt;
     const int NB = meta[0] + 1;
     const unsigned total = base[NB];
     const int nr = ts->nruns;
-    if (threadIdx.x == 0) {
-        unsigned long long t = max((unsigned long long)BNB_MIN_RANGE,
-                                   (unsigned long long)sqrt(0.8 * (double)total));
-        t = max(t, ((unsigned long long)total + G - 1) / G);
-        for (;;) {
-            unsigned long long cnt = 0;
-            for (int r = 0; r < nr; ++r) {
-                const unsigned len = base[runs[2 * r + 1]] - base[runs[2 * r]];
-                cnt += (len + t - 1) / t;
-            }
-            if (cnt <= (unsigned long long)W) break;
-            t *= 2;
-        }
-        s_target = t;
-        ts->swept = total;
+    // run lengths, RPT per thread (strided), then the smallest target of the
+    // form t0 2^k whose pieces number at most W
+    constexpr int RPT = (BND_MAX + 1) / TREE_THREADS + 1;
+    unsigned len[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int r = threadIdx.x + i * TREE_THREADS;
+        len[i] = r < nr ? base[runs[2 * r + 1]] - base[runs[2 * r]] : 0u;
     }
-    __syncthreads();
-    const unsigned long long t = s_target;
+    unsigned long long t = max((unsigned long long)BNB_MIN_RANGE, (unsigned long long)sqrt(0.8 * (double)total));
+    t = max(t, ((unsigned long long)total + G - 1) / G);
+    for (;;) {
+        long long c = 0;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) c += (long long)((len[i] + t - 1) / t);
+        c = block_scan<false>(c, s_warp);
+        if (threadIdx.x == blockDim.x - 1) s_cnt = c;
+        __syncthreads();
+        const long long cnt = s_cnt;
+        __syncthreads();
+        if (cnt <= (long long)W) break;
+        t *= 2;
+    }
+    if (threadIdx.x == 0) ts->swept = total;
     // pieces per run, exclusive offsets (runs in chunks per thread)
     const int per = (nr + blockDim.x - 1) / blockDim.x;
     const int r0 = threadIdx.x * per, r1 = min(nr, r0 + per);
@@ -1126,7 +1163,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     if (pred_ready && cudaStreamWaitEvent(st, pred_ready, 0) != cudaSuccess) return LMS_ERR_CUDA;
     {
         StageTimer _t(STAGE_SEEDS, st);
-        k_pick_seeds<<<1, 128, 0, st>>>(sorted_sample(p), p.S, pred_dev, seed_mode, KS, seed_keys);
+        k_pick_seeds<<<1, 128, 0, st>>>(sorted_sample(p), p.meta, pred_dev, seed_mode, KS, seed_keys);
     }
     const int Ps = P < 1024 ? 1024 : P;   // the shared-memory sorts fill whole 1024-thread CTAs
     // 32-bit keys: one sorted array plus merge scratch; two sorted arrays plus scratch
@@ -1143,7 +1180,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         long long *keys_r = seed_keys + (size_t)(r - 1) * KS, *w_r = seed_w + (size_t)(r - 1) * KS;
         {
             StageTimer _t(STAGE_SEEDS, st);
-            k_zoom_seeds<<<1, 256, 0, st>>>(sorted_sample(p), p.S, keys_r - KS, w_r - KS, KS, r, keys_r);
+            k_zoom_seeds<<<1, 256, 0, st>>>(sorted_sample(p), p.meta, keys_r - KS, w_r - KS, KS, r, keys_r);
         }
         {
             StageTimer _t(STAGE_SEEDS, st);

@@ -109,7 +109,9 @@ struct SweepPlan {
     long long *skeys2;         // [S] merge ping-pong
     long long *bnd;            // [BND_MAX] bucket boundaries, padded with INT64_MAX
     int *meta;                 // [16] 0 nbnd, 1 P2, 2 oversize count, 3 error flags, 4 range counter,
-                               //      5 pairs with distinct x, 6 listed kept pairs (restricted count)
+                               //      5 pairs with distinct x, 6 listed kept pairs (restricted count),
+                               //      7 / 8 events covered by the ranges / events there are,
+                               //      10 valid sampled keys
     unsigned *hist;            // [C][BND_MAX] per-CTA bucket counts, then offsets
     unsigned *base;            // [BND_MAX + 1] bucket starts; base[NB] = E
     int *oversize;             // [BND_MAX] buckets too large for the shared-memory sort
@@ -154,7 +156,7 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
 // A restricted pass (the branch-and-bound's) lists the pairs whose exact
 // slope key lies in a kept bucket; the kept buckets form at most PRE_MAX
 // covers, given as key ranges [cov[2c], cov[2c + 1]) (unused covers empty).
-constexpr int PRE_MAX = 8;
+constexpr int PRE_MAX = 32;
 // the sample half of the prepare step (pack, sample, sort, splitters), and
 // the restricted count (the kept pairs listed into ev2 and counted per
 // bucket, then prefix and scan)

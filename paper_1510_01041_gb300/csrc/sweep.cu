@@ -196,23 +196,36 @@ __global__ void __launch_bounds__(1024) k_splitters(const long long *__restrict_
                                                     long long *__restrict__ bnd, int *__restrict__ meta,
                                                     const int *__restrict__ bcount = nullptr, int bper = 1)
 {
+    extern __shared__ long long s_q[];   // the B - 1 quantiles (at most BND_MAX / 2)
     __shared__ int s_m;
     __shared__ int s_scan[1024];
     if (bcount) {
         const long long want = ((long long)max(*bcount, 0) + bper - 1) / bper;
         B = (int)min((long long)B, max(want, 1LL));
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // first KEY_INF (invalid samples sort last), by a 32-way search
+        const int lane = threadIdx.x;
         int lo = 0, hi = S;
-        while (lo < hi) { int m = (lo + hi) >> 1; if (sorted[m] < KEY_INF) lo = m + 1; else hi = m; }
-        s_m = lo;
+        while (hi - lo > 32) {
+            const int step = (hi - lo + 31) / 32;
+            const int at = lo + (lane + 1) * step - 1;
+            const int c = __popc(__ballot_sync(FULL, at < hi && sorted[at] < KEY_INF));
+            lo += c * step;
+            hi = min(hi, lo + step);
+        }
+        const int c = __popc(__ballot_sync(FULL, lo + lane < hi && sorted[lo + lane] < KEY_INF));
+        if (lane == 0) s_m = lo + c;
     }
     __syncthreads();
     const int m = s_m;
     const int nq = (m > 0) ? B - 1 : 0;          // quantiles b = 1 .. B-1
+    // the quantiles, read once with consecutive threads on consecutive b
+    for (int b = 1 + threadIdx.x; b <= nq; b += blockDim.x) s_q[b - 1] = sorted[(long long)b * m / B];
+    __syncthreads();
     const int per = (nq + blockDim.x - 1) / blockDim.x;
     const int b0 = 1 + threadIdx.x * per;
-    auto q = [&](int b) { return sorted[(long long)b * m / B]; };
+    auto q = [&](int b) { return s_q[b - 1]; };
     int cnt = 0;
     for (int b = b0; b < b0 + per && b <= nq; ++b) {
         const long long v = q(b);
@@ -247,6 +260,7 @@ __global__ void __launch_bounds__(1024) k_splitters(const long long *__restrict_
     if (threadIdx.x == 0) {
         meta[0] = nbnd; meta[1] = P2; meta[2] = 0; meta[3] = 0; meta[5] = 0; meta[6] = 0;
         meta[7] = 0;   // events covered by the sweep's ranges (start sorts and k_sweep add to it)
+        meta[10] = m;  // valid sampled keys
     }
 }
 
@@ -2253,7 +2267,12 @@ static cudaError_t events_sample(const SweepPlan &p, const void *pts, cudaStream
     const int n = p.n;
     { StageTimer _t(STAGE_SAMPLE, st); k_sample<G><<<(p.S + 255) / 256, 256, 0, st>>>(pts, n, p.emax, p.S, p.skeys); }
     const long long *src = sort_sample(p.skeys, p.skeys2, p.S, st);
-    { StageTimer _t(STAGE_SPLITTERS, st); k_splitters<<<1, 1024, 0, st>>>(src, p.S, p.B, p.bnd, p.meta); }
+    {
+        const size_t qs = (size_t)BND_MAX / 2 * 8;
+        cudaFuncSetAttribute(k_splitters, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qs);
+        StageTimer _t(STAGE_SPLITTERS, st);
+        k_splitters<<<1, 1024, qs, st>>>(src, p.S, p.B, p.bnd, p.meta);
+    }
     return cudaGetLastError();
 }
 
@@ -2355,7 +2374,9 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
             const long long *src = sort_sample(p.skeys, p.skeys2, S2, st);
             {
                 StageTimer _t(STAGE_SPLITTERS, st);
-                k_splitters<<<1, 1024, 0, st>>>(src, S2, BND_MAX / 2, p.bnd2, p.meta2, p.meta + 6, RESPLIT_PER);
+                const size_t qs = (size_t)BND_MAX / 2 * 8;
+                cudaFuncSetAttribute(k_splitters, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qs);
+                k_splitters<<<1, 1024, qs, st>>>(src, S2, BND_MAX / 2, p.bnd2, p.meta2, p.meta + 6, RESPLIT_PER);
             }
             if (cudaMemsetAsync(p.base2, 0, (size_t)(BND_MAX + 1) * 4, st) != cudaSuccess) return cudaGetLastError();
             cudaFuncSetAttribute(k_list_hist<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);

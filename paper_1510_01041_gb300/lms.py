@@ -246,9 +246,10 @@ class BnbStats(ctypes.Structure):
 
 
 def fit_bnb(x, y, h: int = 0, seed=None, out=None, stream=None, sweepers: int = 0, buckets: int = 0,
-            seed_mode: str = "quantiles"):
+            seed_mode: str = "quantiles", stats: bool = True):
     """Exact LMS by branch-and-bound (lms_fit_bnb).  ``seed``: a CUDA float32
-    tensor holding a predicted slope, or None.  Returns (out, stats dict)."""
+    tensor holding a predicted slope, or None.  Returns (out, stats dict); with
+    stats=False the call does not wait for the fit and the dict is None."""
     import torch
     L = lib()
     if not getattr(L, "_bnb_ready", False):
@@ -267,11 +268,11 @@ def fit_bnb(x, y, h: int = 0, seed=None, out=None, stream=None, sweepers: int = 
     sp = ctypes.c_void_p(seed.data_ptr()) if seed is not None else ctypes.c_void_p(0)
     opt = options("bnb", sweepers, buckets, seed_mode)
     rc = L.lms_fit_bnb(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(), int(h), sp,
-                       ctypes.byref(opt), ctypes.c_void_p(out.data_ptr()), ctypes.byref(st),
+                       ctypes.byref(opt), ctypes.c_void_p(out.data_ptr()), ctypes.byref(st) if stats else None,
                        _stream_handle(stream))
     if rc != LMS_OK:
         raise LmsError(rc, "lms_fit_bnb")
-    return out, {f: getattr(st, f) for f, _ in BnbStats._fields_}
+    return out, ({f: getattr(st, f) for f, _ in BnbStats._fields_} if stats else None)
 
 
 # ------------------------------------------------------------------ learned slope proposal
@@ -390,8 +391,10 @@ class SetNet:
             raise LmsError(rc, "lms_setnet_load")
         return self
 
-    def fit(self, x, y, h: int = 0, out=None, stream=None):
-        """lms_fit_learned: predict the slope, then exact branch-and-bound."""
+    def fit(self, x, y, h: int = 0, out=None, stream=None, stats: bool = True):
+        """lms_fit_learned: predict the slope, then exact branch-and-bound.
+        Returns (out, stats dict); with stats=False the call does not wait for
+        the fit and the dict is None."""
         import torch
         if out is None:
             out = torch.empty(RESULT_DTYPE.itemsize, dtype=torch.uint8, device=x.device)
@@ -399,15 +402,16 @@ class SetNet:
         opt = options("bnb")
         rc = self.L.lms_fit_learned(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                     x.numel(), int(h), ctypes.byref(opt), ctypes.c_void_p(out.data_ptr()),
-                                    ctypes.byref(st), _stream_handle(stream))
+                                    ctypes.byref(st) if stats else None, _stream_handle(stream))
         if rc != LMS_OK:
             raise LmsError(rc, "lms_fit_learned")
-        return out, {f: getattr(st, f) for f, _ in BnbStats._fields_}
+        return out, ({f: getattr(st, f) for f, _ in BnbStats._fields_} if stats else None)
 
-    def fit_host(self, x, y, h: int = 0, out=None, stream=None):
+    def fit_host(self, x, y, h: int = 0, out=None, stream=None, stats: bool = True):
         """lms_fit_learned_host on host int16 arrays (numpy or CPU tensors;
         pinned tensors copy asynchronously).  ``out``: optional host uint8
-        buffer of 88 bytes that receives the lms_result.  Returns (out, stats)."""
+        buffer of 88 bytes that receives the lms_result.  Returns (out, stats)
+        (stats None with stats=False)."""
         def ptr(a):
             return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
         n = x.numel() if hasattr(x, "numel") else x.size
@@ -416,11 +420,11 @@ class SetNet:
         st = BnbStats()
         opt = options("bnb")
         rc = self.L.lms_fit_learned_host(self.h, ctypes.c_void_p(ptr(x)), ctypes.c_void_p(ptr(y)), int(n), int(h),
-                                         ctypes.byref(opt), ctypes.c_void_p(ptr(out)), ctypes.byref(st),
-                                         _stream_handle(stream))
+                                         ctypes.byref(opt), ctypes.c_void_p(ptr(out)),
+                                         ctypes.byref(st) if stats else None, _stream_handle(stream))
         if rc != LMS_OK:
             raise LmsError(rc, "lms_fit_learned_host")
-        return out, {f: getattr(st, f) for f, _ in BnbStats._fields_}
+        return out, ({f: getattr(st, f) for f, _ in BnbStats._fields_} if stats else None)
 
 
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "setnet.bin")
