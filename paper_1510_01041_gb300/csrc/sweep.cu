@@ -406,11 +406,14 @@ __global__ void __launch_bounds__(1024) k_band_sort(const int *__restrict__ xy, 
 }
 
 // Restricted count by the band scan: item (c, p) is position p of cover c's
-// sorted words; its thread walks forward while the truncated Z stays within
-// the band and pushes every pair met onto its warp's stack, which is
-// resolved 32 pairs at a time with all lanes busy (the exact key, bucket
-// search, keep test, count and list are the costly part).  Counts go to this
-// CTA's row of hist, the kept pairs to list (meta[6] counts them).
+// sorted words; its lane finds where its band ends (a binary search on the
+// truncated Z), the warp flattens its 32 bands into one list of pairs and
+// walks it 32 pairs at a time (a long band, the dense points near the line,
+// no longer holds the warp with one lane busy), pushing every pair onto the
+// warp's stack, which is resolved 32 pairs at a time with all lanes busy
+// (the exact key, bucket search, keep test, count and list are the costly
+// part).  Counts go to this CTA's row of hist, the kept pairs to list
+// (meta[6] counts them).
 constexpr int BAND_THREADS = 1024;
 constexpr int BAND_WARPS = BAND_THREADS / 32;
 constexpr int BAND_STACK = 64;   // per warp: at most 31 left + 32 pushed
@@ -487,34 +490,55 @@ __global__ void __launch_bounds__(BAND_THREADS) k_band_pairs(const int *__restri
         const unsigned long long *w = words + (size_t)c * n;
         const unsigned long long wp = act ? w[p] : 0ull;
         const long long kp = (long long)(wp >> 16);
-        const unsigned ip = (unsigned)(wp & 0xffffu);
-        const bool unb = B == LLONG_MAX;   // every later point: pre-test the slope in float
-        const int Pp = xy[ip];
-        const float flo = s_flo[c], fhi = s_fhi[c];
-        int q = p + 1;
-        for (;;) {
+        // the band's end: the first later position whose key exceeds kp + B
+        int end = p + 1;
+        if (act) {
+            int lo = p + 1, hi = n;
+            if (B != LLONG_MAX) {
+                while (lo < hi) {
+                    const int md = (lo + hi) >> 1;
+                    if ((long long)(w[md] >> 16) - kp <= B) lo = md + 1; else hi = md;
+                }
+            } else {
+                lo = n;
+            }
+            end = lo;
+        }
+        // the warp's bands flattened into one list of pairs, 32 at a time:
+        // pair t belongs to the lane whose prefix range holds t
+        const int L = act ? end - p - 1 : 0;
+        int incl = L;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int v = __shfl_sync(FULL, incl, j + step - 1);
+                if (v <= t) j += step;
+            }
+            j = min(j, 31);
+            const int pj = __shfl_sync(FULL, p, j), cj = __shfl_sync(FULL, c, j);
+            const int exj = __shfl_sync(FULL, incl - L, j);
+            const unsigned ipj = (unsigned)(__shfl_sync(FULL, wp, j) & 0xffffu);
             bool cand = false;
             unsigned long long e = 0;
-            if (act) {
-                if (q < n) {
-                    const unsigned long long wq = w[q];
-                    if ((long long)(wq >> 16) - kp <= B) {
-                        const unsigned iq = (unsigned)(wq & 0xffffu);
-                        const unsigned a = min(ip, iq), b = max(ip, iq);
-                        e = ((unsigned long long)c << 32) | (a << 16) | b;
-                        cand = true;
-                        if (unb) {
-                            const int Pq = xy[iq];
-                            int dx = px(Pq) - px(Pp), dy = py(Pq) - py(Pp);
-                            if (dx < 0) { dx = -dx; dy = -dy; }
-                            cand = dx != 0 && flo * (float)dx <= (float)dy && (float)dy <= fhi * (float)dx;
-                        }
-                        ++q;
-                    } else {
-                        act = false;
-                    }
-                } else {
-                    act = false;
+            if (t < total) {
+                const unsigned long long wq = words[(size_t)cj * n + pj + 1 + (t - exj)];
+                const unsigned iq = (unsigned)(wq & 0xffffu);
+                const unsigned a = min(ipj, iq), b = max(ipj, iq);
+                e = ((unsigned long long)cj << 32) | (a << 16) | b;
+                cand = true;
+                if (s_band[cj] == LLONG_MAX) {
+                    // unbounded band: every later point, pre-tested in float
+                    const int Pp = xy[ipj], Pq = xy[iq];
+                    int dx = px(Pq) - px(Pp), dy = py(Pq) - py(Pp);
+                    if (dx < 0) { dx = -dx; dy = -dy; }
+                    cand = dx != 0 && s_flo[cj] * (float)dx <= (float)dy && (float)dy <= s_fhi[cj] * (float)dx;
                 }
             }
             const unsigned m = __ballot_sync(FULL, cand);
@@ -529,11 +553,121 @@ __global__ void __launch_bounds__(BAND_THREADS) k_band_pairs(const int *__restri
                     resolve(se, true);
                 }
             }
-            if (!__any_sync(FULL, act)) break;
         }
     }
     __syncwarp();
     if (top > 0) resolve(lane < top ? stk[lane] : 0ull, lane < top);
+    __syncthreads();
+    unsigned *my_hist = hist + (size_t)blockIdx.x * BND_MAX;
+    for (int k = threadIdx.x; k < NB; k += blockDim.x) my_hist[k] = s_cnt[k];
+}
+
+// Restricted count over all pairs, for small sets (n <= TILE_COUNT_MAX_N),
+// where one sort of the points per cover costs more than testing every
+// pair: upper-triangle tiles of RC_TILE x RC_TILE pairs, each pair's slope
+// tested in float against the covers (widened by 2^-18 relative; with
+// dx > 0 the test lo dx <= dy <= hi dx needs no division, dx and dy exact,
+// one rounding of 2^-24 per product), the survivors (about one pair in a
+// hundred) pushed onto the warp's stack and resolved 32 at a time exactly
+// (key, bucket, keep) like the band scan's.
+constexpr int TILE_COUNT_MAX_N = 8192;
+constexpr int RC_TILE = 128;   // pair tile edge
+
+__global__ void __launch_bounds__(BAND_THREADS) k_tile_pairs(const int *__restrict__ xy, int n,
+                                                             const long long *__restrict__ bnd,
+                                                             unsigned *__restrict__ hist,
+                                                             const unsigned char *__restrict__ keep,
+                                                             const long long *__restrict__ cov,
+                                                             int *__restrict__ meta, unsigned *__restrict__ list)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long *s_bnd = reinterpret_cast<long long *>(smem);
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(smem + BND_MAX * sizeof(long long));
+    __shared__ unsigned s_stack[BAND_WARPS][BAND_STACK];
+    __shared__ float2 s_fc[2 * PRE_MAX];   // sorted float covers, then +inf (the search never reads past)
+    if (threadIdx.x < 2 * PRE_MAX) {
+        const int c = threadIdx.x;
+        float2 f = make_float2(INFINITY, INFINITY);
+        if (c < PRE_MAX && cov[2 * c] < cov[2 * c + 1]) {
+            const long long lo = cov[2 * c], hi = cov[2 * c + 1];
+            const double dlo = (double)lo * 0x1p-32, dhi = (double)hi * 0x1p-32;
+            f.x = lo <= -(1LL << 62) ? -INFINITY : __double2float_rd(dlo - (fabs(dlo) * 0x1p-18 + 0x1p-30));
+            f.y = hi >= (1LL << 62) ? INFINITY : __double2float_ru(dhi + (fabs(dhi) * 0x1p-18 + 0x1p-30));
+        }
+        s_fc[c] = f;
+    }
+    const int P2 = meta[1], NB = meta[0] + 1;
+    for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
+    for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    unsigned *stk = s_stack[threadIdx.x >> 5];
+    const unsigned below = (1u << lane) - 1u;
+    int top = 0;   // warp-uniform stack height
+    auto resolve = [&](unsigned pr, bool have) {
+        bool kept = false;
+        if (have) {
+            long long key;
+            if (KeyI16::key(xy, (int)(pr >> 16), (int)(pr & 0xffffu), key)) {
+                const int b = bucket_of(s_bnd, P2, key);
+                if (!keep || keep[b]) {
+                    atomicAdd(&s_cnt[b], 1u);
+                    kept = true;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(FULL, kept);
+        if (m) {
+            unsigned at = 0;
+            if (lane == 0) at = atomicAdd(reinterpret_cast<unsigned *>(meta + 6), (unsigned)__popc(m));
+            at = __shfl_sync(FULL, at, 0) + __popc(m & below);
+            if (kept) list[at] = pr;
+        }
+    };
+    const int T = (n + RC_TILE - 1) / RC_TILE;
+    const int ntiles = T * (T + 1) / 2;
+    const int il = threadIdx.x & (RC_TILE - 1);
+    constexpr int JPT = RC_TILE * RC_TILE / BAND_THREADS;
+    const int jl0 = (threadIdx.x / RC_TILE) * JPT;
+    for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
+        int bi, bj;
+        tile_decode(q, bi, bj);
+        const int i = bi * RC_TILE + il;
+        const bool row = i < n;
+        const int Pi = row ? __ldg(xy + i) : 0;
+#pragma unroll 4
+        for (int jj = 0; jj < JPT; ++jj) {
+            const int j = bj * RC_TILE + jl0 + jj;
+            bool cand = false;
+            if (row && j > i && j < n) {
+                const int Pj = __ldg(xy + j);
+                int dx = px(Pj) - px(Pi), dy = py(Pj) - py(Pi);
+                if (dx != 0) {
+                    if (dx < 0) { dx = -dx; dy = -dy; }
+                    const float fx = (float)dx, fy = (float)dy;
+                    int c = 0;
+#pragma unroll
+                    for (int step = PRE_MAX; step >= 1; step >>= 1)
+                        if (s_fc[c + step - 1].x * fx <= fy) c += step;
+                    cand = c > 0 && fy <= s_fc[c - 1].y * fx;
+                }
+            }
+            const unsigned m = __ballot_sync(FULL, cand);
+            if (m) {
+                if (cand) stk[top + __popc(m & below)] = ((unsigned)i << 16) | (unsigned)j;
+                top += __popc(m);
+                if (top >= 32) {
+                    __syncwarp();
+                    top -= 32;
+                    const unsigned pr = stk[top + lane];
+                    __syncwarp();
+                    resolve(pr, true);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (top > 0) resolve(lane < top ? stk[lane] : 0u, lane < top);
     __syncthreads();
     unsigned *my_hist = hist + (size_t)blockIdx.x * BND_MAX;
     for (int k = threadIdx.x; k < NB; k += blockDim.x) my_hist[k] = s_cnt[k];
@@ -2326,13 +2460,17 @@ cudaError_t launch_sweep_count(const SweepPlan &p, const unsigned char *keep, co
     long long *band = reinterpret_cast<long long *>(q);
     q += a256((size_t)PRE_MAX * 8);
     unsigned long long *gscr = P > 8192 ? reinterpret_cast<unsigned long long *>(q) : nullptr;
-    const int Ps = P > 8192 ? 8192 : (P < 1024 ? 1024 : P);
-    const size_t sort_smem = (size_t)2 * Ps * 8;
-    cudaFuncSetAttribute(k_band_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
-    { StageTimer _t(STAGE_COUNT_PAIRS, st); k_band_sort<<<PRE_MAX, 1024, sort_smem, st>>>(p.xy, n, cov, words, band, gscr); }
     const size_t cnt_smem = (size_t)BND_MAX * 8 + (size_t)BND_MAX * 4;
-    cudaFuncSetAttribute(k_band_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
-    {
+    if (n <= TILE_COUNT_MAX_N) {
+        cudaFuncSetAttribute(k_tile_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
+        StageTimer _t(STAGE_COUNT_PAIRS, st);
+        k_tile_pairs<<<p.C, BAND_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.hist, keep, cov, p.meta, p.ev2);
+    } else {
+        const int Ps = P > 8192 ? 8192 : (P < 1024 ? 1024 : P);
+        const size_t sort_smem = (size_t)2 * Ps * 8;
+        cudaFuncSetAttribute(k_band_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
+        { StageTimer _t(STAGE_COUNT_PAIRS, st); k_band_sort<<<PRE_MAX, 1024, sort_smem, st>>>(p.xy, n, cov, words, band, gscr); }
+        cudaFuncSetAttribute(k_band_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cnt_smem);
         StageTimer _t(STAGE_COUNT_PAIRS, st);
         k_band_pairs<<<p.C, BAND_THREADS, cnt_smem, st>>>(p.xy, n, p.bnd, p.hist, keep, cov, words, band, p.meta, p.ev2);
     }
