@@ -1415,8 +1415,10 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
     }
     int P = 1;
     while (P < n) P <<= 1;
+    // global sort space above SORT_SMEM_N points: 2 P words per range (the
+    // chunked sort's two buffers), then W P 16-bit payloads
     unsigned long long *a = (n <= SORT_SMEM_N) ? reinterpret_cast<unsigned long long *>(smem)
-                                               : gsort + (size_t)w * P;
+                                               : gsort + (size_t)w * 2 * P;
     // the slope of the first event (the vertical fallback uses slope 0)
     if (threadIdx.x == 0) {
         int dy = 0, dx = 1;
@@ -1440,9 +1442,43 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
     // above 32768 points the index needs 16 bits: the word then holds
     // (key + 2^32, 2^15 - 1 - x) and the index travels in a payload array (equal
     // words are identical points, whose order is immaterial)
-    const bool wide = n > 32768;
-    unsigned short *pay = wide ? reinterpret_cast<unsigned short *>(gsort + (size_t)W * P) + (size_t)w * P : nullptr;
-    if (wide) {
+    // Above SORT_SMEM_N points, when the projections at the slope span less
+    // than 2^32: words (Z - Zmin) << 32 | (32767 - x) << 16 | index, sorted
+    // in 8192-word chunks in shared memory and merged in global memory.
+    long long zmin = 0;
+    bool compact = false;
+    if (n > SORT_SMEM_N) {
+        long long mn = LLONG_MAX, mx = LLONG_MIN;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const long long z = proj(xy[k], dy, dx);
+            mn = min(mn, z);
+            mx = max(mx, z);
+        }
+        for (int m = 16; m >= 1; m >>= 1) {
+            mn = min(mn, __shfl_xor_sync(FULL, mn, m));
+            mx = max(mx, __shfl_xor_sync(FULL, mx, m));
+        }
+        __shared__ long long s_mn[32], s_mx[32];
+        if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; }
+        __syncthreads();
+        mn = s_mn[0];
+        mx = s_mx[0];
+        for (int k = 1; k < nw; ++k) { mn = min(mn, s_mn[k]); mx = max(mx, s_mx[k]); }
+        zmin = mn;
+        compact = mx - mn < (1LL << 32);
+    }
+    const bool wide = !compact && n > 32768;
+    unsigned short *pay = wide ? reinterpret_cast<unsigned short *>(gsort + (size_t)W * 2 * P) + (size_t)w * P
+                               : nullptr;
+    if (compact) {
+        auto cword = [&](int k) -> unsigned long long {
+            if (k >= n) return ~0ull;
+            const int pk = xy[k];
+            return ((unsigned long long)(proj(pk, dy, dx) - zmin) << 32) |
+                   ((unsigned long long)(unsigned)(32767 - px(pk)) << 16) | (unsigned long long)(unsigned)k;
+        };
+        a = cta_sort_chunked<8192>(reinterpret_cast<unsigned long long *>(smem), a, a + P, P, cword);
+    } else if (wide) {
         for (int k = threadIdx.x; k < P; k += blockDim.x) {
             if (k < n) {
                 const int pk = xy[k];
@@ -1461,9 +1497,13 @@ __global__ void __launch_bounds__(1024) k_sweep_init(const int *__restrict__ xy,
         __syncthreads();
         cta_bitonic_u64(a, P);
     }
-    auto akey = [&](int q) { return wide ? (long long)(a[q] >> 16) - (1LL << 32) : word_key(a[q]); };
+    auto akey = [&](int q) {
+        return compact ? (long long)(a[q] >> 32) + zmin
+                       : (wide ? (long long)(a[q] >> 16) - (1LL << 32) : word_key(a[q]));
+    };
     for (int k = threadIdx.x; k < n; k += blockDim.x)
-        orders[(size_t)w * n + k] = wide ? pay[k] : (unsigned short)word_index(a[k]);
+        orders[(size_t)w * n + k] =
+            compact ? (unsigned short)(a[k] & 0xffffu) : (wide ? pay[k] : (unsigned short)word_index(a[k]));
     // every window at the first slope
     long long bw = KEY_INF;
     int ba = 0x7fffffff;
@@ -2344,7 +2384,7 @@ size_t sweep_plan_bytes(const SweepPlan &p)
     b += a256((size_t)(emax > 0 ? emax : 1) * 4);   // merge copy of large buckets, list of a restricted pass
     b += a256((size_t)2 * W * 4);
     b += a256((size_t)W * n * 2);
-    b += (n > SORT_SMEM_N) ? a256((size_t)W * P * (n > 32768 ? 10 : 8)) : 0;
+    b += (n > SORT_SMEM_N) ? a256((size_t)W * P * 18) : 0;   // start sorts: 2 P words + P payloads per range
     b += a256((size_t)(2 * W + 8) * sizeof(Cand));
     b += p.pos_smem ? 0 : a256((size_t)p.G * n * 2);
     b += a256((size_t)BND_MAX * 8) + a256((size_t)(BND_MAX + 1) * 4) + a256(64);   // resplit buckets
@@ -2369,7 +2409,7 @@ void sweep_plan_carve(SweepPlan &p, void *ws)
     p.ev2 = (unsigned *)take((size_t)(p.emax > 0 ? p.emax : 1) * 4);
     p.range = (unsigned *)take((size_t)2 * p.W * 4);
     p.orders = (unsigned short *)take((size_t)p.W * p.n * 2);
-    p.gsort = (p.n > SORT_SMEM_N) ? (unsigned long long *)take((size_t)p.W * P * (p.n > 32768 ? 10 : 8)) : nullptr;
+    p.gsort = (p.n > SORT_SMEM_N) ? (unsigned long long *)take((size_t)p.W * P * 18) : nullptr;
     p.cands = (Cand *)take((size_t)(2 * p.W + 8) * sizeof(Cand));
     p.gpos = p.pos_smem ? nullptr : (unsigned short *)take((size_t)p.G * p.n * 2);
     p.bnd2 = (long long *)take((size_t)BND_MAX * 8);
@@ -2570,7 +2610,8 @@ cudaError_t launch_sweep_finish(const SweepPlan &p, const unsigned char *keep, c
     if (e != cudaSuccess) return e;
     int P = 1;
     while (P < n) P <<= 1;
-    const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)(P < 1024 ? 1024 : P) * 16 : 0;   // words + merge scratch
+    // words + merge scratch (whole sort, or one 8192-word chunk above SORT_SMEM_N)
+    const size_t init_smem = (n <= SORT_SMEM_N) ? (size_t)(P < 1024 ? 1024 : P) * 16 : (size_t)8192 * 16;
     cudaFuncSetAttribute(k_sweep_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)init_smem);
     {
         StageTimer _t(STAGE_INIT, st);
