@@ -347,34 +347,69 @@ __device__ bool cta_fill_merge_sort_any(T *s, T *s2, int P, F fill)
     }
 }
 
-// Merge of the sorted runs a[0, len) and b[0, len) into out[0, 2 len), all
-// in global memory: every thread writes an equal share of the outputs, its
-// start on the merge path found by a binary search on its diagonal (the
-// split with a[i - 1] <= b[d - i]; equal words are interchangeable).
-template <class T>
-__device__ void cta_merge_global(const T *a, const T *b, int len, T *out)
+// Merge of the sorted runs a[0, len) and b[0, len) (global memory) into
+// out[0, 2 len) through shared memory s of 2 TILE words: the outputs are cut
+// into tiles of TILE; the merge-path splits at every tile boundary (the
+// number of a's words among the first d outputs, ties taken from a first)
+// are found first, one binary search per boundary, all at once; then each
+// tile's inputs (TILE words of the two runs together) are read with
+// coalesced loads into s, merged there (each thread finds its start on the
+// tile's merge path by a binary search and merges its share into the second
+// half of s) and written out with coalesced stores.  Global memory is only
+// streamed, never chased word by word.  Every thread of the CTA calls it.
+constexpr int MERGE_SPLITS_MAX = 64;
+template <int TILE, class T>
+__device__ void cta_merge_tiled(const T *a, const T *b, int len, T *out, T *s)
 {
+    __shared__ int s_split[MERGE_SPLITS_MAX + 1];
     const int total = 2 * len;
-    const int per = (total + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int d = (int)threadIdx.x * per;
-    if (d >= total) return;
-    int lo = d > len ? d - len : 0, hi = d < len ? d : len;
-    while (lo < hi) {
-        const int m = (lo + hi) >> 1;
-        if (a[m] <= b[d - 1 - m]) lo = m + 1; else hi = m;
-    }
-    int i = lo, j = d - lo;
-    for (int o = d; o < d + per && o < total; ++o) {
-        const bool take_a = j >= len || (i < len && a[i] <= b[j]);
-        out[o] = take_a ? a[i++] : b[j++];
+    for (int t0 = 0; t0 < total; t0 += TILE * MERGE_SPLITS_MAX) {
+        const int nt = min(MERGE_SPLITS_MAX, (total - t0 + TILE - 1) / TILE);
+        for (int t = threadIdx.x; t <= nt; t += blockDim.x) {
+            const int d = min(t0 + t * TILE, total);
+            int lo = d > len ? d - len : 0, hi = d < len ? d : len;
+            while (lo < hi) {
+                const int m = (lo + hi) >> 1;
+                if (a[m] <= b[d - 1 - m]) lo = m + 1; else hi = m;
+            }
+            s_split[t] = lo;
+        }
+        __syncthreads();
+        for (int t = 0; t < nt; ++t) {
+            const int d0 = t0 + t * TILE, d1 = min(d0 + TILE, total);
+            const int i0 = s_split[t], i1 = s_split[t + 1];
+            const int j0 = d0 - i0, j1 = d1 - i1;
+            const int na = i1 - i0, nb = j1 - j0, m = d1 - d0;
+            for (int k = threadIdx.x; k < na; k += blockDim.x) s[k] = a[i0 + k];
+            for (int k = threadIdx.x; k < nb; k += blockDim.x) s[na + k] = b[j0 + k];
+            __syncthreads();
+            const int per = (m + (int)blockDim.x - 1) / (int)blockDim.x;
+            const int dd = (int)threadIdx.x * per;
+            if (dd < m) {
+                int lo = dd > nb ? dd - nb : 0, hi = dd < na ? dd : na;
+                while (lo < hi) {
+                    const int mm = (lo + hi) >> 1;
+                    if (s[mm] <= s[na + dd - 1 - mm]) lo = mm + 1; else hi = mm;
+                }
+                int i = lo, j = dd - lo;
+                for (int o = dd; o < dd + per && o < m; ++o) {
+                    const bool take_a = j >= nb || (i < na && s[i] <= s[na + j]);
+                    s[TILE + o] = take_a ? s[i++] : s[na + j++];
+                }
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < m; k += blockDim.x) out[d0 + k] = s[TILE + k];
+            __syncthreads();
+        }
     }
 }
 
 // Ascending sort of the P words key(0 .. P - 1) (P a power of two, a
 // multiple of Q) into global memory: chunks of Q words (Q = IPT blockDim.x
 // with IPT in 1 .. 16) are merge-sorted in shared memory (s: 2 Q words)
-// and written to A, then runs are merged pairwise between A and B.
-// Returns the buffer holding the result.  Every thread of the CTA calls it.
+// and written to A, then runs are merged pairwise between A and B
+// (cta_merge_tiled, with s as its tile space).  Returns the buffer holding
+// the result.  Every thread of the CTA calls it.
 template <int Q, class T, class F>
 __device__ T *cta_sort_chunked(T *s, T *A, T *B, int P, F key)
 {
@@ -385,7 +420,7 @@ __device__ T *cta_sort_chunked(T *s, T *A, T *B, int P, F key)
     }
     T *src = A, *dst = B;
     for (int len = Q; len < P; len <<= 1) {
-        for (int r = 0; r < P; r += 2 * len) cta_merge_global(src + r, src + r + len, len, dst + r);
+        for (int r = 0; r < P; r += 2 * len) cta_merge_tiled<Q>(src + r, src + r + len, len, dst + r, s);
         __syncthreads();
         T *t = src; src = dst; dst = t;
     }
