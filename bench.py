@@ -569,7 +569,7 @@ def _roof(stage, stages, units_per_fit, ops_per_unit, fits, peak_tops, mhz_basis
 # dram__bytes_write.sum) from the ncu captures summarised under profiles/;
 # a kernel changed after its capture has no entry.
 KERNEL_OF_STAGE = {"sweep": "k_sweep", "node_bounds": "k_node_lb"}
-DRAM_BYTES = {}
+DRAM_BYTES = {"k_node_lb": 152_320, "k_sweep": 386_048, "k_sweep_plain": 194_637_824}
 
 
 def _instances(seeds):

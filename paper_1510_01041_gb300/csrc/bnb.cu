@@ -1196,7 +1196,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     cudaFuncSetAttribute(k_tree_first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tree_smem);
     cudaFuncSetAttribute(k_tree_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tree_smem);
     {
-        StageTimer _t(STAGE_NODE_LB, st);
+        StageTimer _t(STAGE_TREE, st);
         k_tree_first<<<1, TREE_THREADS, tree_smem, st>>>(scount, p.meta, p.bnd, sms, sbase, nodes[0], nkeys[0], keep,
                                                           ts);
     }
@@ -1207,7 +1207,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
                                                     gscr);
         }
         {
-            StageTimer _t(STAGE_NODE_LB, st);
+            StageTimer _t(STAGE_TREE, st);
             k_tree_step<<<1, TREE_THREADS, tree_smem, st>>>(L, sms, p.meta, p.bnd, sbase, nodes[L & 1], prune,
                                                             nodes[(L + 1) & 1], nkeys[(L + 1) & 1], offs, keep, ts);
         }
@@ -1215,14 +1215,14 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     {
         // kept buckets cut into sub-intervals and bounded once more (lbv and
         // offs, no longer needed, hold the new boundaries and flags meanwhile)
-        StageTimer _t(STAGE_NODE_LB, st);
-        k_refine_nodes<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, scount, p.S, p.emax, sms, nkeys[0], ts);
-        k_node_lb<<<sms, 1024, two_sorts, st>>>(p.xy, n, h, xc, nkeys[0], &ts->refine, ub, prune, lbv, gscr);
+        { StageTimer _t(STAGE_TREE, st); k_refine_nodes<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, scount, p.S, p.emax, sms, nkeys[0], ts); }
+        { StageTimer _t(STAGE_NODE_LB, st); k_node_lb<<<sms, 1024, two_sorts, st>>>(p.xy, n, h, xc, nkeys[0], &ts->refine, ub, prune, lbv, gscr); }
+        StageTimer _t(STAGE_TREE, st);
         k_refine_apply<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, prune, scount, p.S, p.emax, sms, lbv,
                                                    reinterpret_cast<unsigned char *>(offs), ts);
     }
     {
-        StageTimer _t(STAGE_NODE_LB, st);
+        StageTimer _t(STAGE_TREE, st);
         k_tree_covers<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, runs, cov, ts);
     }
     // exact events of the kept buckets only: p.base becomes their starts

@@ -11,7 +11,7 @@ namespace lms {
 enum Stage {
     STAGE_PACK, STAGE_SAMPLE, STAGE_SAMPLE_SORT, STAGE_SPLITTERS, STAGE_COUNT_PAIRS, STAGE_PREFIX,
     STAGE_SCAN, STAGE_SCATTER, STAGE_SEGSORT, STAGE_SEGSORT_BIG, STAGE_PLAN, STAGE_INIT, STAGE_SWEEP,
-    STAGE_ARGMIN, STAGE_PLAIN, STAGE_OTHER, STAGE_NODE_LB, STAGE_SEEDS, STAGE_SETNET, STAGE_HOUGH,
+    STAGE_ARGMIN, STAGE_PLAIN, STAGE_OTHER, STAGE_NODE_LB, STAGE_SEEDS, STAGE_SETNET, STAGE_HOUGH, STAGE_TREE,
     STAGE_COUNT
 };
 

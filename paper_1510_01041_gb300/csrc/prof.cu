@@ -43,7 +43,7 @@ cudaEvent_t take_event()
 const char *const kNames[STAGE_COUNT] = {
     "pack", "sample", "sample_sort", "splitters", "count", "bucket_prefix", "bucket_scan", "scatter",
     "segsort", "segsort_big", "plan", "sweep_init", "sweep", "argmin", "plain", "other", "node_bounds", "seeds",
-    "setnet", "hough"};
+    "setnet", "hough", "tree"};
 
 }  // namespace
 
