@@ -280,14 +280,6 @@ __global__ void __launch_bounds__(1024) k_node_lb(const int *__restrict__ xy, in
     }
 }
 
-__global__ void k_min_ub(const long long *__restrict__ w, int nk, long long *__restrict__ ub)
-{
-    long long m = I64_MAX;
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) m = min(m, w[k]);
-    for (int s = 16; s >= 1; s >>= 1) m = min(m, __shfl_xor_sync(FULL, m, s));
-    if (threadIdx.x == 0) *ub = m;
-}
-
 constexpr unsigned long long BNB_MIN_RANGE = 64;   // events per swept range, at least
 #ifndef LMS_PRED_WINDOW
 #define LMS_PRED_WINDOW 0.35
@@ -543,17 +535,32 @@ __device__ __forceinline__ void node_keys_of(const long long *bnd, int NB, int b
 // min(NB, max(b_k, f_{k-1} + 1)), b_k the first bucket boundary reaching
 // k/m0 of the sampled pairs (b_m0 = NB), f_0 = 0; written as a prefix
 // maximum, f_k = min(NB, k + max_{j<=k} (b_j - j)).
+// It also writes the upper bound: the smallest of the nw seed widths w.
 __global__ void __launch_bounds__(TREE_THREADS) k_tree_first(const unsigned *__restrict__ counts,
                                                              const int *__restrict__ meta,
                                                              const long long *__restrict__ bnd, int sms,
                                                              unsigned *__restrict__ sbase, int2 *__restrict__ nodes,
                                                              long long *__restrict__ keys,
                                                              unsigned char *__restrict__ keep,
-                                                             TreeState *__restrict__ ts)
+                                                             TreeState *__restrict__ ts,
+                                                             const long long *__restrict__ w, int nw,
+                                                             long long *__restrict__ ub)
 {
     extern __shared__ unsigned s_base[];   // NB + 1 prefix values, for the searches
     __shared__ long long s_warp[32];
     __shared__ unsigned s_tot;
+    {
+        long long m = I64_MAX;
+        for (int k = threadIdx.x; k < nw; k += blockDim.x) m = min(m, w[k]);
+        for (int s = 16; s >= 1; s >>= 1) m = min(m, __shfl_xor_sync(FULL, m, s));
+        if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = min(m, s_warp[k]);
+            *ub = m;
+        }
+        __syncthreads();
+    }
     const int NB = meta[0] + 1;
     constexpr int PER = BND_MAX / TREE_THREADS;
     // exclusive scan of the counts, PER consecutive buckets per thread
@@ -1026,7 +1033,8 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_covers(const int *__restr
 // one after another, so R ranges of K kept events take about
 // (R / SMs) T_sort + (K / R) T_event; with T_sort / T_event about 128
 // events' worth at 152 SMs that is least near K / R = sqrt(0.8 K) events per
-// range.  At least BNB_MIN_RANGE events per range and at most W ranges.
+// range.  At least BNB_MIN_RANGE events per range, at least total / G (the
+// caller passes the SM count: one wave of start sorts) and at most W ranges.
 __global__ void __launch_bounds__(TREE_THREADS) k_tree_ranges(const int *__restrict__ meta,
                                                               const unsigned *__restrict__ base,
                                                               const int *__restrict__ runs, int W, int G,
@@ -1187,10 +1195,6 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
             k_score_dyadic<<<std::min(KS, grid), 1024, one_sort, st>>>(p.xy, n, h, xc, keys_r, KS, w_r, gscr);
         }
     }
-    {
-        StageTimer _t(STAGE_SEEDS, st);
-        k_min_ub<<<1, 32, 0, st>>>(seed_w, KS * rounds, ub);
-    }
     // the interval tree, level by level, all on the device
     const size_t tree_smem = (size_t)(BND_MAX + 1) * sizeof(unsigned);
     cudaFuncSetAttribute(k_tree_first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tree_smem);
@@ -1198,7 +1202,7 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     {
         StageTimer _t(STAGE_TREE, st);
         k_tree_first<<<1, TREE_THREADS, tree_smem, st>>>(scount, p.meta, p.bnd, sms, sbase, nodes[0], nkeys[0], keep,
-                                                          ts);
+                                                          ts, seed_w, KS * rounds, ub);
     }
     for (int L = 0; L < BNB_LEVELS; ++L) {
         {
@@ -1229,7 +1233,8 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     if (launch_sweep_count(p, keep, cov, band_scr, stats != nullptr, st) != cudaSuccess) return LMS_ERR_CUDA;
     {
         StageTimer _t(STAGE_PLAN, st);
-        k_tree_ranges<<<1, TREE_THREADS, 0, st>>>(p.meta, p.base, runs, p.W, p.G, p.range, ts);
+        // at least kept / SMs events a range: one wave of start sorts
+        k_tree_ranges<<<1, TREE_THREADS, 0, st>>>(p.meta, p.base, runs, p.W, std::min(p.G, sms), p.range, ts);
     }
     if (launch_sweep_finish(p, keep, st, false, true) != cudaSuccess) return LMS_ERR_CUDA;
     if (launch_argmin(p.cands, p.W + p.G, out, LMS_ALGO_BNB, p.meta + 3, st) != cudaSuccess) return LMS_ERR_CUDA;

@@ -600,6 +600,12 @@ __global__ void __launch_bounds__(BAND_THREADS) k_tile_pairs(const int *__restri
     for (int k = threadIdx.x; k < P2; k += blockDim.x) s_bnd[k] = bnd[k];
     for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0u;
     __syncthreads();
+    // hull of the covers: the first one's lower end to the last used one's upper end
+    float2 ghull = make_float2(INFINITY, -INFINITY);
+    for (int c = 0; c < PRE_MAX && s_fc[c].x < INFINITY; ++c) {
+        ghull.x = fminf(ghull.x, s_fc[c].x);
+        ghull.y = fmaxf(ghull.y, s_fc[c].y);
+    }
     const int lane = threadIdx.x & 31;
     unsigned *stk = s_stack[threadIdx.x >> 5];
     const unsigned below = (1u << lane) - 1u;
@@ -645,11 +651,14 @@ __global__ void __launch_bounds__(BAND_THREADS) k_tile_pairs(const int *__restri
                 if (dx != 0) {
                     if (dx < 0) { dx = -dx; dy = -dy; }
                     const float fx = (float)dx, fy = (float)dy;
-                    int c = 0;
+                    // the hull of all covers first: nearly every pair falls outside it
+                    if (ghull.x * fx <= fy && fy <= ghull.y * fx) {
+                        int c = 0;
 #pragma unroll
-                    for (int step = PRE_MAX; step >= 1; step >>= 1)
-                        if (s_fc[c + step - 1].x * fx <= fy) c += step;
-                    cand = c > 0 && fy <= s_fc[c - 1].y * fx;
+                        for (int step = PRE_MAX; step >= 1; step >>= 1)
+                            if (s_fc[c + step - 1].x * fx <= fy) c += step;
+                        cand = c > 0 && fy <= s_fc[c - 1].y * fx;
+                    }
                 }
             }
             const unsigned m = __ballot_sync(FULL, cand);
@@ -792,13 +801,6 @@ __global__ void __launch_bounds__(CNT_THREADS) k_list_hist(const void *__restric
         if (s_cnt[k]) atomicAdd(&total[k], s_cnt[k]);
 }
 
-__global__ void k_copy_starts(const unsigned *__restrict__ base, const int *__restrict__ meta,
-                              unsigned *__restrict__ cursor)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b <= meta[0]) cursor[b] = base[b];
-}
-
 // Per bucket: the number of valid sampled keys in it (the sample is sorted
 // and the buckets are its quantile ranges, so two binary searches suffice).
 __global__ void k_sample_counts(const long long *__restrict__ sorted, int S, const long long *__restrict__ bnd,
@@ -833,7 +835,9 @@ __global__ void k_bucket_prefix(unsigned *__restrict__ hist, int C, const int *_
 }
 
 // Exclusive scan of bucket totals (in place, NB <= BND_MAX); base[NB] = E.
-__global__ void __launch_bounds__(1024) k_bucket_scan(unsigned *__restrict__ base, const int *__restrict__ meta)
+// copy (optional): receives the bucket starts too (the list scatter's cursors).
+__global__ void __launch_bounds__(1024) k_bucket_scan(unsigned *__restrict__ base, const int *__restrict__ meta,
+                                                      unsigned *__restrict__ copy = nullptr)
 {
     __shared__ unsigned s[1024];
     const int NB = meta[0] + 1;
@@ -853,6 +857,7 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(unsigned *__restrict__ bas
     for (int b = b0; b < b0 + per && b < NB; ++b) {
         unsigned v = base[b];
         base[b] = run;
+        if (copy) copy[b] = run;
         run += v;
     }
     if (threadIdx.x == 1023) base[NB] = s[1023];
@@ -2520,7 +2525,8 @@ cudaError_t launch_sweep_count(const SweepPlan &p, const unsigned char *keep, co
         k_distinct_x_pairs<<<1, 1024, 32768 * 4, st>>>(p.xy, n, p.meta);
     }
     { StageTimer _t(STAGE_PREFIX, st); k_bucket_prefix<<<(BND_MAX + 255) / 256, 256, 0, st>>>(p.hist, p.C, p.meta, p.base); }
-    { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta); }
+    // without a resplit the list scatter's cursors are these bucket starts
+    { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base, p.meta, p.resplit ? nullptr : p.hist); }
     return cudaGetLastError();
 }
 
@@ -2559,12 +2565,12 @@ cudaError_t launch_events_finish(const SweepPlan &p, const void *pts, const unsi
             if (cudaMemsetAsync(p.base2, 0, (size_t)(BND_MAX + 1) * 4, st) != cudaSuccess) return cudaGetLastError();
             cudaFuncSetAttribute(k_list_hist<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
             { StageTimer _t(STAGE_COUNT_PAIRS, st); k_list_hist<G><<<p.C, CNT_THREADS, bsm, st>>>(pts, p.bnd2, p.meta2, p.ev2, p.meta + 6, p.base2); }
-            { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base2, p.meta2); }
+            { StageTimer _t(STAGE_SCAN, st); k_bucket_scan<<<1, 1024, 0, st>>>(p.base2, p.meta2, cursor); }
             sbnd = p.bnd2;
             sbase = p.base2;
             smeta = p.meta2;
         }
-        { StageTimer _t(STAGE_SCATTER, st); k_copy_starts<<<(BND_MAX + 255) / 256, 256, 0, st>>>(sbase, smeta, cursor); }
+        // cursor: the bucket starts, written by the scan of the count (or of the resplit)
         cudaFuncSetAttribute(k_scatter_list<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
         StageTimer _t(STAGE_SCATTER, st);
         k_scatter_list<G><<<p.C, CNT_THREADS, bsm, st>>>(pts, sbnd, smeta, p.ev2, cursor, p.ev, p.meta + 6);
