@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_first(const unsigned *__r
 // m'_q = min(max(m_q, m'_{q-1} + 1), b1 - parts + q), m_q the first bucket
 // boundary above q/parts of the node's sampled pairs; with u_q = m'_q - q this
 // is u_q = max(b0, max_{j<=q} min(m_j - j, b1 - parts)), one warp per node.
-__global__ void __launch_bounds__(TREE_THREADS) k_tree_step(int level, int sms, const int *__restrict__ meta,
+__device__ void tree_step_body(int level, int sms, const int *__restrict__ meta,
                                                             const long long *__restrict__ bnd,
                                                             const unsigned *__restrict__ sbase,
                                                             const int2 *__restrict__ cur,
@@ -811,7 +811,7 @@ __device__ __forceinline__ long long sub_key(long long lo, long long hi, int i, 
     return lo + (hi - lo) * i / Fb;
 }
 
-__global__ void __launch_bounds__(TREE_THREADS) k_refine_nodes(const int *__restrict__ meta,
+__device__ void refine_nodes_body(const int *__restrict__ meta,
                                                                const long long *__restrict__ bnd,
                                                                const unsigned char *__restrict__ keep,
                                                                const unsigned *__restrict__ scount, int S,
@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_refine_nodes(const int *__rest
 // Replace the buckets by their sub-intervals: boundaries and keep flags into
 // the scratch arrays, then copied over bnd (padded with I64_MAX to the new
 // power of two) and keep, and the new counts into meta.
-__global__ void __launch_bounds__(TREE_THREADS) k_refine_apply(int *__restrict__ meta, long long *__restrict__ bnd,
+__device__ void refine_apply_body(int *__restrict__ meta, long long *__restrict__ bnd,
                                                                unsigned char *__restrict__ keep,
                                                                const unsigned char *__restrict__ prune,
                                                                const unsigned *__restrict__ scount, int S,
@@ -908,7 +908,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_refine_apply(int *__restrict__
 // neighbours one at a time; gaps measured in slope); each cover is the key
 // range from its first run's start to its last run's end.  Unused entries
 // are empty ranges.
-__global__ void __launch_bounds__(TREE_THREADS) k_tree_covers(const int *__restrict__ meta,
+__device__ void tree_covers_body(const int *__restrict__ meta,
                                                               const long long *__restrict__ bnd,
                                                               const unsigned char *__restrict__ keep,
                                                               int *__restrict__ runs, long long *__restrict__ cov,
@@ -1021,6 +1021,44 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_covers(const int *__restr
         for (int c = nc; c < PRE_MAX; ++c) cov[2 * c] = cov[2 * c + 1] = I64_MAX;   // empty
         ts->covers = nc;
     }
+}
+
+// The tree kernels.  The last tree step also plans the refinement (its
+// sub-intervals' keys into rkeys, their number into ts->refine); the covers
+// kernel first applies it (the bounds of the sub-intervals are computed
+// between the two), so the refinement costs no launches of its own.
+__global__ void __launch_bounds__(TREE_THREADS) k_tree_step(int level, int sms, const int *__restrict__ meta,
+                                                            const long long *__restrict__ bnd,
+                                                            const unsigned *__restrict__ sbase,
+                                                            const int2 *__restrict__ cur,
+                                                            const unsigned char *__restrict__ prune,
+                                                            int2 *__restrict__ nxt, long long *__restrict__ nkeys,
+                                                            int *__restrict__ offs,
+                                                            unsigned char *__restrict__ keep,
+                                                            TreeState *__restrict__ ts,
+                                                            const unsigned *__restrict__ scount, int S,
+                                                            long long emax, long long *__restrict__ rkeys)
+{
+    tree_step_body(level, sms, meta, bnd, sbase, cur, prune, nxt, nkeys, offs, keep, ts);
+    if (level == BNB_LEVELS - 1) {
+        __syncthreads();
+        refine_nodes_body(meta, bnd, keep, scount, S, emax, sms, rkeys, ts);
+    }
+}
+
+__global__ void __launch_bounds__(TREE_THREADS) k_tree_covers(int *__restrict__ meta, long long *__restrict__ bnd,
+                                                              unsigned char *__restrict__ keep,
+                                                              const unsigned char *__restrict__ prune,
+                                                              const unsigned *__restrict__ scount, int S,
+                                                              long long emax, int sms,
+                                                              long long *__restrict__ bnd_tmp,
+                                                              unsigned char *__restrict__ keep_tmp,
+                                                              int *__restrict__ runs, long long *__restrict__ cov,
+                                                              TreeState *__restrict__ ts)
+{
+    refine_apply_body(meta, bnd, keep, prune, scount, S, emax, sms, bnd_tmp, keep_tmp, ts);
+    __syncthreads();
+    tree_covers_body(meta, bnd, keep, runs, cov, ts);
 }
 
 // Sweep ranges over the kept events (after the restricted count: base holds
@@ -1204,6 +1242,9 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         k_tree_first<<<1, TREE_THREADS, tree_smem, st>>>(scount, p.meta, p.bnd, sms, sbase, nodes[0], nkeys[0], keep,
                                                           ts, seed_w, KS * rounds, ub);
     }
+    // the refinement's sub-interval keys: the last level's input keys, consumed
+    // by its bounds before the last tree step writes them
+    long long *rkeys = nkeys[(BNB_LEVELS - 1) & 1];
     for (int L = 0; L < BNB_LEVELS; ++L) {
         {
             StageTimer _t(STAGE_NODE_LB, st);
@@ -1213,21 +1254,21 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
         {
             StageTimer _t(STAGE_TREE, st);
             k_tree_step<<<1, TREE_THREADS, tree_smem, st>>>(L, sms, p.meta, p.bnd, sbase, nodes[L & 1], prune,
-                                                            nodes[(L + 1) & 1], nkeys[(L + 1) & 1], offs, keep, ts);
+                                                            nodes[(L + 1) & 1], nkeys[(L + 1) & 1], offs, keep, ts,
+                                                            scount, p.S, p.emax, rkeys);
         }
     }
     {
-        // kept buckets cut into sub-intervals and bounded once more (lbv and
-        // offs, no longer needed, hold the new boundaries and flags meanwhile)
-        { StageTimer _t(STAGE_TREE, st); k_refine_nodes<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, scount, p.S, p.emax, sms, nkeys[0], ts); }
-        { StageTimer _t(STAGE_NODE_LB, st); k_node_lb<<<sms, 1024, two_sorts, st>>>(p.xy, n, h, xc, nkeys[0], &ts->refine, ub, prune, lbv, gscr); }
-        StageTimer _t(STAGE_TREE, st);
-        k_refine_apply<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, prune, scount, p.S, p.emax, sms, lbv,
-                                                   reinterpret_cast<unsigned char *>(offs), ts);
+        // the kept buckets' sub-intervals (planned by the last tree step) bounded
+        StageTimer _t(STAGE_NODE_LB, st);
+        k_node_lb<<<sms, 1024, two_sorts, st>>>(p.xy, n, h, xc, rkeys, &ts->refine, ub, prune, lbv, gscr);
     }
     {
+        // refinement applied (lbv and offs, no longer needed, hold the new
+        // boundaries and flags meanwhile), then the covers
         StageTimer _t(STAGE_TREE, st);
-        k_tree_covers<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, runs, cov, ts);
+        k_tree_covers<<<1, TREE_THREADS, 0, st>>>(p.meta, p.bnd, keep, prune, scount, p.S, p.emax, sms, lbv,
+                                                  reinterpret_cast<unsigned char *>(offs), runs, cov, ts);
     }
     // exact events of the kept buckets only: p.base becomes their starts
     if (launch_sweep_count(p, keep, cov, band_scr, stats != nullptr, st) != cudaSuccess) return LMS_ERR_CUDA;
