@@ -911,6 +911,99 @@ __device__ void merge_halves_to_events(const unsigned long long *A, const unsign
     }
 }
 
+// Sort of m <= SEG_CAP events src[0, m) whose keys lie in [klo, klo + span)
+// into dst (src == dst allowed) by (exact slope key, pair), with the
+// "same slope as the previous event" flags; false (dst untouched) when it
+// cannot (a cell of equal shifted keys needing more than SEG_REPAIR_MAX
+// passes, or no merge-sort shape for the size).  The word
+// ((key - klo) >> sh) << 32 | pair, with sh the smallest shift that brings
+// the span below 2^32, orders events by (key, pair) except inside a cell of
+// equal shifted keys, where it orders them by pair alone.  The words are
+// sorted in registers and shared memory; when sh > 0 the rare cells of two
+// or more events are then put in (key, pair) order by odd-even
+// transposition with the exact keys.  (int16 keys of one bucket span less
+// than 2^32: sh = 0 and no repair.)  smem: SEG_CAP * 12 bytes.  Every
+// thread of the CTA calls it.
+template <class G>
+__device__ bool sort_bucket_words(const void *__restrict__ xy, const unsigned *src, unsigned *dst, unsigned m,
+                                  long long klo, unsigned long long span, unsigned char *smem)
+{
+    int P = 1;
+    while (P < (int)m) P <<= 1;
+    const int sh = span > 0xffffffffull ? 32 - __clzll((long long)span) : 0;
+    unsigned long long *w = reinterpret_cast<unsigned long long *>(smem);
+    auto word = [&](int k) {
+        if (k >= (int)m) return ~0ull;
+        const unsigned e = src[k];
+        return (((unsigned long long)event_key<G>(xy, e) - (unsigned long long)klo) >> sh << 32) | pair_of(e);
+    };
+    auto exact = [&](unsigned long long v) {
+        return event_key<G>(xy, ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), false));
+    };
+    // (key, pair) order of two words; the padding word ~0 is last
+    auto less = [&](unsigned long long u, unsigned long long v) {
+        if (sh == 0 || (u >> 32) != (v >> 32) || u == ~0ull || v == ~0ull) return u < v;
+        const long long ku = exact(u), kv = exact(v);
+        return ku < kv || (ku == kv && (unsigned)u < (unsigned)v);
+    };
+    auto same = [&](unsigned long long u, unsigned long long v) {
+        return (u >> 32) == (v >> 32) && (sh == 0 || exact(u) == exact(v));
+    };
+    auto repair = [&](unsigned long long *a, int len) {
+        if (sh == 0) return true;
+        int cells = 0;
+        for (int k = threadIdx.x; k + 1 < len; k += blockDim.x) cells |= (a[k] >> 32) == (a[k + 1] >> 32);
+        if (!__syncthreads_or(cells)) return true;
+        for (int pass = 0; pass < SEG_REPAIR_MAX; ++pass) {
+            int swapped = 0;
+            for (int par = 0; par < 2; ++par) {
+                for (int k = 2 * (int)threadIdx.x + par; k + 1 < len; k += 2 * (int)blockDim.x) {
+                    const unsigned long long u = a[k], v = a[k + 1];
+                    if ((u >> 32) == (v >> 32) && less(v, u)) {
+                        a[k] = v;
+                        a[k + 1] = u;
+                        swapped = 1;
+                    }
+                }
+                __syncthreads();
+            }
+            if (!__syncthreads_or(swapped)) return true;
+        }
+        return false;
+    };
+    __syncthreads();
+    const int Pw = P < (int)blockDim.x ? (int)blockDim.x : P;
+    if (2 * Pw > SEG_CAP * 3 / 2 && Pw == 2 * (int)blockDim.x * 8) {
+        // too large for one merge sort and its scratch: two halves are
+        // merge-sorted one after the other (scratch after both), then merged
+        // by merge path straight into the event array
+        const int Hh = Pw / 2;
+        unsigned long long *A = w, *Bw = w + Hh, *scr = w + 2 * Hh;
+        cta_fill_merge_sort<8>(A, scr, Hh, word);
+        cta_fill_merge_sort<8>(Bw, scr, Hh, [&](int k) { return word(Hh + k); });
+        __syncthreads();
+        const bool ok = repair(A, Hh);
+        if (!(ok && repair(Bw, (int)m - Hh))) return false;
+        if (src == dst) __syncthreads();
+        merge_halves_to_events(A, Bw, Hh, (int)m, dst, less, same);
+        __syncthreads();
+        return true;
+    }
+    // merge sort (registers, then merge-path levels) where its scratch copy
+    // fits beside the words, else the register-blocked bitonic sort
+    const bool sorted = 2 * Pw <= SEG_CAP * 3 / 2 ? cta_fill_merge_sort_any(w, w + Pw, Pw, word)
+                                                   : cta_fill_sort_any(w, Pw, word);
+    if (sorted) __syncthreads();
+    if (!(sorted && repair(w, (int)m))) return false;
+    for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
+        const unsigned long long v = w[k];
+        const bool cont = k > 0 && same(w[k - 1], v);
+        dst[k] = ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), cont);
+    }
+    __syncthreads();
+    return true;
+}
+
 // Sort each bucket by (exact slope key, pair); buckets with more than
 // SEG_CAP events are listed for k_segsort_big.  A bucket holding a single
 // slope only needs its smallest pair moved to the front.
@@ -988,93 +1081,11 @@ __global__ void __launch_bounds__(1024) k_segsort(const void *__restrict__ xy, u
             }
             int P = 1;
             while (P < (int)m) P <<= 1;
-            // An interior bucket holds keys in [bnd[b - 1], bnd[b]).  The word
-            // ((key - bnd[b - 1]) >> sh) << 32 | pair, with sh the smallest shift
-            // that brings the span below 2^32, orders events by (key, pair)
-            // except inside a cell of equal shifted keys, where it orders them
-            // by pair alone.  The words are sorted in registers; when sh > 0 the
-            // rare cells of two or more events are then put in (key, pair)
-            // order by odd-even transposition with the exact keys.  (int16 keys
-            // of one bucket span less than 2^32: sh = 0 and no repair.)
-            if (b > 0 && b < NB - 1) {
-                const long long klo = bnd[b - 1];
-                const unsigned long long span = (unsigned long long)(bnd[b] - bnd[b - 1]);
-                const int sh = span > 0xffffffffull ? 32 - __clzll((long long)span) : 0;
-                unsigned long long *w = reinterpret_cast<unsigned long long *>(smem);
-                auto word = [&](int k) {
-                    if (k >= (int)m) return ~0ull;
-                    const unsigned e = ev[off + k];
-                    return ((unsigned long long)(event_key<G>(xy, e) - klo) >> sh << 32) | pair_of(e);
-                };
-                auto exact = [&](unsigned long long v) {
-                    return event_key<G>(xy, ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), false));
-                };
-                // (key, pair) order of two words; the padding word ~0 is last
-                auto less = [&](unsigned long long u, unsigned long long v) {
-                    if (sh == 0 || (u >> 32) != (v >> 32) || u == ~0ull || v == ~0ull) return u < v;
-                    const long long ku = exact(u), kv = exact(v);
-                    return ku < kv || (ku == kv && (unsigned)u < (unsigned)v);
-                };
-                auto same = [&](unsigned long long u, unsigned long long v) {
-                    return (u >> 32) == (v >> 32) && (sh == 0 || exact(u) == exact(v));
-                };
-                // false when a cell needs more than SEG_REPAIR_MAX passes (then
-                // the bucket goes to the exact-key bitonic sort below)
-                auto repair = [&](unsigned long long *a, int len) {
-                    if (sh == 0) return true;
-                    int cells = 0;
-                    for (int k = threadIdx.x; k + 1 < len; k += blockDim.x) cells |= (a[k] >> 32) == (a[k + 1] >> 32);
-                    if (!__syncthreads_or(cells)) return true;
-                    for (int pass = 0; pass < SEG_REPAIR_MAX; ++pass) {
-                        int swapped = 0;
-                        for (int par = 0; par < 2; ++par) {
-                            for (int k = 2 * (int)threadIdx.x + par; k + 1 < len; k += 2 * (int)blockDim.x) {
-                                const unsigned long long u = a[k], v = a[k + 1];
-                                if ((u >> 32) == (v >> 32) && less(v, u)) {
-                                    a[k] = v;
-                                    a[k + 1] = u;
-                                    swapped = 1;
-                                }
-                            }
-                            __syncthreads();
-                        }
-                        if (!__syncthreads_or(swapped)) return true;
-                    }
-                    return false;
-                };
-                __syncthreads();
-                const int Pw = P < (int)blockDim.x ? (int)blockDim.x : P;
-                if (2 * Pw > SEG_CAP * 3 / 2 && Pw == 2 * (int)blockDim.x * 8) {
-                    // too large for one merge sort and its scratch: two halves are
-                    // merge-sorted one after the other (scratch after both), then
-                    // merged by merge path straight into the event array
-                    const int Hh = Pw / 2;
-                    unsigned long long *A = w, *Bw = w + Hh, *scr = w + 2 * Hh;
-                    cta_fill_merge_sort<8>(A, scr, Hh, word);
-                    cta_fill_merge_sort<8>(Bw, scr, Hh, [&](int k) { return word(Hh + k); });
-                    __syncthreads();
-                    const bool ok = repair(A, Hh);
-                    if (ok && repair(Bw, (int)m - Hh)) {
-                        merge_halves_to_events(A, Bw, Hh, (int)m, ev + off, less, same);
-                        continue;
-                    }
-                } else {
-                    // merge sort (registers, then merge-path levels) where its
-                    // scratch copy fits beside the words, else the register-blocked
-                    // bitonic sort
-                    const bool sorted = 2 * Pw <= SEG_CAP * 3 / 2 ? cta_fill_merge_sort_any(w, w + Pw, Pw, word)
-                                                                   : cta_fill_sort_any(w, Pw, word);
-                    if (sorted) __syncthreads();
-                    if (sorted && repair(w, (int)m)) {
-                        for (int k = threadIdx.x; k < (int)m; k += blockDim.x) {
-                            const unsigned long long v = w[k];
-                            const bool cont = k > 0 && same(w[k - 1], v);
-                            ev[off + k] = ev_pack((int)((v >> 16) & 0xffffu), (int)(v & 0xffffu), cont);
-                        }
-                        continue;
-                    }
-                }
-            }
+            // an interior bucket: its keys lie in [bnd[b - 1], bnd[b])
+            if (b > 0 && b < NB - 1 &&
+                sort_bucket_words<G>(xy, ev + off, ev + off, m, bnd[b - 1],
+                                     (unsigned long long)bnd[b] - (unsigned long long)bnd[b - 1], smem))
+                continue;
             __syncthreads();
             for (int k = threadIdx.x; k < P; k += blockDim.x) {
                 if (k < (int)m) {
@@ -1111,12 +1122,118 @@ __global__ void __launch_bounds__(1024) k_segsort(const void *__restrict__ xy, u
     }
 }
 
-// Buckets above SEG_CAP events, one CTA each: chunks of SEG_CAP events are
-// sorted in shared memory and written back, then runs are merged pairwise
-// (merge path: every thread finds its output range by a binary search on
-// the diagonal and merges it sequentially) between the bucket and its copy
-// in ev2, keys recomputed from the points.  (key, pair) is a strict total
-// order, so the result is the one of a full sort.
+// Buckets above SEG_CAP events, one CTA each, by one more level of sample
+// sort inside the bucket: SB_SAMPLE evenly spaced events' keys are sorted
+// and give F - 1 splitters (about SB_TARGET events a sub-bucket; a key equal
+// to a splitter goes above it, so equal keys share a sub-bucket); one pass
+// counts the events of every sub-bucket (and the bucket's least and largest
+// key), a second moves them, grouped by sub-bucket, into the bucket's range
+// of ev2, and each sub-bucket is then sorted from there into its place in ev
+// by the word sort of the ordinary buckets, its keys in [splitter below,
+// splitter above).  The buckets are sorted by (key, pair) and key ranges of
+// sub-buckets do not overlap, so the result is the bucket's full sort.  A
+// sub-bucket still above SEG_CAP (a slope shared by very many pairs) is
+// sorted by the merge fallback: SEG_CAP-event chunks in shared memory, then
+// pairwise merges with keys recomputed from the points.
+constexpr int SB_SAMPLE = 2048;
+constexpr int SB_TARGET = 6144;
+constexpr int SB_MAX = 256;   // sub-buckets of one bucket
+
+template <class G>
+__device__ void sort_big_merge(const void *__restrict__ xy, unsigned *A, unsigned *scratch, unsigned m,
+                               unsigned char *smem)
+{
+    long long *s_key = reinterpret_cast<long long *>(smem);
+    unsigned *s_ev = reinterpret_cast<unsigned *>(smem + SEG_CAP * sizeof(long long));
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // sorted runs of SEG_CAP events
+    for (unsigned c0 = 0; c0 < m; c0 += SEG_CAP) {
+        const int mc = (int)min((unsigned)SEG_CAP, m - c0);
+        int P = 1;
+        while (P < mc) P <<= 1;
+        for (int k = tid; k < P; k += nt) {
+            if (k < mc) {
+                const unsigned e = A[c0 + k];
+                s_key[k] = event_key<G>(xy, e);
+                s_ev[k] = e;
+            } else {
+                s_key[k] = KEY_INF;
+                s_ev[k] = 0xffffffffu;
+            }
+        }
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j >= 1; j >>= 1) {
+                for (int t = tid; t < P / 2; t += nt) {
+                    const int i = 2 * t - (t & (j - 1));
+                    const int l = i + j;
+                    const bool up = (i & k) == 0;
+                    const long long a = s_key[i], c = s_key[l];
+                    const unsigned ea = s_ev[i], ec = s_ev[l];
+                    if (up ? ev_less(c, ec, a, ea) : ev_less(a, ea, c, ec)) {
+                        s_key[i] = c; s_key[l] = a;
+                        s_ev[i] = ec; s_ev[l] = ea;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int k = tid; k < mc; k += nt) A[c0 + k] = s_ev[k];
+        __syncthreads();
+    }
+    // pairwise merges of the runs
+    unsigned *src = A, *dst = scratch;
+    for (unsigned L = SEG_CAP; L < m; L <<= 1) {
+        for (unsigned r0 = 0; r0 < m; r0 += 2 * L) {
+            const int la = (int)min(L, m - r0);
+            const int lb = (int)min(L, m - r0 - la);
+            const unsigned *ra = src + r0, *rb = src + r0 + la;
+            unsigned *o = dst + r0;
+            const long long T = (long long)la + lb;
+            const int d0 = (int)(T * tid / nt), d1 = (int)(T * (tid + 1) / nt);
+            auto split = [&](int d) {
+                int lo = max(0, d - lb), hi = min(d, la);
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const unsigned x = ra[mid], y = rb[d - 1 - mid];
+                    if (ev_less(event_key<G>(xy, x), x, event_key<G>(xy, y), y)) lo = mid + 1;
+                    else hi = mid;
+                }
+                return lo;
+            };
+            int ia = split(d0), ib = d0 - ia;
+            long long ka = ia < la ? event_key<G>(xy, ra[ia]) : KEY_INF;
+            long long kb = ib < lb ? event_key<G>(xy, rb[ib]) : KEY_INF;
+            for (int d = d0; d < d1; ++d) {
+                const bool take_a = ib >= lb || (ia < la && ev_less(ka, ra[ia], kb, rb[ib]));
+                if (take_a) {
+                    o[d] = ra[ia];
+                    ++ia;
+                    ka = ia < la ? event_key<G>(xy, ra[ia]) : KEY_INF;
+                } else {
+                    o[d] = rb[ib];
+                    ++ib;
+                    kb = ib < lb ? event_key<G>(xy, rb[ib]) : KEY_INF;
+                }
+            }
+        }
+        __syncthreads();
+        unsigned *t = src; src = dst; dst = t;
+    }
+    if (src != A) {
+        for (unsigned k = tid; k < m; k += nt) A[k] = src[k];
+        __syncthreads();
+    }
+    // group flags; decoding ignores the halves' order, so neighbours may
+    // be rewritten concurrently
+    for (unsigned k = tid; k < m; k += nt) {
+        const unsigned e = A[k];
+        const bool c = k > 0 && event_key<G>(xy, A[k - 1]) == event_key<G>(xy, e);
+        A[k] = ev_pack(ev_i(e), ev_j(e), c);
+    }
+    __syncthreads();
+}
+
 template <class G>
 __global__ void __launch_bounds__(1024) k_segsort_big(const void *__restrict__ xy, unsigned *__restrict__ ev,
                                                       unsigned *__restrict__ ev2,
@@ -1125,98 +1242,88 @@ __global__ void __launch_bounds__(1024) k_segsort_big(const void *__restrict__ x
                                                       const int *__restrict__ oversize)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    long long *s_key = reinterpret_cast<long long *>(smem);
-    unsigned *s_ev = reinterpret_cast<unsigned *>(smem + SEG_CAP * sizeof(long long));
+    __shared__ long long s_spl[SB_MAX];
+    __shared__ unsigned s_cnt[SB_MAX + 1], s_cur[SB_MAX];
+    __shared__ long long s_kmin[32], s_kmax[32];
+    __shared__ int s_F;
     const int nbig = meta[2];
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
     for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
         const int b = oversize[q];
         const unsigned off = base[b], m = base[b + 1] - off;
-        unsigned *A = ev + off;
-        // sorted runs of SEG_CAP events
-        for (unsigned c0 = 0; c0 < m; c0 += SEG_CAP) {
-            const int mc = (int)min((unsigned)SEG_CAP, m - c0);
-            int P = 1;
-            while (P < mc) P <<= 1;
-            for (int k = tid; k < P; k += nt) {
-                if (k < mc) {
-                    const unsigned e = A[c0 + k];
-                    s_key[k] = event_key<G>(xy, e);
-                    s_ev[k] = e;
-                } else {
-                    s_key[k] = KEY_INF;
-                    s_ev[k] = 0xffffffffu;
-                }
+        unsigned *A = ev + off, *C = ev2 + off;
+        // splitters from a sorted sample of the bucket's keys
+        long long *sw = reinterpret_cast<long long *>(smem);
+        cta_fill_merge_sort<SB_SAMPLE / 1024>(sw, sw + SB_SAMPLE, SB_SAMPLE, [&](int k) {
+            return event_key<G>(xy, A[(unsigned)(((unsigned long long)k * m) / SB_SAMPLE)]);
+        });
+        if (tid == 0) s_F = (int)min((unsigned)SB_MAX, (m + SB_TARGET - 1) / SB_TARGET);
+        __syncthreads();
+        const int F = s_F;
+        for (int j = tid; j < F - 1; j += nt) s_spl[j] = sw[((j + 1) * SB_SAMPLE) / F];
+        for (int j = tid; j <= F; j += nt) s_cnt[j] = 0u;
+        __syncthreads();
+        auto sub_of = [&](long long key) {   // splitters <= key
+            int lo = 0, hi = F - 1;
+            while (lo < hi) {
+                const int md = (lo + hi) >> 1;
+                if (s_spl[md] <= key) lo = md + 1; else hi = md;
             }
-            __syncthreads();
-            for (int k = 2; k <= P; k <<= 1) {
-                for (int j = k >> 1; j >= 1; j >>= 1) {
-                    for (int t = tid; t < P / 2; t += nt) {
-                        const int i = 2 * t - (t & (j - 1));
-                        const int l = i + j;
-                        const bool up = (i & k) == 0;
-                        const long long a = s_key[i], c = s_key[l];
-                        const unsigned ea = s_ev[i], ec = s_ev[l];
-                        if (up ? ev_less(c, ec, a, ea) : ev_less(a, ea, c, ec)) {
-                            s_key[i] = c; s_key[l] = a;
-                            s_ev[i] = ec; s_ev[l] = ea;
-                        }
-                    }
-                    __syncthreads();
-                }
+            return lo;
+        };
+        // counts per sub-bucket, least and largest key
+        long long kmn = KEY_INF, kmx = -KEY_INF;
+        for (unsigned k = tid; k < m; k += nt) {
+            const long long key = event_key<G>(xy, A[k]);
+            kmn = min(kmn, key);
+            kmx = max(kmx, key);
+            atomicAdd(&s_cnt[sub_of(key)], 1u);
+        }
+        for (int s = 16; s >= 1; s >>= 1) {
+            kmn = min(kmn, __shfl_xor_sync(FULL, kmn, s));
+            kmx = max(kmx, __shfl_xor_sync(FULL, kmx, s));
+        }
+        if (lane == 0) { s_kmin[warp] = kmn; s_kmax[warp] = kmx; }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned run = 0;
+            for (int j = 0; j < F; ++j) {
+                const unsigned c = s_cnt[j];
+                s_cnt[j] = run;
+                s_cur[j] = run;
+                run += c;
             }
-            for (int k = tid; k < mc; k += nt) A[c0 + k] = s_ev[k];
-            __syncthreads();
+            s_cnt[F] = run;
+            long long a = s_kmin[0], z = s_kmax[0];
+            for (int w = 1; w < (int)(nt >> 5); ++w) { a = min(a, s_kmin[w]); z = max(z, s_kmax[w]); }
+            s_kmin[0] = a;
+            s_kmax[0] = z;
         }
-        // pairwise merges of the runs
-        unsigned *src = A, *dst = ev2 + off;
-        for (unsigned L = SEG_CAP; L < m; L <<= 1) {
-            for (unsigned r0 = 0; r0 < m; r0 += 2 * L) {
-                const int la = (int)min(L, m - r0);
-                const int lb = (int)min(L, m - r0 - la);
-                const unsigned *ra = src + r0, *rb = src + r0 + la;
-                unsigned *o = dst + r0;
-                const long long T = (long long)la + lb;
-                const int d0 = (int)(T * tid / nt), d1 = (int)(T * (tid + 1) / nt);
-                auto split = [&](int d) {
-                    int lo = max(0, d - lb), hi = min(d, la);
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        const unsigned x = ra[mid], y = rb[d - 1 - mid];
-                        if (ev_less(event_key<G>(xy, x), x, event_key<G>(xy, y), y)) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    return lo;
-                };
-                int ia = split(d0), ib = d0 - ia;
-                long long ka = ia < la ? event_key<G>(xy, ra[ia]) : KEY_INF;
-                long long kb = ib < lb ? event_key<G>(xy, rb[ib]) : KEY_INF;
-                for (int d = d0; d < d1; ++d) {
-                    const bool take_a = ib >= lb || (ia < la && ev_less(ka, ra[ia], kb, rb[ib]));
-                    if (take_a) {
-                        o[d] = ra[ia];
-                        ++ia;
-                        ka = ia < la ? event_key<G>(xy, ra[ia]) : KEY_INF;
-                    } else {
-                        o[d] = rb[ib];
-                        ++ib;
-                        kb = ib < lb ? event_key<G>(xy, rb[ib]) : KEY_INF;
-                    }
-                }
-            }
-            __syncthreads();
-            unsigned *t = src; src = dst; dst = t;
-        }
-        if (src != A) {
-            for (unsigned k = tid; k < m; k += nt) A[k] = src[k];
-            __syncthreads();
-        }
-        // group flags; decoding ignores the halves' order, so neighbours may
-        // be rewritten concurrently
+        __syncthreads();
+        // the events grouped by sub-bucket into ev2
         for (unsigned k = tid; k < m; k += nt) {
             const unsigned e = A[k];
-            const bool c = k > 0 && event_key<G>(xy, A[k - 1]) == event_key<G>(xy, e);
-            A[k] = ev_pack(ev_i(e), ev_j(e), c);
+            C[atomicAdd(&s_cur[sub_of(event_key<G>(xy, e))], 1u)] = e;
+        }
+        __syncthreads();
+        const long long kmin = s_kmin[0], kmax = s_kmax[0];
+        for (int j = 0; j < F; ++j) {
+            const unsigned a0 = s_cnt[j], a1 = s_cnt[j + 1], mj = a1 - a0;
+            if (mj == 0) continue;
+            const long long lo = j == 0 ? kmin : s_spl[j - 1];
+            // kmax < KEY_INF (events have finite keys), so kmax + 1 does not overflow
+            const long long hi = j == F - 1 ? kmax + 1 : s_spl[j];
+            bool done = false;
+            if (mj <= (unsigned)SEG_CAP)
+                done = sort_bucket_words<G>(xy, C + a0, A + a0, mj, lo,
+                                            (unsigned long long)hi - (unsigned long long)lo, smem);
+            if (!done) {
+                // copy back, then the merge fallback in place (scratch: C)
+                for (unsigned k = tid; k < mj; k += nt) A[a0 + k] = C[a0 + k];
+                __syncthreads();
+                sort_big_merge<G>(xy, A + a0, C + a0, mj, smem);
+            }
         }
         __syncthreads();
     }
