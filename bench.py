@@ -467,7 +467,7 @@ def _timed(fit, steps, warmup, flush, stream, barrier):
 
 def batched_short(steps: int, warmup: int):
     """The batch workload (4096 uneven sets) with a fixed plan (plain kernel up
-    to 128 points, 48 streams, branch-and-bound from 1536 points), captured
+    to 128 points, 48 streams, branch-and-bound from 512 points), captured
     into one CUDA graph; each step replays it on a fresh batch already in HBM
     (y coordinates of another seed), timed with CUDA events."""
     import numpy as np
@@ -480,7 +480,7 @@ def batched_short(steps: int, warmup: int):
     y1 = (y0.astype(np.int64) + datagen.Stream(5001).integers(-2, 3, y0.size)).clip(-32768, 32767).astype(np.int16)
     xt, yt, ot = (torch.from_numpy(a).to(dev) for a in (x0, y0, off))
     ys = [torch.from_numpy(y0).to(dev), torch.from_numpy(y1).to(dev)]
-    plan = lms.BatchPlan(off, plain_max_n=128, streams=48, bnb_min_n=1536)
+    plan = lms.BatchPlan(off, plain_max_n=128, streams=48, bnb_min_n=512)
     out = torch.empty((4096, lms.RESULT_DTYPE.itemsize), dtype=torch.uint8, device=dev)
     plan.fit(xt, yt, ot, out=out)
     torch.cuda.synchronize()
@@ -509,7 +509,7 @@ def batched_short(steps: int, warmup: int):
     return {"value": v, "unit": UNIT, "ms_per_step": ms / steps, "candidate_slopes_per_sec": v / 4096 * slopes,
             "steps": steps, "warmup": warmup,
             "workload": "4096 sets, n log-uniform [64,4096], outliers U(0,0.45), angle U(-1.5,1.5)",
-            "plan": "plain kernel <= 128 points, 48 streams, branch-and-bound >= 1536 points, one CUDA graph"}
+            "plan": "plain kernel <= 128 points, 48 streams, branch-and-bound >= 512 points, one CUDA graph"}
 
 
 def hough_short(steps: int, warmup: int):

@@ -213,7 +213,7 @@ LMS_API int lms_fit_learned_host(lms_setnet *net, const void *x, const void *y, 
  * with at most plain_max_n points (0 = 256, at most 256) go to one
  * persistent plain kernel over (set, run of slopes) work items in three
  * size classes; larger sets (up to 32768 points) each get the exact sweep
- * of every slope or, from 1536 points on, the exact branch-and-bound, spread
+ * of every slope or, from 512 points on, the exact branch-and-bound, spread
  * over `streams` internal streams (0 = 8).  It allocates the plan's
  * device memory and waits for the device.
  *   offsets_host  B + 1 offsets of the sets in the x/y arrays (host).
@@ -229,7 +229,7 @@ LMS_API int lms_batch_plan_create(const int64_t *offsets_host, int64_t B, const 
                                   int32_t plain_max_n, int32_t streams, lms_batch_plan **plan);
 /* The same with the size from which a set is fitted by the exact
  * branch-and-bound (lms_fit_bnb's method, asynchronous, without statistics)
- * instead of the sweep of every slope: bnb_min_n 0 = 1536 points (the value
+ * instead of the sweep of every slope: bnb_min_n 0 = 512 points (the value
  * lms_batch_plan_create uses), > 0 = that size (at least 257), < 0 = never.
  * The branch-and-bound's result equals the sweep's bit for bit. */
 LMS_API int lms_batch_plan_create_ex(const int64_t *offsets_host, int64_t B, const int32_t *h_host,

@@ -25,7 +25,7 @@ CACHE = os.environ.get("LMS_AUTOTUNE_CACHE") or os.path.join(os.path.dirname(os.
                                                              "autotune_cache.json")
 PLAIN_MAX = (64, 128, 256)
 STREAMS = (8, 16, 32, 48)
-BNB_MIN = (1024, 1536, 2048, 3072, -1)   # -1: every large set takes the sweep of every slope
+BNB_MIN = (384, 512, 768, 1536, -1)   # -1: every large set takes the sweep of every slope
 
 
 def _key(offsets, device_name):

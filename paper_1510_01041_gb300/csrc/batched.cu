@@ -21,7 +21,7 @@ namespace lms {
 namespace {
 
 constexpr int CHUNK = 64;   // slopes per work item of the plain kernel
-constexpr int BATCH_BNB_MIN_N = 1536;   // default size from which a set takes the branch-and-bound
+constexpr int BATCH_BNB_MIN_N = 512;   // default size from which a set takes the branch-and-bound
 
 template <typename K>
 __device__ __forceinline__ void cxk(K &a, K &b)
