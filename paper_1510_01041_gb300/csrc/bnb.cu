@@ -21,7 +21,10 @@
 //
 // The upper bound comes from a few dyadic slopes: the sampled slopes nearest
 // a seed slope (a learned prediction) or, without a seed, evenly spaced
-// quantiles of the sample.
+// quantiles of the sample, then zoom passes around the best.  Steep and
+// unbounded intervals get the bound |s| dh - yr (any h points span at least
+// dh in x and at most yr in y); kept buckets holding many events are cut
+// into sub-intervals and bounded once more (refinement).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -120,7 +120,7 @@ struct SweepPlan {
                                //        the list of kept pairs of a restricted count
     unsigned *range;           // [2W] range event bounds
     unsigned short *orders;    // [W][n] start orders
-    unsigned long long *gsort; // [W][P] global sort scratch when n > SORT_SMEM_N
+    unsigned long long *gsort; // [W][2P] words, then [W][P] 16-bit payloads: start sorts when n > SORT_SMEM_N
     Cand *cands;               // [W + G] range-start + sweeping-warp candidates
     unsigned short *gpos;      // [G][n] positions of the sweeping warps when !pos_smem (else null)
     // A restricted pass with resplit set sorts its kept events in buckets of

@@ -14,14 +14,18 @@
 // Pipeline (all on one stream, no host synchronisation):
 //   pack      points -> 32-bit words
 //   sample    S pseudo-random pairs -> exact slope keys
-//   sort      sample: shared-memory bitonic chunks + rank merges
+//   sort      sample: shared-memory merge-sorted chunks, one rank merge
 //   splitters quantiles of the sample -> slope-bucket boundaries (a key
 //             that fills whole quantiles gets a bucket of its own)
-//   count     every pair -> bucket, per-CTA shared-memory histograms
+//   count     every pair -> bucket, per-CTA shared-memory histograms (a
+//             restricted pass instead lists the pairs of the kept buckets:
+//             all-pairs tiles with a float cover test, or a band scan over
+//             the points sorted at each cover's lower slope)
 //   prefix    per-bucket offsets of each CTA; scan -> bucket starts
 //   scatter   every pair -> its bucket (4-byte event)
-//   segsort   each bucket sorted by exact slope key in shared memory;
-//             the event word records "same slope as previous event"
+//   segsort   each bucket sorted by exact slope key in shared memory (a
+//             bucket above SEG_CAP events by one more level of sample sort
+//             inside it); the event word records "same slope as previous"
 //   plan      contiguous bucket ranges with equal event counts -> sweepers
 //   init      per sweeper: sort the points at its first slope, score every
 //             window there
