@@ -288,7 +288,7 @@ constexpr unsigned long long BNB_MIN_RANGE = 64;   // events per swept range, at
 #define LMS_PRED_WINDOW 0.35
 #endif
 #ifndef LMS_LEARNED_ROUNDS
-#define LMS_LEARNED_ROUNDS 3
+#define LMS_LEARNED_ROUNDS 2
 #endif
 constexpr double PRED_WINDOW = LMS_PRED_WINDOW;   // radians around a predicted slope angle
 
@@ -379,7 +379,8 @@ __global__ void k_pick_seeds(const long long *__restrict__ sorted, const int *__
 // [r* - span, r* + span] around the best seed of the previous round
 // (smallest width, ties to the smaller index), r* the rank of its key in the
 // sorted sample and span the previous round's spacing of sample ranks
-// (round 2: m / KS, m the valid samples; round 3: 2 span_2 / KS).  The upper
+// (round 2: m / KS, m the valid samples; a round 3, when configured:
+// 2 span_2 / KS).  The upper
 // bound only needs some real slope with a narrow window; narrowing the
 // search where the previous round found the narrowest windows brings it
 // close to the optimum, and the tighter the bound the fewer slope intervals
@@ -440,9 +441,11 @@ size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 }  // namespace
 
 // Upper-bound slopes per round (one CTA each, one wave) and rounds: a first
-// round of seeds, then zoom rounds around the best slope found so far.
+// round of seeds, then a zoom round around the best slope found (a third
+// round tightens the bound but costs more than the events it saves).
 constexpr int BNB_SEEDS_MAX = 256;
-constexpr int BNB_ROUNDS = 3;
+constexpr int BNB_ROUNDS = 2;
+constexpr int ROUNDS_MAX = BNB_ROUNDS > LMS_LEARNED_ROUNDS ? BNB_ROUNDS : LMS_LEARNED_ROUNDS;
 int bnb_seeds(int sms) { return std::max(64, std::min(BNB_SEEDS_MAX, sms)); }
 constexpr int BNB_FIRST_NODES = 128;
 // Levels of the interval tree.  The split after the second-to-last level
@@ -1147,7 +1150,7 @@ size_t bnb_extra_bytes(int n, int sms)
     const int grid = 2 * sms;
     size_t b = 0;
     b += a256(64);                                   // xc, ub
-    b += a256((size_t)BNB_SEEDS_MAX * BNB_ROUNDS * 8 * 2);   // seed keys, seed widths of every round
+    b += a256((size_t)BNB_SEEDS_MAX * ROUNDS_MAX * 8 * 2);   // seed keys, seed widths of every round
     b += a256(sizeof(TreeState));                    // tree state
     b += 2 * a256((size_t)BND_MAX * sizeof(int2));   // nodes, two levels
     b += 2 * a256((size_t)BND_MAX * 2 * 8);          // node keys, two levels
@@ -1179,8 +1182,8 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
     int *xc = (int *)take(64);
     long long *ub = (long long *)(xc + 4);
     const int KS = bnb_seeds(sms);
-    long long *seed_keys = (long long *)take((size_t)BNB_SEEDS_MAX * BNB_ROUNDS * 8 * 2);
-    long long *seed_w = seed_keys + (size_t)KS * BNB_ROUNDS;
+    long long *seed_keys = (long long *)take((size_t)BNB_SEEDS_MAX * ROUNDS_MAX * 8 * 2);
+    long long *seed_w = seed_keys + (size_t)KS * ROUNDS_MAX;
     TreeState *ts = (TreeState *)take(sizeof(TreeState));
     int2 *nodes[2];
     nodes[0] = (int2 *)take((size_t)BND_MAX * sizeof(int2));
