@@ -5,7 +5,8 @@ gives the same result as lms_fit's plain path and as the oracle.  Called
 directly through the C ABI, twice in a row on different inputs, so the
 second call reuses the shared fixed scratch array left by the first; the
 capacity edge (n = 1024) and a non-default order statistic are compared with
-the oracle, and n = 1025 is refused.  Kept in a file that pytest collects
+the oracle, and n = 1025 is refused.  The call is also captured in a CUDA
+graph and replayed on new points.  Kept in a file that pytest collects
 last."""
 import ctypes
 
@@ -80,3 +81,43 @@ def test_noalloc_rejects_above_capacity(L):
         rc = L.lib().lms_fit_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), n, 0,
                                      ctypes.c_void_p(out.data_ptr()), None)
         assert rc == L.LMS_ERR_TOO_LARGE and "capacity" in L.status_str(rc)
+
+
+def test_noalloc_captured_in_a_cuda_graph(L, orc):
+    """After one warm-up call, the call is captured in a CUDA graph on a side
+    stream in torch's global capture mode, which refuses the allocation and
+    synchronising calls a capture cannot hold.  The graph is replayed on new
+    points copied into the same input buffers, and each replay equals the
+    oracle.  The replays leave the device's free memory unchanged."""
+    n = 900
+    x, y = datagen.line_with_outliers(n, 41)
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    out = torch.zeros(L.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+
+    def call(stream):
+        return L.lib().lms_fit_noalloc(ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(yt.data_ptr()), n, 0,
+                                       ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+
+    assert call(torch.cuda.current_stream()) == L.LMS_OK
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            rc = call(s)
+    assert rc == L.LMS_OK, L.status_str(rc)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    rng = np.random.default_rng(42)
+    for k in range(3):
+        y2 = (y.astype(np.int64) + rng.integers(-3, 4, n)).clip(-32768, 32767).astype(np.int16)
+        yt.copy_(torch.from_numpy(y2))
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        got = L.decode(out)[0]
+        o = orc.lms_i16(x, y2, 0, "sweep")
+        assert L.exact_fields(got) == o.exact(), k
+        assert (got["theta1"], got["theta2"], got["med_sq"]) == (o.theta1, o.theta2, o.med_sq)
+    assert torch.cuda.mem_get_info()[0] == free0
