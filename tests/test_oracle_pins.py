@@ -321,3 +321,63 @@ def test_float_oracle(orc):
     assert (a.theta1, a.theta2, a.med_sq, a.i, a.j) == (b.theta1, b.theta2, b.med_sq, b.i, b.j)
     c = orc.lms_f32(xf * np.float32(8), yf * np.float32(8), 0, "sweep")
     assert c.med_sq == 64 * b.med_sq and c.theta1 == b.theta1
+
+
+def _float_small(rng, n, trial):
+    """Tiny float32 sets with fractional bits: spread exponents, dyadic
+    grids with duplicates and repeated x, and exact float lines."""
+    kind = trial % 4
+    if kind == 0:
+        x = rng.standard_normal(n) * 2.0 ** rng.integers(-6, 7, n)
+        y = rng.standard_normal(n) * 2.0 ** rng.integers(-6, 7, n)
+    elif kind == 1:
+        x = rng.integers(-12, 12, n) / 8.0
+        y = rng.integers(-40, 40, n) / 16.0
+        m = n // 2
+        x[:m] = x[n - m:]
+    elif kind == 2:
+        x = rng.integers(-3, 3, n) * 0.375
+        y = rng.standard_normal(n) * 10.0
+    else:
+        x = rng.integers(-20, 20, n) / 4.0
+        y = 0.5 * x + 0.25
+        k = n // 3
+        y[:k] = rng.standard_normal(k) * 4.0
+    return x.astype(np.float32), y.astype(np.float32)
+
+
+@pytest.mark.parametrize("method", ["brute", "sweep"])
+def test_float_oracle_equals_exhaustive_subsets(orc, method):
+    """The float path (coordinates scaled by 2^scale_exp into exact integers)
+    against the definition in exact rationals on the float values as given
+    (Sec. 1 Eq. 1, Sec. 3.1): the pair exactly; the width, slope and centre
+    exactly where they fit the result's int64 fields (which hold 0 when they
+    do not); and the reported doubles within the roundings of their
+    conversion (the 128-bit numerator and denominator each rounded to double,
+    one division, and for med_sq one product)."""
+    rng = np.random.default_rng(4242)
+    checked = exact = 0
+    for trial in range(160):
+        n = int(rng.integers(2, 9))
+        x, y = _float_small(rng, n, trial)
+        h = int(rng.integers(1, n + 1)) if trial % 3 == 0 else n // 2 + 1
+        r = orc.lms_f32(x, y, h, method)
+        pts = [(Fraction(float(a)), Fraction(float(b))) for a, b in zip(x, y)]
+        t = tiny.lms_subsets(pts, h)
+        if t is None:
+            assert r.status == orc.ERR_VERTICAL
+            continue
+        w, s, c, pair = t
+        assert r.status == orc.OK
+        assert (r.i, r.j) == pair, (x, y, h)
+        if r.s_den:
+            sc = Fraction(2) ** r.scale_exp
+            got = (Fraction(r.w_num, r.w_den) / sc, Fraction(r.s_num, r.s_den), Fraction(r.t_num, r.t_den) / sc)
+            assert got == (w, s, c), (x, y, h)
+            exact += 1
+        u = 2.0 ** -53
+        assert abs(r.theta1 - float(s)) <= 4 * u * abs(float(s))
+        assert abs(r.theta2 - float(c)) <= 4 * u * abs(float(c))
+        assert abs(r.med_sq - float((w / 2) ** 2)) <= 8 * u * float((w / 2) ** 2)
+        checked += 1
+    assert checked > 120 and exact > 80
