@@ -193,7 +193,9 @@ LMS_API int lms_setnet_train_step(lms_setnet *net, const int16_t *x, const int16
 /* checkpoint: weights and optimiser state (synchronous) */
 LMS_API int lms_setnet_save(const lms_setnet *net, const char *path);
 LMS_API int lms_setnet_load(lms_setnet *net, const char *path);
-/* the network predicts the slope of one set, branch-and-bound takes it as its seed */
+/* the network predicts the slope of one set, branch-and-bound takes it as its
+ * seed.  LMS_ERR_ARG (a null net, or any argument lms_fit_bnb refuses) is
+ * returned before any work is queued. */
 LMS_API int lms_fit_learned(lms_setnet *net, const void *x, const void *y, int64_t n, int64_t h,
                             const lms_options *opt, lms_result *out, lms_bnb_stats *stats,
                             lms_stream_t stream);

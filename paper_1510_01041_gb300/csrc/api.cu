@@ -190,6 +190,13 @@ int run_fit(const void *x, const void *y, int n, int h, int dtype, const lms_opt
 
 }  // namespace
 
+int check_bnb_args(const void *x, const void *y, int64_t n, int64_t h, const lms_options *opt, const void *out)
+{
+    lms_options o = opt ? *opt : lms_options{};
+    o.algorithm = LMS_ALGO_BNB;
+    return check_args(x, y, n, h, LMS_I16, &o, out);
+}
+
 int fit_bnb_after(const void *x, const void *y, int64_t n, int64_t h, const float *seed_slope, const lms_options *opt,
                   lms_result *out, lms_bnb_stats *stats, cudaStream_t st, cudaEvent_t pred_ready)
 {

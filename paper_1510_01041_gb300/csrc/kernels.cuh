@@ -183,6 +183,8 @@ int run_bnb(const SweepPlan &p, const short *x, const short *y, const float *pre
 // lms_fit_bnb with the event above
 int fit_bnb_after(const void *x, const void *y, int64_t n, int64_t h, const float *seed_slope, const lms_options *opt,
                   lms_result *out, lms_bnb_stats *stats, cudaStream_t st, cudaEvent_t pred_ready);
+// the argument checks of lms_fit_bnb (LMS_OK or LMS_ERR_ARG), no device work
+int check_bnb_args(const void *x, const void *y, int64_t n, int64_t h, const lms_options *opt, const void *out);
 
 // ---------------------------------------------------------------- argmin
 cudaError_t launch_argmin(const Cand *cands, int count, lms_result *out, int algorithm, const int *err,

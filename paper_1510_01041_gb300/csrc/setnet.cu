@@ -523,7 +523,9 @@ int lms_setnet_load(lms_setnet *net, const char *path)
 int lms_fit_learned(lms_setnet *net, const void *x, const void *y, int64_t n, int64_t h, const lms_options *opt,
                     lms_result *out, lms_bnb_stats *stats, lms_stream_t stream)
 {
-    if (!net || !x || !y || !out || n < 2) return LMS_ERR_ARG;
+    // every argument is checked before the forward pass is queued on the
+    // side stream
+    if (!net || check_bnb_args(x, y, n, h, opt, out)) return LMS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!net->side) {
         if (cudaStreamCreateWithFlags(&net->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -553,7 +555,7 @@ int lms_fit_learned(lms_setnet *net, const void *x, const void *y, int64_t n, in
 int lms_fit_learned_host(lms_setnet *net, const void *x, const void *y, int64_t n, int64_t h,
                          const lms_options *opt, lms_result *out, lms_bnb_stats *stats, lms_stream_t stream)
 {
-    if (!net || !x || !y || !out || n < 2 || n > 65536) return LMS_ERR_ARG;
+    if (!net || check_bnb_args(x, y, n, h, opt, out)) return LMS_ERR_ARG;
     if (!net->hx) {
         if (cudaMalloc(&net->hx, sizeof(short) * 65536) != cudaSuccess ||
             cudaMalloc(&net->hy, sizeof(short) * 65536) != cudaSuccess ||
