@@ -19,7 +19,9 @@ oracle):
 The previous fixed-slope workload (slope 0.7, 40% outliers) is timed beside
 them (``line_40pct``).  Every step uses a fresh seeded instance already
 resident in HBM; L2 is flushed (256 MB write) before each step, outside the
-timed events.  ``e2e`` runs the learned fit through the host-buffer entry
+timed events.  The two branch-and-bound arms are timed as CUDA-graph
+replays, one graph per step captured after the warm-up; the others as
+direct calls.  ``e2e`` runs the learned fit through the host-buffer entry
 point lms_fit_learned_host, copies included.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
