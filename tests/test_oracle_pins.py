@@ -381,3 +381,24 @@ def test_float_oracle_equals_exhaustive_subsets(orc, method):
         assert abs(r.med_sq - float((w / 2) ** 2)) <= 8 * u * float((w / 2) ** 2)
         checked += 1
     assert checked > 120 and exact > 80
+
+
+def test_eval_slope_equals_subset_window(orc):
+    """The oracle's window at a given rational slope (used by the large-size
+    certificate tests) equals the definition by subsets at that slope: the
+    narrowest range of h projections and the smallest centre among the
+    narrowest (Sec. 3.1), for reduced and unreduced slopes, h = 1 .. n."""
+    rng = np.random.default_rng(99)
+    for trial in range(300):
+        n = int(rng.integers(1, 9))
+        x, y = _random_small(rng, n, int(rng.choice([3, 30, 30000])))
+        h = int(rng.integers(1, n + 1))
+        sd = int(rng.integers(1, 40))
+        sn = int(rng.integers(-200, 201)) if trial % 5 else int(rng.integers(-40000, 40001))
+        k = int(rng.integers(1, 4))
+        r = orc.eval_slope_i16(x, y, sn * k, sd * k, h)
+        assert r.status == orc.OK
+        w, c = tiny.window_width_at(list(zip(x.tolist(), y.tolist())), h, Fraction(sn, sd))
+        assert Fraction(r.w_num, r.w_den) == w, (x, y, h, sn, sd)
+        assert Fraction(r.t_num, r.t_den) == c, (x, y, h, sn, sd)
+        assert Fraction(r.s_num, r.s_den) == Fraction(sn, sd)
