@@ -203,7 +203,15 @@ LMS_API int lms_fit_learned(lms_setnet *net, const void *x, const void *y, int64
  * memory makes the copies asynchronous) and a host result: copies the points
  * into device staging owned by `net` (allocated on the first such call, kept
  * until lms_setnet_destroy), fits, copies the result back and waits for
- * `stream`.  One net must not run two host-buffer fits at once. */
+ * `stream`.  One net must not run two host-buffer fits at once.  Without
+ * statistics (stats NULL) and with profiling off, the device part of
+ * repeated calls with the same n, h and options runs as one CUDA graph:
+ * captured on a stream owned by `net` by the second such call and replayed
+ * on `stream` by the later ones (the same kernels, without a host launch
+ * call for each).  It is captured again after the workspace moves (it grows,
+ * or lms_set_workspace installs another) or the net's per-set buffers grow,
+ * and is freed by lms_setnet_destroy; a failed capture falls back to direct
+ * calls for that key. */
 LMS_API int lms_fit_learned_host(lms_setnet *net, const void *x, const void *y, int64_t n, int64_t h,
                                  const lms_options *opt, lms_result *out, lms_bnb_stats *stats,
                                  lms_stream_t stream);

@@ -20,6 +20,7 @@ struct DeviceWs {
     size_t own_bytes = 0;
     void *ext = nullptr;       // caller-installed buffer
     size_t ext_bytes = 0;
+    unsigned long long gen = 0;   // bumped whenever the buffer in use may change
 };
 
 constexpr int MAX_DEV = 64;
@@ -63,6 +64,7 @@ int workspace(size_t bytes, cudaStream_t st, void **out)
             w.own_bytes = 0;
         }
         size_t grow = bytes + bytes / 8 + (1u << 20);
+        ++w.gen;
         if (cudaMalloc(&w.own, grow) != cudaSuccess) {
             cudaGetLastError();
             w.own = nullptr;
@@ -190,6 +192,14 @@ int run_fit(const void *x, const void *y, int n, int h, int dtype, const lms_opt
 
 }  // namespace
 
+unsigned long long workspace_generation()
+{
+    int dev;
+    if (current_device(dev)) return ~0ull;
+    std::lock_guard<std::mutex> lock(g_mu);
+    return g_ws[dev].gen;
+}
+
 int check_bnb_args(const void *x, const void *y, int64_t n, int64_t h, const lms_options *opt, const void *out)
 {
     lms_options o = opt ? *opt : lms_options{};
@@ -298,6 +308,7 @@ int lms_set_workspace(void *device_buffer, size_t bytes)
     std::lock_guard<std::mutex> lock(g_mu);
     g_ws[dev].ext = device_buffer;
     g_ws[dev].ext_bytes = device_buffer ? bytes : 0;
+    ++g_ws[dev].gen;
     return LMS_OK;
 }
 

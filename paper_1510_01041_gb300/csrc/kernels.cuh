@@ -185,6 +185,13 @@ int fit_bnb_after(const void *x, const void *y, int64_t n, int64_t h, const floa
                   lms_result *out, lms_bnb_stats *stats, cudaStream_t st, cudaEvent_t pred_ready);
 // the argument checks of lms_fit_bnb (LMS_OK or LMS_ERR_ARG), no device work
 int check_bnb_args(const void *x, const void *y, int64_t n, int64_t h, const lms_options *opt, const void *out);
+// changes whenever the current device's workspace buffer may have moved (a
+// captured graph that uses it must then be captured again)
+unsigned long long workspace_generation();
+// whether per-launch profiling events are on; launches run by replaying a
+// captured graph, added to the launch counter
+bool profiling_on();
+void add_launches(long long count);
 
 // ---------------------------------------------------------------- argmin
 cudaError_t launch_argmin(const Cand *cands, int count, lms_result *out, int algorithm, const int *err,

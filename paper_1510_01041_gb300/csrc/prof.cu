@@ -47,6 +47,10 @@ const char *const kNames[STAGE_COUNT] = {
 
 }  // namespace
 
+bool profiling_on() { return g_on.load(std::memory_order_relaxed); }
+
+void add_launches(long long count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+
 StageTimer::StageTimer(int stage, cudaStream_t st) : stage_(stage), st_(st), a_(nullptr)
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -325,6 +325,15 @@ struct lms_setnet {
     lms_result *hres;                     // device result of host-buffer fits
     cudaStream_t side;                    // the forward pass of a learned fit runs here ...
     cudaEvent_t ev_fork, ev_join;         // ... beside the branch-and-bound's sampling stage
+    // The device part of host-buffer fits (staging to result) as a CUDA graph
+    // for one key (n, h, options, workspace generation), captured on `cap` by
+    // the second call with that key and replayed by the later ones.
+    cudaStream_t cap;
+    cudaGraphExec_t hg_exec;
+    long long hg_n, hg_h, hg_launches;
+    lms_options hg_opt;
+    unsigned long long hg_gen;
+    int hg_seen;                          // calls with the key so far; negative: capture failed
 };
 
 namespace {
@@ -333,6 +342,9 @@ int grow_sets(lms_setnet *net, int B)
 {
     if (B <= net->max_sets) return LMS_OK;
     cudaDeviceSynchronize();
+    if (net->hg_exec) cudaGraphExecDestroy(net->hg_exec);   // it holds the old buffers
+    net->hg_exec = nullptr;
+    net->hg_seen = 0;
     cudaFree(net->state); cudaFree(net->dout); cudaFree(net->pred); cudaFree(net->pool);
     net->state = nullptr; net->dout = nullptr; net->pred = nullptr; net->pool = nullptr;
     int cap = 64;
@@ -412,6 +424,8 @@ void lms_setnet_destroy(lms_setnet *net)
     if (net->side) cudaStreamDestroy(net->side);
     if (net->ev_fork) cudaEventDestroy(net->ev_fork);
     if (net->ev_join) cudaEventDestroy(net->ev_join);
+    if (net->hg_exec) cudaGraphExecDestroy(net->hg_exec);
+    if (net->cap) cudaStreamDestroy(net->cap);
     delete net;
 }
 
@@ -552,6 +566,76 @@ int lms_fit_learned(lms_setnet *net, const void *x, const void *y, int64_t n, in
     return fit_bnb_after(x, y, n, h, net->pred + 2, opt, out, stats, st, net->ev_join);
 }
 
+}  // extern "C"
+
+namespace {
+
+// The device part of a host-buffer fit (points already staged in hx, hy;
+// result into hres), by replaying the graph cached for its key.  The first
+// call with a key returns false (the caller fits directly, which also grows
+// every buffer the fit needs); the second captures the fit on the net's own
+// stream (any stream the caller passes, the legacy default stream included,
+// can then launch it) and replays it.  Returns false also for a key whose
+// capture failed; otherwise rc holds the launch status.
+bool replay_host_fit(lms_setnet *net, int64_t n, int64_t h, const lms_options *opt, cudaStream_t st, int &rc)
+{
+    lms_options o;
+    memset(&o, 0, sizeof o);
+    if (opt) memcpy(&o, opt, sizeof o);
+    const unsigned long long gen = workspace_generation();
+    if (net->hg_n != n || net->hg_h != h || net->hg_gen != gen || memcmp(&net->hg_opt, &o, sizeof o) != 0) {
+        if (net->hg_exec) cudaGraphExecDestroy(net->hg_exec);
+        net->hg_exec = nullptr;
+        net->hg_n = n;
+        net->hg_h = h;
+        net->hg_gen = gen;
+        memcpy(&net->hg_opt, &o, sizeof o);
+        net->hg_seen = 0;
+    }
+    if (!net->hg_exec) {
+        if (net->hg_seen < 1) {
+            if (net->hg_seen == 0) net->hg_seen = 1;
+            return false;
+        }
+        if (!net->cap && cudaStreamCreateWithFlags(&net->cap, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            net->cap = nullptr;
+            net->hg_seen = -1;
+            return false;
+        }
+        const long long l0 = lms_launch_count();
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        if (cudaStreamBeginCapture(net->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const int frc = lms_fit_learned(net, net->hx, net->hy, n, h, opt, net->hres, nullptr,
+                                            reinterpret_cast<lms_stream_t>(net->cap));
+            const cudaError_t ce = cudaStreamEndCapture(net->cap, &g);
+            if (frc == LMS_OK && ce == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess)
+                ex = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (!ex) {
+            net->hg_seen = -1;
+            return false;
+        }
+        net->hg_exec = ex;
+        net->hg_launches = lms_launch_count() - l0;
+    }
+    if (cudaGraphLaunch(net->hg_exec, st) != cudaSuccess) {
+        cudaGetLastError();
+        rc = LMS_ERR_CUDA;
+        return true;
+    }
+    add_launches(net->hg_launches);
+    rc = LMS_OK;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
 int lms_fit_learned_host(lms_setnet *net, const void *x, const void *y, int64_t n, int64_t h,
                          const lms_options *opt, lms_result *out, lms_bnb_stats *stats, lms_stream_t stream)
 {
@@ -571,8 +655,13 @@ int lms_fit_learned_host(lms_setnet *net, const void *x, const void *y, int64_t 
     if (cudaMemcpyAsync(net->hx, x, sizeof(short) * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(net->hy, y, sizeof(short) * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return LMS_ERR_CUDA;
-    const int rc = lms_fit_learned(net, net->hx, net->hy, n, h, opt, net->hres, stats, stream);
-    if (rc) return rc;
+    int rc = LMS_OK;
+    if (!stats && !profiling_on() && replay_host_fit(net, n, h, opt, st, rc)) {
+        if (rc) return rc;
+    } else {
+        rc = lms_fit_learned(net, net->hx, net->hy, n, h, opt, net->hres, stats, stream);
+        if (rc) return rc;
+    }
     if (cudaMemcpyAsync(out, net->hres, sizeof(lms_result), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return LMS_ERR_CUDA;
