@@ -540,8 +540,9 @@ def node_bound_ops(n: int) -> int:
     """Algorithmic int32 instruction-equivalents of one slope interval's lower
     bound: projections of all points at both interval ends (4n, 4 ops each:
     a 32x32->64 multiply-add, shift, subtract, min/max), two comparison sorts
-    of n 64-bit words (n ceil(log2 n) comparisons each, 4 ops per 64-bit
-    compare-and-select) and one scan of the n - h + 1 windows (3 ops each)."""
+    of n 32-bit keys (n ceil(log2 n) merge steps each, 4 ops a step: compare,
+    select the value, advance an index, select the new head) and one scan of
+    the n - h + 1 windows (3 ops each)."""
     lg = max(1, math.ceil(math.log2(n)))
     return 4 * n * 4 + 2 * n * lg * 4 + 3 * n
 
